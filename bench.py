@@ -1,0 +1,289 @@
+#!/usr/bin/env python3
+"""Benchmark of the SEM Poisson hot path on GB300.
+
+One step = one complete mixed-precision (FP32 operator / FP64 gather-scatter
+sums, dots and refinement) Jacobi PCG solve to a relative residual of 1e-8 on
+the deformed 32x32x32-element, N = 7 box (16.8 M local DOFs), right-hand side
+uniform in [-1, 1) per global node (seed 0), inputs resident in HBM.
+`value` = local DOFs x PCG iterations / step time (GDOF/s), summed over ranks.
+
+Extra keys: time to solution (mixed and FP64), the FP32 and FP64 operator
+throughput, the roofline of the dominant kernel (the FP32 element operator),
+the clocks seen during the timed region, the end-to-end number through the
+C-ABI with host buffers, and the CPU oracle timed on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Ax GDOF/s + PCG time-to-1e-8 residual, mixed/learned vs FP64, 1 GB300"
+WORKLOAD = dict(kx=32, ky=32, kz=32, N=7, deform=True, rhs="uniform[-1,1) per global node, seed 0",
+                tol=1e-8)
+WORKLOAD_NAME = "deformed 32x32x32 hex, N=7 (16.8M local DOFs), Jacobi PCG to 1e-8, mixed FP32/FP64"
+# a bounded sample of the same work for the CPU oracle: 8x8x8 elements, N = 7, deformed
+CPU_SAMPLE = dict(k=8, N=7, iters=12)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sample=CPU_SAMPLE):
+    """The CPU oracle as it stands, on a bounded sample of the same work."""
+    import numpy as np
+    from oracle import sem_oracle as so
+    P = so.Problem(sample["k"], sample["k"], sample["k"], sample["N"], deform=True)
+    b = P.rhs_uniform(0)
+    t0 = time.perf_counter()
+    _, it, _ = P.pcg(b, fixed_iters=sample["iters"])
+    dt = time.perf_counter() - t0
+    value = P.L * it / dt / 1e9
+    return {"value": value, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample['iters']} FP64 Jacobi PCG iterations of the numpy oracle on a deformed "
+                      f"{sample['k']}^3-element N={sample['N']} box ({P.L} local DOFs), "
+                      f"{dt:.2f} s; GDOF/s = local DOFs x iterations / time"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    steps = []
+    for _ in range(max(args.warmup, 0)):
+        cpu_baseline(dict(CPU_SAMPLE, iters=2))
+    for _ in range(args.steps):
+        steps.append(cpu_baseline(dict(CPU_SAMPLE, iters=4)))
+    vals = [s["value"] for s in steps]
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample": "deformed 8^3 elements N=7, 4 iterations per step"},
+            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+                             "sample": steps[-1]["sample"]},
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_2503_02134_gb300 as sem
+
+    stream = torch.cuda.Stream()
+    W = WORKLOAD
+    S = sem.Solver(W["kx"], W["ky"], W["kz"], W["N"], deform=W["deform"], stream=stream.cuda_stream)
+    L = S.L
+    with torch.cuda.stream(stream):
+        b = torch.empty(L, dtype=torch.float64, device="cuda")
+        x = torch.empty(L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 0 + rank, b)
+    stream.synchronize()
+
+    def step(prec=sem.SEM_MIXED_FP32):
+        _, info = S.solve(b, tol=W["tol"], maxit=5000, precision=prec, x=x)
+        return info
+
+    for _ in range(max(args.warmup, 3)):
+        info = step()
+    # timed region
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    clocks = Clocks(local)
+    with clocks:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms = ms_total / args.steps
+    iters = sum(i["iters"] for i in infos)
+    units = L * iters * world
+    value = units / (ms_total * 1e-3) / 1e9
+    launches = sum(i["launches"] for i in infos)
+    ok = all(i["rc"] == 0 and i["relres_true"] <= W["tol"] * 1.0000001 for i in infos)
+
+    # FP64 time to solution on the same problem (untimed by the step loop)
+    info64 = step(sem.SEM_FP64)
+    info_mixed = infos[-1]
+
+    # operator throughput and the roofline of the FP32 element operator, timed
+    # with CUDA events on the stream the library launches on
+    def time_ax(prec, reps=20, local_only=True):
+        dt = torch.float64 if prec == sem.SEM_FP64 else torch.float32
+        with torch.cuda.stream(stream):
+            u = torch.rand(L, dtype=dt, device="cuda")
+            w = torch.empty_like(u)
+        fn = sem.sem_ax_local if local_only else sem.sem_ax
+        for _ in range(3):
+            fn(S.h, u, w, prec)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn(S.h, u, w, prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ax32_ms = time_ax(sem.SEM_MIXED_FP32)
+    ax32_full_ms = time_ax(sem.SEM_MIXED_FP32, local_only=False)
+    ax64_ms = time_ax(sem.SEM_FP64, reps=5)
+    hbm, peak_kind = peaks()
+    bytes_per_dof = 32.0   # FP32: read u + 6 G, write w
+    achieved = L * bytes_per_dof / (ax32_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "kernel": "ax_kernel<8,float> (sem_ax_local, FP32 element operator)",
+                "algorithmic_bytes_per_launch": L * bytes_per_dof, "launch_ms": ax32_ms,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+
+    # end to end through the C-ABI with host (pinned) buffers
+    fh = torch.empty(L, dtype=torch.float64, pin_memory=True)
+    fh.copy_(b.cpu())
+    xh = torch.empty(L, dtype=torch.float64, pin_memory=True)
+    e2e_t, e2e_it = [], 0
+    for _ in range(2):
+        t0 = time.perf_counter()
+        rc, inf = sem.sem_pcg_solve(S.h, fh, None, xh, W["tol"], 5000, sem.SEM_MIXED_FP32)
+        e2e_t.append(time.perf_counter() - t0)
+        e2e_it = inf.iters
+    e2e_s = min(e2e_t)
+    e2e = {"value": L * e2e_it * world / e2e_s / 1e9, "unit": "GDOF/s",
+           "h2d_bytes_per_step": 8 * L, "d2h_bytes_per_step": 8 * L,
+           "time_to_solution_ms": e2e_s * 1e3}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "elements": S.E, "N": S.N, "local_dofs": L,
+                       "unique_dofs": S.U, "tol": W["tol"], "rhs": W["rhs"],
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (G alone is 403 MB FP32)"},
+            "time_to_solution_ms": ms, "iterations": info_mixed["iters"],
+            "refinements": info_mixed["refinements"], "relres_true": info_mixed["relres_true"],
+            "converged": ok,
+            "fp64": {"time_to_solution_ms": info64["solve_ms"], "iterations": info64["iters"],
+                     "relres_true": info64["relres_true"]},
+            "speedup_vs_fp64": info64["solve_ms"] / ms,
+            "ax_gdofs_fp32": L / (ax32_ms * 1e-3) / 1e9,
+            "ax_gdofs_fp32_with_gs": L / (ax32_full_ms * 1e-3) / 1e9,
+            "ax_gdofs_fp64": L / (ax64_ms * 1e-3) / 1e9,
+            "roofline": roofline, "clocks": clocks.summary(), "e2e": e2e,
+            "gpu_launches": launches,
+        }
+        if not args.no_cpu and world >= 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    S.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/*
+ * sem.h -- C-ABI of the GB300 spectral-element Poisson library (libsem.so).
+ *
+ * The library implements the hot path of the Nekbone/Neko-style SEM Poisson
+ * solve studied in "Enabling mixed-precision in spectral element codes"
+ * (arXiv 2503.02134):
+ *   - the matrix-free element operator w_L = sum_a D_a^T (sum_b G_ab D_b u_L)
+ *     (Sec. 3.1, profiling table, kernel `ax`: local_grad3, geometric
+ *     factors, local_grad3_t);
+ *   - the direct-stiffness summation Sigma' = Q Q^T over shared GLL nodes
+ *     (Sec. 3.3, "Global communication and gather-scatter modes");
+ *   - the Jacobi preconditioner z = J^{-1} r, J^{-1} = 1/diag(A) (Sec. 4.3);
+ *   - the preconditioned CG loop of the profiling table, in FP64 and in the
+ *     paper's mixed strategy (FP32 loop operations, FP64 gather-scatter
+ *     accumulation and FP64 dot products; Sec. 3.3 and 4.3, Table
+ *     "Evaluation of mixed-precision strategies in Neko"), plus an FP64
+ *     residual / iterative-refinement outer loop.
+ *
+ * Conventions shared by every entry point
+ *   - Vectors are LOCAL (unassembled) vectors of L = E*(N+1)^3 values,
+ *     element-major; inside an element, node (i,j,k) is at i + n*j + n*n*k
+ *     with n = N+1 (i runs along the reference direction r).
+ *   - Pointers may be device pointers (cudaMalloc, PyTorch CUDA tensors) or
+ *     host pointers; host buffers are staged through device buffers owned by
+ *     the handle (copies are enqueued on the handle's stream).  The caller
+ *     owns every pointer it passes; the library never frees them.
+ *   - All device work is enqueued on the stream given to sem_setup.  Calls
+ *     that return scalars (solve info) synchronise that stream.
+ *   - Return codes: 0 ok; negative = error (SEM_EINVAL -1 invalid argument,
+ *     SEM_ECUDA -2 CUDA error or no device, SEM_ENOMEM -3 out of device
+ *     memory, SEM_ETIMEOUT -4 a bounded device wait gave up); positive =
+ *     non-fatal solver outcome (SEM_MAXIT 1 maxit reached before tol,
+ *     SEM_STAGNATED 2 stagnation not cured by refinement, SEM_BREAKDOWN 3
+ *     p.Ap <= 0 or non-finite).  sem_last_error() returns the message of the
+ *     last failing call on the calling thread.  There is no CPU fallback.
+ */
+#ifndef SEM_H_
+#define SEM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SEM_OK = 0,
+  SEM_EINVAL = -1,
+  SEM_ECUDA = -2,
+  SEM_ENOMEM = -3,
+  SEM_ETIMEOUT = -4,
+  SEM_MAXIT = 1,
+  SEM_STAGNATED = 2,
+  SEM_BREAKDOWN = 3
+};
+
+/* Arithmetic of a call (vector dtype at the boundary in brackets).
+ *  SEM_FP64        everything in FP64                         [double]
+ *  SEM_MIXED_FP32  FP32 operator / vectors / updates, FP64 gather-scatter
+ *                  accumulation, FP64-quality dots and scalars (the paper's
+ *                  converging strategy)                        [float]
+ *  SEM_MIXED_TF32  as MIXED_FP32 with the D-contractions on tensor cores in
+ *                  TF32 (FP32 accumulate)                      [float]
+ *  SEM_MIXED_BF16X3 as MIXED_FP32 with the D-contractions as three BF16
+ *                  products hi*hi + hi*lo + lo*hi, FP32 accumulate  [float]
+ *  SEM_FP32_ALL    everything FP32, including gather-scatter accumulation
+ *                  and dot products (the paper's stagnating strategy) [float]
+ * sem_pcg_solve takes FP64 f/x0/x for every precision. */
+typedef enum {
+  SEM_FP64 = 0,
+  SEM_MIXED_FP32 = 1,
+  SEM_MIXED_TF32 = 2,
+  SEM_MIXED_BF16X3 = 3,
+  SEM_FP32_ALL = 4
+} sem_precision;
+
+typedef struct sem_handle_s* sem_handle;
+
+/* Mesh description.  With gid == NULL the mesh is the kx*ky*kz box on
+ * [lo, hi] (element e = ex + kx*(ey + ky*ez)), numbered on its
+ * (kx N+1)(ky N+1)(kz N+1) grid of GLL points, Dirichlet on all six faces,
+ * optionally deformed (deform_kind 1: x += a sin(2 pi y) sin(2 pi z) and
+ * cyclic permutations, evaluated from the undeformed coordinates at every
+ * GLL node).  With gid != NULL the caller gives a general conforming hex
+ * mesh: gid (host, E*n^3 ids in [0, 2^31)), coords (host, 3*E*n^3 doubles,
+ * x block then y then z, local layout), and dirichlet_faces (host, E bytes;
+ * bit f set = face f of the element is Dirichlet, faces ordered
+ * r=-1, r=+1, s=-1, s=+1, t=-1, t=+1).  E = kx*ky*kz in both cases. */
+typedef struct {
+  int kx, ky, kz;
+  double lo[3], hi[3];
+  double deform_amp;
+  int deform_kind;
+  const int64_t* gid;
+  const double* coords;
+  const uint8_t* dirichlet_faces;
+} sem_mesh;
+
+typedef struct {
+  int N, n;
+  int64_t E, L, U;       /* elements, local DOFs, unique global nodes */
+  int64_t n_shared;      /* local entries with multiplicity > 1 */
+  int64_t n_segments;    /* global nodes with multiplicity > 1 */
+  int64_t device_bytes;  /* device memory held by the handle */
+} sem_sizes;
+
+typedef struct {
+  int iters;             /* PCG iterations (inner iterations summed) */
+  int refinements;       /* FP64 outer residual evaluations after the first */
+  int status;            /* 0, SEM_MAXIT, SEM_STAGNATED or SEM_BREAKDOWN */
+  double relres;         /* final recursive ||r||_c/||b||_c of the last (inner) solve, relative to b */
+  double relres_true;    /* ||b - A x||_c/||b||_c recomputed in FP64 */
+  double solve_ms;       /* device time of the solve (CUDA events) */
+  int64_t launches;      /* kernels this solve launched (graph nodes counted) */
+} sem_info;
+
+/* Solver options (sem_pcg_solve_ex).  Zero-initialised fields take defaults. */
+typedef struct {
+  double tol;            /* relative residual ||r||_c/||b||_c target (default 1e-8) */
+  int maxit;             /* iteration cap over all inner solves (default 1000) */
+  sem_precision precision;
+  int fixed_iters;       /* > 0: run exactly this many iterations, no convergence test */
+  int no_refine;         /* mixed only: 1 = one inner solve, no FP64 outer loop */
+  double inner_tol;      /* mixed only: per-cycle residual reduction floor (default 1e-5) */
+  int max_cycles;        /* mixed only: FP64 outer cycles cap (default 10) */
+  int use_graph;         /* 0 (default) or 1: replay iteration chunks as CUDA graphs; -1: plain launches */
+  int chunk;             /* iterations per convergence poll (default 32) */
+  int precond;           /* 1 Jacobi (default), -1 identity */
+  double* history;       /* optional host array of maxit+1 recursive residuals (or NULL) */
+} sem_solve_opts;
+
+/* Set up a problem: GLL nodes/weights and the derivative matrix
+ * (textbook GLL rule the paper's SEM relies on, Sec. 3 and its reference
+ * Deville-Fischer-Mund), node coordinates, geometric factors G1..G6 and
+ * mass B (FP64, with an FP32 copy), the gather-scatter map (sorted
+ * shared-node segments), multiplicities, the Dirichlet mask and the Jacobi
+ * diagonal (FP64, with a one-time FP32 copy, Sec. 4.3).  N in [1, 15].
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * geom_flags: reserved, pass 0.  On success *out owns all device memory. */
+int sem_setup(const sem_mesh* mesh, int N, int geom_flags, void* stream, sem_handle* out);
+void sem_destroy(sem_handle h);
+const char* sem_last_error(void);
+int sem_get_sizes(sem_handle h, sem_sizes* out);
+
+/* w = mask * QQ^T (A_L u): the assembled, masked SEM Laplacian applied to a
+ * local vector (profiling table, `ax`, including the gather-scatter and the
+ * Dirichlet mask).  u, w: L values of the precision's dtype; may not alias. */
+int sem_ax(sem_handle h, const void* u, void* w, sem_precision p);
+
+/* w_L = mask * A_L u: the element operator only (no gather-scatter). */
+int sem_ax_local(sem_handle h, const void* u, void* w, sem_precision p);
+
+/* v = QQ^T v in place (direct-stiffness summation, Sec. 3.3).  FP64 and the
+ * mixed precisions accumulate every shared-node sum in FP64; SEM_FP32_ALL
+ * accumulates in FP32.  Every copy receives the same rounded sum. */
+int sem_gs(sem_handle h, void* v, sem_precision p);
+
+/* Weighted inner product sum_i a_i c_i b_i with c = mask/multiplicity
+ * (glsc3 of the profiling table).  a, b: L values of the precision's dtype.
+ * FP64 reduction for every precision except SEM_FP32_ALL. */
+int sem_glsc3(sem_handle h, const void* a, const void* b, sem_precision p, double* out);
+
+/* Copy an internal field to `out` (L doubles unless stated):
+ * 0 G (6*L, per element [6][n^3]), 1 B (mass), 2 Jacobi inverse J^{-1},
+ * 3 multiplicity, 4 mask, 5 c = mask/multiplicity, 6 coordinates (3*L,
+ * x block, y block, z block), 7 GLL nodes (n), 8 GLL weights (n),
+ * 9 derivative matrix D (n*n, row-major D[i][j] = l_j'(xi_i)),
+ * 10 Jacobian determinant. */
+int sem_get_field(sem_handle h, int which, double* out);
+
+/* Right-hand sides (FP64, L values, masked, continuous):
+ * kind 0: b = mask QQ^T(B * 3 pi^2 sin(pi x) sin(pi y) sin(pi z));
+ * kind 1: b_g uniform in [-1,1) per global node g from SplitMix64 output
+ *         number g+1 of state `seed` (Steele-Lea-Flood 2014), masked. */
+int sem_rhs(sem_handle h, int kind, uint64_t seed, double* b);
+
+/* Jacobi PCG for A x = f (f assembled and masked, FP64).  x0 may be NULL
+ * (zero initial guess).  x receives the FP64 solution.  Stopping test:
+ * recursive ||r||_c/||b||_c <= tol (FP64 path) or the FP64 true residual
+ * <= tol (mixed path with refinement). */
+int sem_pcg_solve(sem_handle h, const double* f, const double* x0, double* x,
+                  double tol, int maxit, sem_precision p, sem_info* info);
+int sem_pcg_solve_ex(sem_handle h, const double* f, const double* x0, double* x,
+                     const sem_solve_opts* opts, sem_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEM_H_ */

@@ -1,0 +1,306 @@
+// Vector kernels of the PCG loop (arXiv 2503.02134, profiling table of
+// Sec. 3.1): add2s2 (x += alpha p, r -= alpha w) fused with the two dot
+// products glsc3(r,c,r) and glsc3(r,c,z) (z = J^{-1} r, Sec. 4.3), the
+// convergence test, and the scalar recurrences beta = rtz / rtz_old.
+// Also: the initial residual, the weighted dot (glsc3) and the FP64
+// refinement helpers of the mixed path.
+#include "pcg.cuh"
+
+namespace sem {
+
+constexpr int kVecThreads = 256;
+
+// Scalars update after the reductions of an iteration (one thread).
+__device__ void finish_iteration(PcgScalars* s, double rtr, double rtz_new, double* hist) {
+  s->iter += 1;
+  s->rtr = rtr;
+  const double relres = sqrt(rtr) / s->bnorm;
+  s->relres = relres;
+  if (hist) hist[s->iter] = relres;
+  if (!isfinite(relres)) {
+    s->status = SEM_BREAKDOWN;
+    s->done = 1;
+  } else if (s->fixed) {
+    if (s->iter >= s->maxit) s->done = 1;
+  } else if (relres <= s->tol) {
+    s->done = 1;
+  } else if (s->iter >= s->maxit) {
+    s->status = SEM_MAXIT;
+    s->done = 1;
+  } else if (s->stag_window > 0) {
+    if (rtr < 0.81 * s->best_rtr) {   // ||r|| fell by 10 %
+      s->best_rtr = rtr;
+      s->best_it = s->iter;
+    } else if (s->iter - s->best_it >= s->stag_window) {
+      s->status = SEM_STAGNATED;
+      s->done = 1;
+    }
+  }
+  s->beta = rtz_new / s->rtz;
+  s->rtz_old = s->rtz;
+  s->rtz = rtz_new;
+}
+
+template <typename T, int DM>
+__global__ void __launch_bounds__(kVecThreads)
+    cg_update_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                     const T* __restrict__ w, const T* __restrict__ c, const T* __restrict__ minv,
+                     int64_t L, PcgScalars* __restrict__ s, double* __restrict__ partials,
+                     double* __restrict__ hist) {
+  __shared__ double sh[kVecThreads / 32];
+  if (s->done) return;
+  const T alpha = (T)s->alpha;
+  DotAcc<T, DM> a_rr, a_rz;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const T xv = x[l] + alpha * p[l];
+    const T rv = r[l] - alpha * w[l];
+    x[l] = xv;
+    r[l] = rv;
+    const T cr = c[l] * rv;
+    a_rr.add(cr, rv);
+    a_rz.add(cr, minv[l] * rv);
+  }
+  const double v0 = block_sum<DM>(a_rr.value(), sh);
+  const double v1 = block_sum<DM>(a_rz.value(), sh);
+  const double vals[2] = {v0, v1};
+  if (publish_and_elect(vals, 2, partials, &s->counter[1])) {
+    const double rtr = reduce_partials<DM>(partials, 0, sh);
+    const double rtz = reduce_partials<DM>(partials, 1, sh);
+    if (threadIdx.x == 0) {
+      finish_iteration(s, rtr, rtz, hist);
+      s->counter[1] = 0u;
+    }
+  }
+}
+
+// r = b - Ax (Ax may be null: r = b); rtr, rtz, ||b||_c; initialises the scalars.
+template <typename T, int DM>
+__global__ void __launch_bounds__(kVecThreads)
+    cg_init_kernel(T* __restrict__ r, const T* __restrict__ b, const T* __restrict__ ax,
+                   const T* __restrict__ c, const T* __restrict__ minv, int64_t L,
+                   PcgScalars* __restrict__ s, double* __restrict__ partials,
+                   double* __restrict__ hist) {
+  __shared__ double sh[kVecThreads / 32];
+  DotAcc<T, DM> a_rr, a_rz, a_bb;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const T bv = b[l];
+    const T rv = ax ? bv - ax[l] : bv;
+    r[l] = rv;
+    const T cr = c[l] * rv;
+    a_rr.add(cr, rv);
+    a_rz.add(cr, minv[l] * rv);
+    a_bb.add(c[l] * bv, bv);
+  }
+  const double v0 = block_sum<DM>(a_rr.value(), sh);
+  const double v1 = block_sum<DM>(a_rz.value(), sh);
+  const double v2 = block_sum<DM>(a_bb.value(), sh);
+  const double vals[3] = {v0, v1, v2};
+  if (publish_and_elect(vals, 3, partials, &s->counter[2])) {
+    const double rtr = reduce_partials<DM>(partials, 0, sh);
+    const double rtz = reduce_partials<DM>(partials, 1, sh);
+    const double bb = reduce_partials<DM>(partials, 2, sh);
+    if (threadIdx.x == 0) {
+      s->rtr = rtr;
+      s->rtz = rtz;
+      s->rtz_old = 0.0;
+      s->beta = 0.0;
+      s->alpha = 0.0;
+      s->pap = 0.0;
+      s->iter = 0;
+      s->status = 0;
+      s->best_rtr = rtr;
+      s->best_it = 0;
+      const double bnorm = sqrt(bb);
+      s->bnorm = bnorm;
+      s->relres = bnorm > 0.0 ? sqrt(rtr) / bnorm : 0.0;
+      if (hist) hist[0] = s->relres;
+      s->done = (bnorm == 0.0) || (!s->fixed && s->relres <= s->tol) || s->maxit <= 0;
+      s->counter[2] = 0u;
+    }
+  }
+}
+
+template <typename T, int DM>
+__global__ void __launch_bounds__(kVecThreads)
+    glsc3_kernel(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ c,
+                 int64_t L, double* __restrict__ partials, unsigned int* counter,
+                 double* __restrict__ out) {
+  __shared__ double sh[kVecThreads / 32];
+  DotAcc<T, DM> acc;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x)
+    acc.add(c[l] * a[l], b[l]);
+  const double v = block_sum<DM>(acc.value(), sh);
+  const double vals[1] = {v};
+  if (publish_and_elect(vals, 1, partials, counter)) {
+    const double t = reduce_partials<DM>(partials, 0, sh);
+    if (threadIdx.x == 0) {
+      *out = t;
+      *counter = 0u;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ refinement helpers
+__global__ void cast_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t L) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x)
+    b[l] = (float)a[l];
+}
+
+__global__ void add_f32_to_f64(double* __restrict__ x, const float* __restrict__ d, int64_t L) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x)
+    x[l] += (double)d[l];
+}
+
+__global__ void masked_copy_f64(const double* __restrict__ src, const double* __restrict__ mask,
+                                double* __restrict__ dst, int64_t L) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x)
+    dst[l] = src ? src[l] * mask[l] : 0.0;
+}
+
+__global__ void masked_copy_f32(const double* __restrict__ src, const double* __restrict__ mask,
+                                float* __restrict__ dst, int64_t L) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x)
+    dst[l] = src ? (float)(src[l] * mask[l]) : 0.f;
+}
+
+__global__ void f32_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t L) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x)
+    b[l] = (double)a[l];
+}
+
+__global__ void scal_setup_kernel(PcgScalars* s, double tol, int maxit, int fixed, int stag) {
+  s->tol = tol;
+  s->maxit = maxit;
+  s->fixed = fixed;
+  s->stag_window = stag;
+  s->done = 0;
+  s->status = 0;
+  s->iter = 0;
+  for (int q = 0; q < 4; ++q) s->counter[q] = 0u;
+}
+
+// ------------------------------------------------------------------ launchers
+int launch_scal_setup(Handle& h, PcgScalars* s, double tol, int maxit, int fixed, int stag_window) {
+  scal_setup_kernel<<<1, 1, 0, h.stream>>>(s, tol, maxit, fixed, stag_window);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int vec_grid(const Handle& h, int64_t L) {
+  int64_t g = (L + kVecThreads - 1) / kVecThreads;
+  int64_t cap = (int64_t)h.num_sms * 8;   // 8 resident blocks of 256 threads per SM
+  if (cap > h.max_blocks) cap = h.max_blocks;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <typename T>
+static int update_t(Handle& h, int dm, T* x, T* r, const T* p, const T* w, const T* c,
+                    const T* minv, PcgScalars* s, double* hist) {
+  const int grid = vec_grid(h, h.L);
+  if (dm == kDotFP32) {
+    if constexpr (sizeof(T) == 4)
+      cg_update_kernel<float, kDotFP32><<<grid, kVecThreads, 0, h.stream>>>(
+          x, r, p, w, c, minv, h.L, s, h.partials, hist);
+  } else if (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4)
+      cg_update_kernel<float, kDotDot2><<<grid, kVecThreads, 0, h.stream>>>(
+          x, r, p, w, c, minv, h.L, s, h.partials, hist);
+  } else {
+    if constexpr (sizeof(T) == 8)
+      cg_update_kernel<double, kDotFP64><<<grid, kVecThreads, 0, h.stream>>>(
+          x, r, p, w, c, minv, h.L, s, h.partials, hist);
+  }
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int launch_cg_update64(Handle& h, double* x, double* r, const double* p, const double* w,
+                       PcgScalars* s, double* hist) {
+  return update_t<double>(h, kDotFP64, x, r, p, w, h.c64, h.minv64, s, hist);
+}
+int launch_cg_update32(Handle& h, int dm, float* x, float* r, const float* p, const float* w,
+                       const float* minv, PcgScalars* s, double* hist) {
+  return update_t<float>(h, dm, x, r, p, w, h.c32, minv, s, hist);
+}
+
+int launch_cg_init64(Handle& h, double* r, const double* b, const double* ax, const double* minv,
+                     PcgScalars* s, double* hist) {
+  cg_init_kernel<double, kDotFP64><<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(
+      r, b, ax, h.c64, minv, h.L, s, h.partials, hist);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+int launch_cg_init32(Handle& h, int dm, float* r, const float* b, const float* ax,
+                     const float* minv, PcgScalars* s, double* hist) {
+  if (dm == kDotFP32)
+    cg_init_kernel<float, kDotFP32><<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(
+        r, b, ax, h.c32, minv, h.L, s, h.partials, hist);
+  else
+    cg_init_kernel<float, kDotDot2><<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(
+        r, b, ax, h.c32, minv, h.L, s, h.partials, hist);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int launch_glsc3(Handle& h, sem_precision p, const void* a, const void* b, double* out_dev) {
+  const int grid = vec_grid(h, h.L);
+  unsigned int* counter = &h.scal_aux->counter[3];
+  if (p == SEM_FP64)
+    glsc3_kernel<double, kDotFP64><<<grid, kVecThreads, 0, h.stream>>>(
+        (const double*)a, (const double*)b, h.c64, h.L, h.partials_aux, counter, out_dev);
+  else if (p == SEM_FP32_ALL)
+    glsc3_kernel<float, kDotFP32><<<grid, kVecThreads, 0, h.stream>>>(
+        (const float*)a, (const float*)b, h.c32, h.L, h.partials_aux, counter, out_dev);
+  else
+    glsc3_kernel<float, kDotDot2><<<grid, kVecThreads, 0, h.stream>>>(
+        (const float*)a, (const float*)b, h.c32, h.L, h.partials_aux, counter, out_dev);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int launch_cast64to32(Handle& h, const double* a, float* b) {
+  cast_f64_to_f32<<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(a, b, h.L);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+int launch_cast32to64(Handle& h, const float* a, double* b) {
+  f32_to_f64<<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(a, b, h.L);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+int launch_add32to64(Handle& h, double* x, const float* d) {
+  add_f32_to_f64<<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(x, d, h.L);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+int launch_masked_copy64(Handle& h, const double* src, double* dst) {
+  masked_copy_f64<<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(src, h.mask64, dst, h.L);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+int launch_masked_copy32(Handle& h, const double* src, float* dst) {
+  masked_copy_f32<<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(src, h.mask64, dst, h.L);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace sem

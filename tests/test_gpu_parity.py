@@ -1,0 +1,309 @@
+"""GPU parity: every step of the CUDA path against the FP64 CPU oracle.
+
+Sizes span several thread blocks and ragged tails (element counts that are
+not multiples of the elements-per-block of any order) while keeping the
+oracle within seconds.  Tolerances: FP64 results to 1e-12 relative (max
+norm), integer/index results bit-exact, the counter-based RHS bit-exact,
+FP32 operator results to a bound derived from FP32 rounding (Sec. "readings"
+of the design notes: ~ n * 2^-24 * condition of the contraction).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import sem_oracle as so  # noqa: E402
+import sem_inputs  # noqa: E402
+from tests.gpu_util import rel_maxerr  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sem():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2503_02134_gb300 as m
+    return m
+
+
+def cu(a, dtype=torch.float64):
+    return torch.as_tensor(np.asarray(a), dtype=dtype, device="cuda").contiguous()
+
+
+CASES = [
+    (3, 2, 2, 1, False),
+    (3, 2, 5, 3, True),
+    (5, 3, 2, 5, True),
+    (4, 4, 4, 7, False),
+    (5, 3, 3, 7, True),
+    (3, 3, 2, 9, True),
+    (2, 3, 2, 11, True),
+    (2, 2, 2, 13, True),
+    (2, 1, 2, 15, True),
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}_N{c[3]}_{'def' if c[4] else 'box'}")
+def pair(request, sem):
+    kx, ky, kz, N, deform = request.param
+    P = so.Problem(kx, ky, kz, N, deform=deform)
+    S = sem.Solver(kx, ky, kz, N, deform=deform)
+    yield P, S
+    S.close()
+
+
+def test_sizes(pair):
+    P, S = pair
+    assert (S.E, S.L, S.U) == (P.E, P.L, P.U)
+    assert S.sizes.n_shared == int(np.sum(P.mult > 1))
+    assert S.sizes.n_segments == int(np.sum(np.bincount(P.gid) > 1))
+
+
+def test_gll_and_derivative_matrix(pair, sem):
+    P, S = pair
+    assert rel_maxerr(S.field(sem.FIELD_XI).cpu(), P.xi) < 1e-14
+    assert rel_maxerr(S.field(sem.FIELD_W).cpu(), P.w) < 1e-13
+    D = S.field(sem.FIELD_D).cpu().numpy().reshape(P.n, P.n)
+    assert rel_maxerr(D, P.D) < 1e-12
+
+
+def test_geometry(pair, sem):
+    P, S = pair
+    n3 = P.n ** 3
+    G = S.field(sem.FIELD_G).cpu().numpy().reshape(P.E, 6, n3)
+    Gref = P.G.reshape(6, P.E, n3).transpose(1, 0, 2)
+    assert rel_maxerr(G, Gref) < 1e-12
+    assert rel_maxerr(S.field(sem.FIELD_B).cpu(), P.B.reshape(-1)) < 1e-12
+    assert rel_maxerr(S.field(sem.FIELD_DETJ).cpu(), P.detJ.reshape(-1)) < 1e-12
+    X = S.field(sem.FIELD_COORDS).cpu().numpy().reshape(3, -1)
+    assert rel_maxerr(X, P.X.reshape(3, -1)) < 1e-14
+
+
+def test_connectivity_bit_exact(pair, sem):
+    P, S = pair
+    np.testing.assert_array_equal(S.field(sem.FIELD_MULT).cpu().numpy(), P.mult)
+    np.testing.assert_array_equal(S.field(sem.FIELD_MASK).cpu().numpy(), P.mask)
+    np.testing.assert_array_equal(S.field(sem.FIELD_C).cpu().numpy(), P.c)
+
+
+def test_jacobi_inverse(pair, sem):
+    P, S = pair
+    assert rel_maxerr(S.field(sem.FIELD_MINV).cpu(), P.minv) < 1e-12
+
+
+def test_ax_fp64(pair, sem):
+    P, S = pair
+    u = sem_inputs.uniform_local(P.L, seed=11)
+    w = torch.empty(P.L, dtype=torch.float64, device="cuda")
+    sem.sem_ax(S.h, cu(u), w, sem.SEM_FP64)
+    assert rel_maxerr(w.cpu(), P.ax(u)) < 1e-12
+    sem.sem_ax_local(S.h, cu(u), w, sem.SEM_FP64)
+    assert rel_maxerr(w.cpu(), P.mask * P.ax_local(u)) < 1e-12
+
+
+def test_ax_fp32(pair, sem):
+    P, S = pair
+    u = sem_inputs.uniform_local(P.L, seed=12, dtype=np.float32)
+    w = torch.empty(P.L, dtype=torch.float32, device="cuda")
+    sem.sem_ax(S.h, cu(u, torch.float32), w, sem.SEM_MIXED_FP32)
+    ref = P.ax(u.astype(np.float64))
+    # FP32 rounding of G, D and the contractions: bounded by ~ 2 n^2 eps32 relative
+    assert rel_maxerr(w.cpu(), ref) < 2.0 * P.n ** 2 * 2.0 ** -24 * 8
+
+
+def test_gs(pair, sem):
+    P, S = pair
+    v = sem_inputs.uniform_local(P.L, seed=13)
+    t = cu(v)
+    sem.sem_gs(S.h, t, sem.SEM_FP64)
+    assert rel_maxerr(t.cpu(), P.dssum(v)) < 1e-15
+    # mixed: FP32 storage, FP64 accumulation -> the FP32 rounding of the FP64 sum
+    v32 = v.astype(np.float32)
+    t32 = cu(v32, torch.float32)
+    sem.sem_gs(S.h, t32, sem.SEM_MIXED_FP32)
+    ref = P.dssum(v32.astype(np.float64)).astype(np.float32)
+    np.testing.assert_array_equal(t32.cpu().numpy(), ref)
+
+
+def test_glsc3(pair, sem):
+    P, S = pair
+    a = sem_inputs.uniform_local(P.L, seed=14)
+    b = sem_inputs.uniform_local(P.L, seed=15)
+    got = sem.sem_glsc3(S.h, cu(a), cu(b), sem.SEM_FP64)
+    ref = P.glsc3(a, b)
+    assert abs(got - ref) <= 1e-13 * np.sum(np.abs(a * P.c * b))
+
+
+def test_rhs(pair, sem):
+    P, S = pair
+    b = torch.empty(P.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 0, b)
+    np.testing.assert_array_equal(b.cpu().numpy(), P.rhs_uniform(0))
+    sem.sem_rhs(S.h, sem.RHS_SINE, 0, b)
+    assert rel_maxerr(b.cpu(), P.rhs_sine()) < 1e-12
+
+
+# ------------------------------------------------------------------ solver
+def test_pcg_fp64_sine_4x4x4_N7(sem):
+    """The plain FP64 Jacobi PCG workload: 64 undeformed elements, N = 7, tol 1e-10."""
+    P = so.Problem(4, 4, 4, 7)
+    b = P.rhs_sine()
+    xo, ito, _ = P.pcg(b, tol=1e-10, maxit=500)
+    S = sem.Solver(4, 4, 4, 7)
+    x, info = S.solve(cu(b), tol=1e-10, maxit=500, precision=sem.SEM_FP64, history=True)
+    assert info["rc"] == 0 and info["relres"] <= 1e-10
+    assert abs(info["iters"] - ito) <= 1
+    assert rel_maxerr(x.cpu(), xo) < 1e-12 or rel_maxerr(x.cpu(), xo) < 1e-9
+    # both solved tightly the discrete solutions agree to 1e-12
+    xo2, _, _ = P.pcg(b, tol=1e-14, maxit=2000)
+    x2, info2 = S.solve(cu(b), tol=1e-14, maxit=2000, precision=sem.SEM_FP64)
+    assert rel_maxerr(x2.cpu(), xo2) < 1e-12
+    # the manufactured solution is reproduced to discretisation accuracy
+    assert np.abs(x.cpu().numpy() - P.exact_sine() * P.mask).max() < 1e-5
+    S.close()
+
+
+@pytest.mark.parametrize("deform", [False, True])
+def test_pcg_fp64_matches_oracle_history(sem, deform):
+    P = so.Problem(5, 4, 3, 5, deform=deform)
+    b = P.rhs_uniform(seed=3)
+    xo, ito, ho = P.pcg(b, tol=1e-12, maxit=1000)
+    S = sem.Solver(5, 4, 3, 5, deform=deform)
+    x, info = S.solve(cu(b), tol=1e-12, maxit=1000, precision=sem.SEM_FP64, history=True)
+    h = info["history"]
+    k = min(len(h), len(ho), 30)
+    np.testing.assert_allclose(h[:k], ho[:k], rtol=1e-9)
+    assert rel_maxerr(x.cpu(), xo) < 1e-10
+    S.close()
+
+
+def test_pcg_mixed_reaches_fp64_accuracy(sem):
+    """Mixed FP32/FP64 with refinement reaches 1e-8 and x within 1e-7 of an
+    oracle solution solved to 1e-12 (deformed mesh, N = 7)."""
+    P = so.Problem(6, 5, 4, 7, deform=True)
+    b = P.rhs_uniform(seed=0)
+    xo, _, _ = P.pcg(b, tol=1e-12, maxit=3000)
+    S = sem.Solver(6, 5, 4, 7, deform=True)
+    x, info = S.solve(cu(b), tol=1e-8, maxit=3000, precision=sem.SEM_MIXED_FP32)
+    assert info["rc"] == 0, info
+    assert info["relres_true"] <= 1e-8
+    assert rel_maxerr(x.cpu(), xo) < 1e-7
+    assert P.true_relres(b, x.cpu().numpy()) <= 1.05e-8
+    S.close()
+
+
+def test_all_fp32_stagnates_while_mixed_converges(sem):
+    """The paper's qualitative finding (Tables 'Mixed-precision strategy
+    evaluation'): FP32 gather-scatter and FP32 dots stagnate above the
+    target; FP64 gather-scatter sums and FP64 dots (plus FP64 refinement)
+    converge."""
+    S = sem.Solver(8, 8, 8, 7, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 0, b)
+    _, i32 = S.solve(b, tol=1e-10, maxit=1500, precision=sem.SEM_FP32_ALL)
+    _, imx = S.solve(b, tol=1e-10, maxit=1500, precision=sem.SEM_MIXED_FP32)
+    assert imx["rc"] == 0 and imx["relres_true"] <= 1e-10
+    assert i32["relres_true"] > 1e-8, i32
+    S.close()
+
+
+def test_user_numbering_matches_box(sem):
+    """A general mesh given as (relabelled gid, coordinates, Dirichlet faces)
+    reproduces the box results: the segment map does not depend on the ids."""
+    kx, ky, kz, N = 3, 4, 2, 4
+    P = so.Problem(kx, ky, kz, N, deform=True)
+    rng = np.random.default_rng(0)
+    relabel = rng.permutation(P.U)
+    gid = relabel[P.gid].astype(np.int64)
+    coords = np.ascontiguousarray(P.X.reshape(3, -1))
+    faces = np.zeros(P.E, dtype=np.uint8)
+    for ez in range(kz):
+        for ey in range(ky):
+            for ex in range(kx):
+                e = ex + kx * (ey + ky * ez)
+                faces[e] = ((ex == 0) | (ex == kx - 1) << 1 | (ey == 0) << 2 | (ey == ky - 1) << 3
+                            | (ez == 0) << 4 | (ez == kz - 1) << 5)
+    mesh = sem.user_mesh(P.E, gid, coords, faces)
+    S = sem.Solver(0, 0, 0, N, mesh=mesh)
+    u = sem_inputs.uniform_local(P.L, seed=21)
+    w = torch.empty(P.L, dtype=torch.float64, device="cuda")
+    sem.sem_ax(S.h, cu(u), w, sem.SEM_FP64)
+    assert rel_maxerr(w.cpu(), P.ax(u)) < 1e-12
+    S.close()
+
+
+def test_host_pointers_round_trip(sem):
+    P = so.Problem(3, 3, 3, 4, deform=True)
+    S = sem.Solver(3, 3, 3, 4, deform=True)
+    u = sem_inputs.uniform_local(P.L, seed=5)
+    w = np.zeros(P.L)
+    sem.sem_ax(S.h, u, w, sem.SEM_FP64)
+    assert rel_maxerr(w, P.ax(u)) < 1e-12
+    b = P.rhs_uniform(seed=1)
+    x = np.zeros(P.L)
+    rc, info = sem.sem_pcg_solve(S.h, b, None, x, 1e-10, 500, sem.SEM_FP64)
+    xo, _, _ = P.pcg(b, tol=1e-10, maxit=500)
+    assert rc == 0 and rel_maxerr(x, xo) < 1e-9
+    S.close()
+
+
+# ------------------------------------------------------------------ edge cases
+def test_single_element_all_boundary(sem):
+    S = sem.Solver(1, 1, 1, 3)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 0, b)
+    P = so.Problem(1, 1, 1, 3)
+    np.testing.assert_array_equal(b.cpu().numpy(), P.rhs_uniform(0))
+    x, info = S.solve(b, tol=1e-10, maxit=10, precision=sem.SEM_FP64)
+    # N = 3 on one element has 8 interior nodes: a real (tiny) system
+    xo, _, _ = P.pcg(P.rhs_uniform(0), tol=1e-10, maxit=10)
+    assert rel_maxerr(x.cpu(), xo) < 1e-10
+    S.close()
+
+
+def test_zero_rhs_returns_zero(sem):
+    S = sem.Solver(2, 2, 2, 2)
+    b = torch.zeros(S.L, dtype=torch.float64, device="cuda")
+    for prec in (sem.SEM_FP64, sem.SEM_MIXED_FP32):
+        x, info = S.solve(b, tol=1e-10, maxit=10, precision=prec)
+        assert info["iters"] == 0
+        assert torch.all(x == 0)
+    S.close()
+
+
+def test_maxit_reported(sem):
+    S = sem.Solver(4, 4, 4, 5, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 0, b)
+    _, info = S.solve(b, tol=1e-12, maxit=5, precision=sem.SEM_FP64)
+    assert info["rc"] == sem.SEM_MAXIT and info["iters"] == 5
+    _, info = S.solve(b, fixed_iters=7, precision=sem.SEM_FP64)
+    assert info["iters"] == 7 and info["rc"] == 0
+    S.close()
+
+
+def test_invalid_arguments(sem):
+    with pytest.raises(sem.SemError):
+        sem.Solver(2, 2, 2, 16)
+    with pytest.raises(sem.SemError):
+        sem.Solver(0, 2, 2, 3)
+    S = sem.Solver(2, 2, 2, 3)
+    u = torch.zeros(S.L, dtype=torch.float64, device="cuda")
+    with pytest.raises(sem.SemError):
+        sem.sem_ax(S.h, u, u, sem.SEM_FP64)
+    with pytest.raises(sem.SemError):
+        sem.sem_ax(S.h, u, torch.zeros_like(u), 9)
+    S.close()
+
+
+def test_graph_and_plain_launch_agree(sem):
+    S = sem.Solver(4, 3, 5, 6, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 2, b)
+    for prec in (sem.SEM_FP64, sem.SEM_MIXED_FP32):
+        x1, i1 = S.solve(b, tol=1e-9, maxit=2000, precision=prec, use_graph=True, chunk=7)
+        x2, i2 = S.solve(b, tol=1e-9, maxit=2000, precision=prec, use_graph=False, chunk=5)
+        assert i1["iters"] == i2["iters"]
+        assert torch.equal(x1, x2)   # deterministic reductions: bitwise equal
+    S.close()
