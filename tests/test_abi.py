@@ -18,10 +18,11 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2503_02134_gb300 import build
-    if not os.path.exists(build.LIB):
-        build.build()
-    return ctypes.CDLL(build.LIB)
+    import __graft_entry__
+    b = __graft_entry__._build_module()
+    if not os.path.exists(b.LIB):
+        b.build()
+    return ctypes.CDLL(b.LIB)
 
 
 def test_header_declares_the_boundary():
