@@ -184,11 +184,13 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bench_timed_steps")
         ev0.record(stream)
         for _ in range(args.steps):
             infos.append(step())
         ev1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         if world > 1:
             dist.barrier()
     ms_total = ev0.elapsed_time(ev1)

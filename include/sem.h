@@ -123,7 +123,7 @@ typedef struct {
   int fixed_iters;       /* > 0: run exactly this many iterations, no convergence test */
   int no_refine;         /* mixed only: 1 = one inner solve, no FP64 outer loop */
   double inner_tol;      /* mixed only: per-cycle residual reduction floor (default 1e-5) */
-  int max_cycles;        /* mixed only: FP64 outer cycles cap (default 10) */
+  int max_cycles;        /* mixed only: FP64 outer cycles cap (default 20) */
   int use_graph;         /* 0 (default) or 1: replay iteration chunks as CUDA graphs; -1: plain launches */
   int chunk;             /* iterations per convergence poll (default 32) */
   int precond;           /* 1 Jacobi (default), -1 identity */

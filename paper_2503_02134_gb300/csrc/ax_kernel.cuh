@@ -188,8 +188,8 @@ int ax_launch(Handle& h, const T* u, T* w, const T* G, const T* D, const AxProlo
   using S = AxShape<n>;
   auto kern = ax_kernel<n, T, PCG, DM>;
   const size_t smem = sizeof(T) * 3 * S::EPB * S::n3;
-  if (smem > 48 * 1024)
-    SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // opt in above the 48 KB default (static shared memory comes on top of this)
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::NT, smem));
   if (per_sm < 1) per_sm = 1;

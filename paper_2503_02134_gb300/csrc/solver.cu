@@ -34,6 +34,11 @@ int launch_ax_local(Handle& h, sem_precision p, const void* u, void* w, const Ax
 
 namespace {
 
+// A restart of the inner FP32 recursion is forced when its residual has not
+// fallen by 10 % for this many iterations (CG residuals plateau for tens of
+// iterations on hard problems, so the window is long).
+constexpr int kStagWindow = 200;
+
 enum GraphKind { kG64 = 0, kGMixed = 1, kGFP32 = 2 };
 
 // Enqueue `iters` PCG iterations (no host interaction).
@@ -155,7 +160,7 @@ int pcg_solve(Handle& h, const double* f, const double* x0, double* x, const sem
   const int chunk = o.chunk > 0 ? o.chunk : 32;
   const sem_precision prec = o.precision;
   const double inner_floor = o.inner_tol > 0 ? o.inner_tol : 1e-5;
-  const int max_cycles = o.max_cycles > 0 ? o.max_cycles : 10;
+  const int max_cycles = o.max_cycles > 0 ? o.max_cycles : 20;
   const bool identity = o.precond < 0;
   int rc;
   const int cap_it = fixed ? fixed : maxit;
@@ -249,7 +254,8 @@ int pcg_solve(Handle& h, const double* f, const double* x0, double* x, const sem
       double inner_tol = tol;
       int inner_max = fixed ? fixed : maxit - total_it;
       if (refine) inner_tol = std::max(inner_floor, 0.5 * tol / std::max(relres_true, 1e-300));
-      if ((rc = launch_scal_setup(h, h.scal, inner_tol, inner_max, fixed ? 1 : 0, refine ? 20 : 0))) {
+      if ((rc = launch_scal_setup(h, h.scal, inner_tol, inner_max, fixed ? 1 : 0,
+                                   refine ? kStagWindow : 0))) {
         restore();
         return rc;
       }

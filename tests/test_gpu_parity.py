@@ -75,7 +75,11 @@ def test_geometry(pair, sem):
     Gref = P.G.reshape(6, P.E, n3).transpose(1, 0, 2)
     assert rel_maxerr(G, Gref) < 1e-12
     assert rel_maxerr(S.field(sem.FIELD_B).cpu(), P.B.reshape(-1)) < 1e-12
-    assert rel_maxerr(S.field(sem.FIELD_DETJ).cpu(), P.detJ.reshape(-1)) < 1e-12
+    # det J is a cubic in the Jacobian entries dx/dr = sum_l D_il x_l, whose
+    # rounding error grows with the row sums of |D| (~ N^2): two independent
+    # FP64 evaluations differ by up to ~ eps N^3 relative.
+    tol_det = max(1e-12, 2e-15 * P.N ** 3)
+    assert rel_maxerr(S.field(sem.FIELD_DETJ).cpu(), P.detJ.reshape(-1)) < tol_det
     X = S.field(sem.FIELD_COORDS).cpu().numpy().reshape(3, -1)
     assert rel_maxerr(X, P.X.reshape(3, -1)) < 1e-14
 
@@ -154,7 +158,7 @@ def test_pcg_fp64_sine_4x4x4_N7(sem):
     x, info = S.solve(cu(b), tol=1e-10, maxit=500, precision=sem.SEM_FP64, history=True)
     assert info["rc"] == 0 and info["relres"] <= 1e-10
     assert abs(info["iters"] - ito) <= 1
-    assert rel_maxerr(x.cpu(), xo) < 1e-12 or rel_maxerr(x.cpu(), xo) < 1e-9
+    assert rel_maxerr(x.cpu(), xo) < 1e-12
     # both solved tightly the discrete solutions agree to 1e-12
     xo2, _, _ = P.pcg(b, tol=1e-14, maxit=2000)
     x2, info2 = S.solve(cu(b), tol=1e-14, maxit=2000, precision=sem.SEM_FP64)
