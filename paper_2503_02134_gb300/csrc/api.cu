@@ -48,7 +48,7 @@ static void free_handle(Handle* h) {
     if (h->graph_exec[q]) cudaGraphExecDestroy(h->graph_exec[q]);
   void* ptrs[] = {h->xi,     h->wq,      h->D64,    h->D32,      h->coords,   h->G64,
                   h->G32,    h->B64,     h->detJ,   h->gid,      h->bfaces,   h->mask64,
-                  h->mult64, h->c64,     h->c32,    h->seg_off,  h->perm,     h->minv64,
+                  h->mult64, h->c64,     h->c32,    h->seg_off,  h->perm, h->gs_slots, h->gs_chunks,     h->minv64,
                   h->minv32, h->x64,     h->r64,    h->p64,      h->w64,      h->x32,
                   h->r32,    h->p32,     h->w32,    h->b32,      h->partials, h->partials_aux,
                   h->scal,   h->scal_aux, h->dot_out, h->hist_dev, h->stage_a, h->stage_b,
@@ -213,6 +213,7 @@ int sem_setup(const sem_mesh* mesh, int N, int geom_flags, void* stream, sem_han
       (ce = cudaMemsetAsync(h->scal_aux, 0, sizeof(PcgScalars), h->stream)) != cudaSuccess)
     return fail(cuda_fail(ce, "cudaMemset"));
 
+  h->dev_err = &h->scal->err;
   if ((rc = launch_gll(*h))) return fail(rc);
   double* ucoords = nullptr;
   if (mesh->gid) {

@@ -1,11 +1,23 @@
 // FP32 instantiations of the element operator (CUDA cores), plain and PCG-fused
 // with the compensated (Dot2) or the plain FP32 pap reduction.
-#include "ax_kernel.cuh"
+#include "ax_tma.cuh"
 
 namespace sem {
 
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 template <int n>
 static int run32(Handle& h, const float* u, float* w, const AxPrologue* pro, int dm) {
+  // bulk-copy staged kernel: even n (16-byte element blocks) up to n = 10
+  if constexpr (n % 2 == 0 && n <= 10) {
+    const bool ok = h.use_tma && aligned16(u) && aligned16(w) &&
+                    (!pro || (aligned16(pro->r) && aligned16(pro->minv)));
+    if (ok) {
+      if (!pro) return ax_tma_launch<n, false, kDotDot2>(h, u, w, nullptr);
+      if (dm == kDotFP32) return ax_tma_launch<n, true, kDotFP32>(h, u, w, pro);
+      return ax_tma_launch<n, true, kDotDot2>(h, u, w, pro);
+    }
+  }
   if (!pro) return ax_launch<n, float, false, kDotDot2>(h, u, w, h.G32, h.D32, nullptr);
   if (dm == kDotFP32) return ax_launch<n, float, true, kDotFP32>(h, u, w, h.G32, h.D32, pro);
   return ax_launch<n, float, true, kDotDot2>(h, u, w, h.G32, h.D32, pro);

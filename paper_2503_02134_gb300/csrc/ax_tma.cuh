@@ -1,0 +1,251 @@
+// FP32 element operator with bulk-copy (TMA) staging.
+//
+// Same arithmetic as ax_kernel (ax_kernel.cuh: local_grad3, geometric
+// factors, local_grad3_t of the paper's `ax`, Sec. 3.1) but the streamed
+// inputs of a group of EPB consecutive elements -- u (or r, J^{-1} and p in
+// PCG mode) and G1..G6, all contiguous in the element-major layout -- are
+// brought into shared memory by 1-D cp.async.bulk copies issued by one
+// thread, two stages deep, while the block computes the previous group.
+// The copies complete on an mbarrier (transaction bytes), so the math warps
+// never issue a global load: the memory pipe is kept busy by the copy engine
+// instead of by occupancy.  Requires 16-byte aligned element blocks, i.e. an
+// even number of GLL points per direction (n^3 * 4 bytes % 16 == 0).
+#pragma once
+
+#include "ax_kernel.cuh"
+#include "tma.cuh"
+
+namespace sem {
+
+template <int n>
+struct TmaShape {
+  static constexpr int n2 = n * n;
+  static constexpr int n3 = n * n * n;
+  static constexpr int EPB = (128 / n2) > 0 ? (128 / n2) : 1;   // ~128 threads per block
+  static constexpr int NT = ((n2 * EPB + 31) / 32) * 32;
+  static constexpr uint32_t VEC = EPB * n3 * 4;                 // bytes of one vector per stage
+};
+
+template <int n, bool PCG>
+constexpr size_t tma_smem_bytes() {
+  using S = TmaShape<n>;
+  constexpr int NV = PCG ? 3 : 1;
+  return 2 * (size_t)(NV + 6) * S::VEC + 2 * (size_t)S::VEC + 2 * sizeof(uint64_t);
+}
+
+template <int n, bool PCG, int DM>
+__global__ void __launch_bounds__(TmaShape<n>::NT)
+    ax_tma_kernel(const float* __restrict__ uin, float* __restrict__ wout,
+                  const float* __restrict__ G, const float* __restrict__ Dg,
+                  const uint8_t* __restrict__ faces, int64_t E, const float* __restrict__ rr,
+                  const float* __restrict__ minv, float* pp, PcgScalars* __restrict__ scal,
+                  double* __restrict__ partials, int* __restrict__ err) {
+  using S = TmaShape<n>;
+  constexpr int n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  constexpr int NV = PCG ? 3 : 1;
+  constexpr int SV = EPB * n3;                 // floats of one vector per stage
+  constexpr int STAGE = (NV + 6) * SV;         // floats per stage
+  extern __shared__ __align__(128) float smem_f[];
+  float* const stage0 = smem_f;
+  float* const sr = smem_f + 2 * STAGE;
+  float* const ss = sr + SV;
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(ss + SV);
+  __shared__ float sD[n][n + 1];
+  __shared__ double sh_red[S::NT / 32];
+
+  if (PCG && scal->done) return;
+  const float beta = PCG ? (float)scal->beta : 0.f;
+
+  const int tid = threadIdx.x;
+  const int le = tid / n2;
+  const int ij = tid - le * n2;
+  const int i = ij % n, j = ij / n;
+  const bool lane_ok = le < EPB;
+  const int ir = lane_ok ? i : 0, jr = lane_ok ? j : 0, ler = lane_ok ? le : 0;
+  const int64_t ngroups = (E + EPB - 1) / EPB;
+
+  auto issue = [&](int st, int64_t g) {
+    const int64_t e0 = g * EPB;
+    const int64_t cnt = E - e0 < EPB ? E - e0 : EPB;
+    const uint32_t vb = (uint32_t)(cnt * n3 * 4);
+    float* dst = stage0 + st * STAGE;
+    mbar_arrive_expect_tx(&bar[st], (NV + 6) * vb);
+    if (PCG) {
+      bulk_load(dst, rr + e0 * n3, vb, &bar[st]);
+      bulk_load(dst + SV, minv + e0 * n3, vb, &bar[st]);
+      bulk_load(dst + 2 * SV, pp + e0 * n3, vb, &bar[st]);
+    } else {
+      bulk_load(dst, uin + e0 * n3, vb, &bar[st]);
+    }
+    bulk_load(dst + NV * SV, G + e0 * 6 * n3, 6 * vb, &bar[st]);
+  };
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  for (int q = tid; q < n2; q += blockDim.x) sD[q / n][q % n] = Dg[q];
+  __syncthreads();
+  if (tid == 0) {
+    if ((int64_t)blockIdx.x < ngroups) issue(0, blockIdx.x);
+    if ((int64_t)blockIdx.x + gridDim.x < ngroups) issue(1, (int64_t)blockIdx.x + gridDim.x);
+  }
+  float Di[n], Dj[n], DiT[n], DjT[n];
+#pragma unroll
+  for (int l = 0; l < n; ++l) {
+    Di[l] = sD[ir][l];
+    Dj[l] = sD[jr][l];
+    DiT[l] = sD[l][ir];
+    DjT[l] = sD[l][jr];
+  }
+
+  DotAcc<float, DM> acc;
+  bool aborted = false;
+  int t = 0;
+  int waited[2] = {0, 0};   // completed phases per stage
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, ++t) {
+    const int st = t & 1;
+    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)(waited[st] & 1));
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    ++waited[st];
+    float* const sb = stage0 + st * STAGE;
+    float* const su = PCG ? sb + 2 * SV : sb;   // p (formed in place) or u
+    const float* const Gs = sb + NV * SV + ler * 6 * n3 + ij;
+    float* const su_e = su + ler * n3;
+    float* const sr_e = sr + ler * n3;
+    float* const ss_e = ss + ler * n3;
+    const int64_t e = g * EPB + le;
+    const bool act = lane_ok && e < E;
+
+    float ureg[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      const int si = k * n2 + ij;
+      float v;
+      if (PCG) {
+        v = sb[SV + ler * n3 + si] * sb[ler * n3 + si] + beta * su_e[si];
+        if (lane_ok) su_e[si] = v;
+        if (act) pp[e * n3 + si] = v;
+      } else {
+        v = su_e[si];
+      }
+      ureg[k] = v;
+    }
+    if (PCG) __syncthreads();
+
+    float wreg[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) wreg[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      float ur = 0.f, us = 0.f, ut = 0.f;
+#pragma unroll
+      for (int l = 0; l < n; ++l) {
+        ur += Di[l] * su_e[k * n2 + jr * n + l];
+        us += Dj[l] * su_e[k * n2 + l * n + ir];
+        ut += sD[k][l] * ureg[l];
+      }
+      const float g0 = Gs[0 * n3 + k * n2], g1 = Gs[1 * n3 + k * n2], g2 = Gs[2 * n3 + k * n2];
+      const float g3 = Gs[3 * n3 + k * n2], g4 = Gs[4 * n3 + k * n2], g5 = Gs[5 * n3 + k * n2];
+      const float vr = g0 * ur + g3 * us + g4 * ut;
+      const float vs = g3 * ur + g1 * us + g5 * ut;
+      const float vt = g4 * ur + g5 * us + g2 * ut;
+      if (lane_ok) {
+        sr_e[k * n2 + ij] = vr;
+        ss_e[k * n2 + ij] = vs;
+      }
+#pragma unroll
+      for (int kk = 0; kk < n; ++kk) wreg[kk] += sD[k][kk] * vt;
+    }
+    __syncthreads();
+
+    const uint8_t f = act ? faces[e] : uint8_t(0);
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      float wv = wreg[k];
+#pragma unroll
+      for (int l = 0; l < n; ++l) {
+        wv += DiT[l] * sr_e[k * n2 + jr * n + l];
+        wv += DjT[l] * ss_e[k * n2 + l * n + ir];
+      }
+      if (on_dirichlet(f, i, j, k, n - 1)) wv = 0.f;
+      if (act) {
+        wout[e * n3 + k * n2 + ij] = wv;
+        if (PCG) acc.add(ureg[k], wv);
+      }
+    }
+    __syncthreads();   // stage st and sr/ss are free again
+    if (tid == 0) {
+      const int64_t gn = g + 2 * (int64_t)gridDim.x;
+      if (gn < ngroups) {
+        fence_proxy_async_smem();
+        issue(st, gn);
+      }
+    }
+  }
+
+  if (aborted) {
+    // A bulk copy never completed: report it, give the copies this block
+    // still has in flight a bounded time to land (each stage has at most one
+    // outstanding phase), and leave without publishing a partial sum.
+    if (tid == 0) {
+      atomicExch(err, 1);
+      const int64_t g_abort = blockIdx.x + (int64_t)t * gridDim.x;
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int64_t g_out = g_abort + (int64_t)((s2 - (t & 1) + 2) & 1) * gridDim.x;
+        if (g_out < ngroups) mbar_wait_bounded(&bar[s2], (uint32_t)(waited[s2] & 1));
+      }
+    }
+    return;
+  }
+
+  if (PCG) {
+    const double part = block_sum<DM>(acc.value(), sh_red);
+    const double vals[1] = {part};
+    if (publish_and_elect(vals, 1, partials, &scal->counter[0])) {
+      const double pap = reduce_partials<DM>(partials, 0, sh_red);
+      if (threadIdx.x == 0) {
+        scal->pap = pap;
+        if (!(pap > 0.0) || !isfinite(pap)) {
+          scal->status = SEM_BREAKDOWN;
+          scal->done = 1;
+          scal->alpha = 0.0;
+        } else {
+          scal->alpha = scal->rtz / pap;
+        }
+        scal->counter[0] = 0u;
+      }
+    }
+  }
+}
+
+template <int n, bool PCG, int DM>
+int ax_tma_launch(Handle& h, const float* u, float* w, const AxPrologue* pro) {
+  using S = TmaShape<n>;
+  auto kern = ax_tma_kernel<n, PCG, DM>;
+  constexpr size_t smem = tma_smem_bytes<n, PCG>();
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::NT, smem));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t groups = (h.E + S::EPB - 1) / S::EPB;
+  int64_t cap = (int64_t)h.num_sms * per_sm;
+  if (cap > h.max_blocks) cap = h.max_blocks;
+  const int grid = (int)(groups < cap ? groups : cap);
+  const float* r = PCG ? (const float*)pro->r : nullptr;
+  const float* minv = PCG ? (const float*)pro->minv : nullptr;
+  PcgScalars* scal = PCG ? const_cast<PcgScalars*>(pro->scal) : nullptr;
+  double* partials = PCG ? pro->pap_partials : nullptr;
+  float* pp = PCG ? const_cast<float*>(u) : nullptr;
+  kern<<<grid, S::NT, smem, h.stream>>>(u, w, h.G32, h.D32, h.bfaces, h.E, r, minv, pp, scal,
+                                        partials, h.dev_err);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace sem

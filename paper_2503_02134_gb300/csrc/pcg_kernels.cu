@@ -177,6 +177,7 @@ __global__ void f32_to_f64(const float* __restrict__ a, double* __restrict__ b, 
 }
 
 __global__ void scal_setup_kernel(PcgScalars* s, double tol, int maxit, int fixed, int stag) {
+  // s->err is left alone: it reports a bounded wait that gave up
   s->tol = tol;
   s->maxit = maxit;
   s->fixed = fixed;

@@ -32,7 +32,7 @@ struct PcgScalars {
   int done;          // set once converged, capped, stagnated or broken down
   int status;        // 0 / SEM_MAXIT / SEM_STAGNATED / SEM_BREAKDOWN
   int stag_window;   // iterations without a 10% drop of ||r|| that mean stagnation (0 = off)
-  int pad;
+  int err;           // set by a kernel whose bounded wait gave up
   unsigned int counter[4];   // last-block election counters (reset by the last block)
   double hist_dummy;
 };
@@ -71,6 +71,11 @@ struct Handle {
   int* seg_off = nullptr;      // n_segments + 1
   int* perm = nullptr;         // n_shared local indices grouped by global node
   int64_t n_segments = 0, n_shared = 0;
+  int* gs_slots = nullptr;     // bucketed, transposed copy indices (-1 = padding)
+  int2* gs_chunks = nullptr;   // per 32-segment chunk: {copies m, first slot}
+  int64_t n_chunks = 0, n_slots = 0;
+  bool use_tma = true;         // FP32 operator: bulk-copy staged kernel where it applies
+  int gs_acc = 2;              // mixed-path accumulation: 2 TwoSum (default), 0 FP64, 1 FP32
 
   // Jacobi
   double* minv64 = nullptr;
@@ -95,6 +100,7 @@ struct Handle {
   void* stage_c = nullptr;
 
   int64_t device_bytes = 0;
+  int* dev_err = nullptr;        // &scal->err: error word of the bounded device waits
   int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
 
   // graphs cache: one per (precision, chunk) combination
@@ -141,6 +147,8 @@ int launch_ax_local(Handle& h, sem_precision p, const void* u, void* w, const Ax
 
 // gs_kernels.cu
 int launch_gs(Handle& h, sem_precision p, void* v);
+int launch_gs_acc(Handle& h, sem_precision p, void* v, int acc);
+int build_gs_buckets(Handle& h);
 
 // pcg_kernels.cu
 int launch_glsc3(Handle& h, sem_precision p, const void* a, const void* b, double* out_dev);

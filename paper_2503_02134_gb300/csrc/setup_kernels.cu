@@ -382,7 +382,7 @@ __global__ void scan_tiles(const uint64_t* in, uint64_t* out, int64_t n, const u
 }
 
 // in/out may alias.  grand_total is a device pointer.
-static int exclusive_scan_u64(Handle& h, const uint64_t* in, uint64_t* out, int64_t n,
+int exclusive_scan_u64(Handle& h, const uint64_t* in, uint64_t* out, int64_t n,
                               uint64_t* grand_total) {
   int64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles < 1) tiles = 1;
@@ -505,7 +505,7 @@ int launch_gs_map(Handle& h) {
   SEM_CUDA(cudaFreeAsync(packed, h.stream));
   SEM_CUDA(cudaFreeAsync(tot_d, h.stream));
   SEM_CUDA(cudaStreamSynchronize(h.stream));
-  return 0;
+  return build_gs_buckets(h);
 }
 
 // ------------------------------------------------------------------ Jacobi

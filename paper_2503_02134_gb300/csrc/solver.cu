@@ -111,6 +111,10 @@ int iterate(Handle& h, GraphKind kind, int chunk, bool use_graph, PcgScalars* fi
     int rc = run_chunk(h, kind, chunk, use_graph);
     if (rc) return rc;
     if ((rc = read_scalars(h, h.scal, fin))) return rc;
+    if (fin->err) {
+      set_error("pcg: a bounded device wait gave up (bulk copy did not complete)");
+      return SEM_ETIMEOUT;
+    }
     if (fin->done) return 0;
   }
 }

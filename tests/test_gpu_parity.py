@@ -34,7 +34,9 @@ def cu(a, dtype=torch.float64):
 CASES = [
     (3, 2, 2, 1, False),
     (3, 2, 5, 3, True),
+    (3, 2, 3, 4, True),
     (5, 3, 2, 5, True),
+    (2, 3, 3, 6, True),
     (4, 4, 4, 7, False),
     (5, 3, 3, 7, True),
     (3, 3, 2, 9, True),
@@ -127,7 +129,17 @@ def test_gs(pair, sem):
     t32 = cu(v32, torch.float32)
     sem.sem_gs(S.h, t32, sem.SEM_MIXED_FP32)
     ref = P.dssum(v32.astype(np.float64)).astype(np.float32)
-    np.testing.assert_array_equal(t32.cpu().numpy(), ref)
+    got = t32.cpu().numpy()
+    # error-free (TwoSum) accumulation rounded once: equal to the FP64 sum
+    # rounded to FP32 up to one unit in the last place in rare tie cases
+    ulp = np.spacing(np.abs(ref).astype(np.float32))
+    assert np.all(np.abs(got - ref) <= ulp)
+    assert np.mean(got != ref) < 1e-3
+    # copies of one global node stay bit-identical
+    g = P.gid
+    first = np.full(P.U, np.nan, dtype=np.float32)
+    first[g[::-1]] = got[::-1]
+    np.testing.assert_array_equal(got, first[g])
 
 
 def test_glsc3(pair, sem):
