@@ -290,6 +290,10 @@ def main():
             "ax_gdofs_fp32_with_gs": L / (ax32_full_ms * 1e-3) / 1e9,
             "ax_gdofs_fp64": L / (ax64_ms * 1e-3) / 1e9,
             "roofline": roofline, "clocks": clocks.summary(), "e2e": e2e,
+            "autotune": {k: sem.sem_get_option(S.h, k) for k in
+                         ("ax_variant", "ax_variant_pcg", "ax_tune_ms_plain_0", "ax_tune_ms_plain_1",
+                          "ax_tune_ms_plain_2", "ax_tune_ms_pcg_0", "ax_tune_ms_pcg_1",
+                          "ax_tune_ms_pcg_2")},
             "gpu_launches": launches,
         }
         if not args.no_cpu and world >= 1:

@@ -184,6 +184,20 @@ int sem_pcg_solve(sem_handle h, const double* f, const double* x0, double* x,
 int sem_pcg_solve_ex(sem_handle h, const double* f, const double* x0, double* x,
                      const sem_solve_opts* opts, sem_info* info);
 
+/* Tuning knobs and diagnostics of the implementation (the paper has no
+ * counterpart; they never change results beyond rounding).  Keys:
+ *   "ax_variant", "ax_variant_pcg"  launch variant (0..2) of the bulk-copy
+ *                                   staged FP32 operator, plain / PCG mode;
+ *                                   sem_setup's autotuner picks the fastest
+ *   "use_tma"     1 (default) staged FP32 operator where it applies, 0 off
+ *   "gs_acc"      mixed-path gather-scatter accumulation: 2 error-free
+ *                 FP32 TwoSum (default), 0 FP64, 1 plain FP32
+ * sem_get_option also reads "ax_tune_ms_plain_<v>", "ax_tune_ms_pcg_<v>"
+ * (autotuner timings, ms) and "launches" (kernels enqueued so far).
+ * Unknown keys and out-of-range values return SEM_EINVAL. */
+int sem_set_option(sem_handle h, const char* key, int64_t value);
+int sem_get_option(sem_handle h, const char* key, double* value);
+
 #ifdef __cplusplus
 }
 #endif

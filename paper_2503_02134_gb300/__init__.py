@@ -67,7 +67,7 @@ class sem_solve_opts(ctypes.Structure):
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libsem.so not built ({LIB_PATH}); run "
-                          "`python -m paper_2503_02134_gb300.build` (needs nvcc)")
+                          "`python paper_2503_02134_gb300/build.py` (needs nvcc)")
     lib = ctypes.CDLL(LIB_PATH)
     vp, i, d, h = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
     sig = {
@@ -84,6 +84,8 @@ def _load():
         "sem_pcg_solve": (i, [h, vp, vp, vp, d, i, i, ctypes.POINTER(sem_info)]),
         "sem_pcg_solve_ex": (i, [h, vp, vp, vp, ctypes.POINTER(sem_solve_opts),
                                  ctypes.POINTER(sem_info)]),
+        "sem_set_option": (i, [h, ctypes.c_char_p, ctypes.c_int64]),
+        "sem_get_option": (i, [h, ctypes.c_char_p, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -95,7 +97,7 @@ def _load():
 _lib = _load()
 EXPORTED = ("sem_setup", "sem_destroy", "sem_last_error", "sem_get_sizes", "sem_ax",
             "sem_ax_local", "sem_gs", "sem_glsc3", "sem_get_field", "sem_rhs", "sem_pcg_solve",
-            "sem_pcg_solve_ex")
+            "sem_pcg_solve_ex", "sem_set_option", "sem_get_option")
 
 
 class SemError(RuntimeError):
@@ -185,6 +187,16 @@ def sem_pcg_solve_ex(h, f, x0, x, opts: sem_solve_opts):
     rc = _check(_lib.sem_pcg_solve_ex(h, _ptr(f), _ptr(x0), _ptr(x), ctypes.byref(opts),
                                       ctypes.byref(info)), "sem_pcg_solve_ex")
     return rc, info
+
+
+def sem_set_option(h, key: str, value: int):
+    return _check(_lib.sem_set_option(h, key.encode(), int(value)), "sem_set_option")
+
+
+def sem_get_option(h, key: str) -> float:
+    out = ctypes.c_double()
+    _check(_lib.sem_get_option(h, key.encode(), ctypes.byref(out)), "sem_get_option")
+    return out.value
 
 
 # ----------------------------------------------------------------- convenience

@@ -1,7 +1,8 @@
 """Build libsem.so in-tree with nvcc for sm_103a (GB300).
 
 Every translation unit is compiled in parallel, then linked into one shared
-library next to this file.  Usage: ``python -m paper_2503_02134_gb300.build``.
+library next to this file.  Usage: ``python paper_2503_02134_gb300/build.py`` (run as a
+script: importing the package loads the library it builds).
 """
 from __future__ import annotations
 

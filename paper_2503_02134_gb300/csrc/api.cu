@@ -48,7 +48,7 @@ static void free_handle(Handle* h) {
     if (h->graph_exec[q]) cudaGraphExecDestroy(h->graph_exec[q]);
   void* ptrs[] = {h->xi,     h->wq,      h->D64,    h->D32,      h->coords,   h->G64,
                   h->G32,    h->B64,     h->detJ,   h->gid,      h->bfaces,   h->mask64,
-                  h->mult64, h->c64,     h->c32,    h->seg_off,  h->perm, h->gs_slots, h->gs_chunks,     h->minv64,
+                  h->mult64, h->c64,     h->c32, h->cw8,    h->seg_off,  h->perm, h->gs_slots, h->gs_chunks,     h->minv64,
                   h->minv32, h->x64,     h->r64,    h->p64,      h->w64,      h->x32,
                   h->r32,    h->p32,     h->w32,    h->b32,      h->partials, h->partials_aux,
                   h->scal,   h->scal_aux, h->dot_out, h->hist_dev, h->stage_a, h->stage_b,
@@ -196,7 +196,7 @@ int sem_setup(const sem_mesh* mesh, int N, int geom_flags, void* stream, sem_han
       (rc = alloc_t(*h, &h->detJ, L)) || (rc = alloc_t(*h, &h->gid, L)) ||
       (rc = alloc_t(*h, &h->bfaces, (size_t)E)) || (rc = alloc_t(*h, &h->mask64, L)) ||
       (rc = alloc_t(*h, &h->mult64, L)) || (rc = alloc_t(*h, &h->c64, L)) ||
-      (rc = alloc_t(*h, &h->c32, L)) || (rc = alloc_t(*h, &h->minv64, L)) ||
+      (rc = alloc_t(*h, &h->c32, L)) || (rc = alloc_t(*h, &h->cw8, L)) || (rc = alloc_t(*h, &h->minv64, L)) ||
       (rc = alloc_t(*h, &h->minv32, L)) || (rc = alloc_t(*h, &h->x64, L)) ||
       (rc = alloc_t(*h, &h->r64, L)) || (rc = alloc_t(*h, &h->p64, L)) ||
       (rc = alloc_t(*h, &h->w64, L)) || (rc = alloc_t(*h, &h->x32, L)) ||
@@ -242,6 +242,7 @@ int sem_setup(const sem_mesh* mesh, int N, int geom_flags, void* stream, sem_han
   if (rc) return fail(rc);
   if ((rc = launch_gs_map(*h))) return fail(rc);
   if ((rc = launch_jacobi(*h))) return fail(rc);
+  if ((rc = autotune_ax32(*h))) return fail(rc);
   if ((ce = cudaStreamSynchronize(h->stream)) != cudaSuccess)
     return fail(cuda_fail(ce, "sem_setup"));
   *out = h;
@@ -425,6 +426,55 @@ int sem_pcg_solve(sem_handle h, const double* f, const double* x0, double* x, do
   o.precision = p;
   o.use_graph = 1;
   return sem_pcg_solve_ex(h, f, x0, x, &o, info);
+}
+
+static void drop_graphs(Handle& h) {
+  for (int q = 0; q < 8; ++q) {
+    if (h.graph_exec[q]) cudaGraphExecDestroy(h.graph_exec[q]);
+    h.graph_exec[q] = nullptr;
+  }
+}
+
+int sem_set_option(sem_handle h, const char* key, int64_t value) {
+  if (!h || !key) {
+    set_error("sem_set_option: null argument");
+    return SEM_EINVAL;
+  }
+  const std::string k(key);
+  if ((k == "ax_variant" || k == "ax_variant_pcg") && value >= 0 && value < 3) {
+    (k == "ax_variant" ? h->ax_variant : h->ax_variant_pcg) = (int)value;
+  } else if (k == "use_tma" && (value == 0 || value == 1)) {
+    h->use_tma = value != 0;
+  } else if (k == "gs_acc" && value >= 0 && value <= 2) {
+    h->gs_acc = (int)value;
+  } else {
+    set_error("sem_set_option: unknown key or value out of range: " + k);
+    return SEM_EINVAL;
+  }
+  drop_graphs(*h);   // captured graphs hold the old launch choices
+  return SEM_OK;
+}
+
+int sem_get_option(sem_handle h, const char* key, double* value) {
+  if (!h || !key || !value) {
+    set_error("sem_get_option: null argument");
+    return SEM_EINVAL;
+  }
+  const std::string k(key);
+  if (k == "ax_variant") *value = h->ax_variant;
+  else if (k == "ax_variant_pcg") *value = h->ax_variant_pcg;
+  else if (k == "use_tma") *value = h->use_tma ? 1 : 0;
+  else if (k == "gs_acc") *value = h->gs_acc;
+  else if (k == "launches") *value = (double)h->launches;
+  else if (k.rfind("ax_tune_ms_plain_", 0) == 0 && k.size() == 18 && k[17] >= '0' && k[17] <= '2')
+    *value = h->ax_tune_ms[0][k[17] - '0'];
+  else if (k.rfind("ax_tune_ms_pcg_", 0) == 0 && k.size() == 16 && k[15] >= '0' && k[15] <= '2')
+    *value = h->ax_tune_ms[1][k[15] - '0'];
+  else {
+    set_error("sem_get_option: unknown key: " + k);
+    return SEM_EINVAL;
+  }
+  return SEM_OK;
 }
 
 }  // extern "C"

@@ -6,6 +6,13 @@ namespace sem {
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+template <int n, int V>
+static int tma_variant(Handle& h, const float* u, float* w, const AxPrologue* pro, int dm) {
+  if (!pro) return ax_tma_launch<n, false, kDotDot2, V>(h, u, w, nullptr);
+  if (dm == kDotFP32) return ax_tma_launch<n, true, kDotFP32, V>(h, u, w, pro);
+  return ax_tma_launch<n, true, kDotDot2, V>(h, u, w, pro);
+}
+
 template <int n>
 static int run32(Handle& h, const float* u, float* w, const AxPrologue* pro, int dm) {
   // bulk-copy staged kernel: even n (16-byte element blocks) up to n = 10
@@ -13,9 +20,12 @@ static int run32(Handle& h, const float* u, float* w, const AxPrologue* pro, int
     const bool ok = h.use_tma && aligned16(u) && aligned16(w) &&
                     (!pro || (aligned16(pro->r) && aligned16(pro->minv)));
     if (ok) {
-      if (!pro) return ax_tma_launch<n, false, kDotDot2>(h, u, w, nullptr);
-      if (dm == kDotFP32) return ax_tma_launch<n, true, kDotFP32>(h, u, w, pro);
-      return ax_tma_launch<n, true, kDotDot2>(h, u, w, pro);
+      const int v = pro ? h.ax_variant_pcg : h.ax_variant;
+      switch (v) {
+        case 1: return tma_variant<n, 1>(h, u, w, pro, dm);
+        case 2: return tma_variant<n, 2>(h, u, w, pro, dm);
+        default: return tma_variant<n, 0>(h, u, w, pro, dm);
+      }
     }
   }
   if (!pro) return ax_launch<n, float, false, kDotDot2>(h, u, w, h.G32, h.D32, nullptr);
@@ -42,6 +52,57 @@ int ax_dispatch_fp32(Handle& h, const float* u, float* w, const AxPrologue* pro,
     case 16: return run32<16>(h, u, w, pro, dm);
     default: set_error("ax: unsupported order"); return SEM_EINVAL;
   }
+}
+
+}  // namespace sem
+
+namespace sem {
+
+int launch_scal_setup(Handle& h, PcgScalars* s, double tol, int maxit, int fixed, int stag_window);
+
+// Project autotuner of the staged FP32 operator: times every launch variant
+// (elements per block x pipeline stages) of both modes on this handle's mesh
+// with CUDA events and keeps the fastest.  Runs once, at set-up.
+int autotune_ax32(Handle& h) {
+  if (!(h.n % 2 == 0 && h.n <= 10) || !h.use_tma) return 0;
+  cudaEvent_t a, b;
+  SEM_CUDA(cudaEventCreate(&a));
+  SEM_CUDA(cudaEventCreate(&b));
+  // positive data (0x3f3f3f3f ~ 0.747) so the PCG-mode pap stays positive
+  SEM_CUDA(cudaMemsetAsync(h.b32, 0x3f, sizeof(float) * h.L, h.stream));
+  SEM_CUDA(cudaMemsetAsync(h.x32, 0x3f, sizeof(float) * h.L, h.stream));
+  int rc = launch_scal_setup(h, h.scal_aux, 0.0, 1, 0, 0);
+  AxPrologue pro;
+  pro.r = h.b32;
+  pro.minv = h.minv32;
+  pro.scal = h.scal_aux;
+  pro.pap_partials = h.partials_aux;
+  const int reps = 3;
+  for (int mode = 0; mode < 2 && !rc; ++mode) {
+    float best = 1e30f;
+    int best_v = 0;
+    for (int v = 0; v < kTmaVariants && !rc; ++v) {
+      if (mode == 0) h.ax_variant = v; else h.ax_variant_pcg = v;
+      const AxPrologue* pp = mode ? &pro : nullptr;
+      if ((rc = ax_dispatch_fp32(h, h.x32, h.w32, pp, kDotDot2))) break;
+      SEM_CUDA(cudaEventRecord(a, h.stream));
+      for (int q = 0; q < reps && !rc; ++q) rc = ax_dispatch_fp32(h, h.x32, h.w32, pp, kDotDot2);
+      SEM_CUDA(cudaEventRecord(b, h.stream));
+      SEM_CUDA(cudaEventSynchronize(b));
+      float ms = 0.f;
+      SEM_CUDA(cudaEventElapsedTime(&ms, a, b));
+      h.ax_tune_ms[mode][v] = ms / reps;
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+      }
+    }
+    if (mode == 0) h.ax_variant = best_v; else h.ax_variant_pcg = best_v;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!rc) rc = launch_scal_setup(h, h.scal_aux, 0.0, 1, 0, 0);
+  return rc;
 }
 
 }  // namespace sem

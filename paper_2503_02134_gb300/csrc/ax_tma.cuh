@@ -17,37 +17,43 @@
 
 namespace sem {
 
-template <int n>
+// Launch variants (elements per block, pipeline stages); the set-up
+// autotuner times them on the actual mesh and keeps the fastest.
+template <int n, int V>
 struct TmaShape {
   static constexpr int n2 = n * n;
   static constexpr int n3 = n * n * n;
-  static constexpr int EPB = (128 / n2) > 0 ? (128 / n2) : 1;   // ~128 threads per block
+  static constexpr int EPB_BIG = (128 / n2) > 0 ? (128 / n2) : 1;
+  static constexpr int EPB_SMALL = (64 / n2) > 0 ? (64 / n2) : 1;
+  static constexpr int EPB = V == 0 ? EPB_BIG : EPB_SMALL;
+  static constexpr int NS = V == 0 ? 2 : (V == 1 ? 3 : 4);     // bulk-copy stages
   static constexpr int NT = ((n2 * EPB + 31) / 32) * 32;
   static constexpr uint32_t VEC = EPB * n3 * 4;                 // bytes of one vector per stage
 };
+constexpr int kTmaVariants = 3;
 
-template <int n, bool PCG>
+template <int n, bool PCG, int V>
 constexpr size_t tma_smem_bytes() {
-  using S = TmaShape<n>;
+  using S = TmaShape<n, V>;
   constexpr int NV = PCG ? 3 : 1;
-  return 2 * (size_t)(NV + 6) * S::VEC + 2 * (size_t)S::VEC + 2 * sizeof(uint64_t);
+  return S::NS * (size_t)(NV + 6) * S::VEC + 2 * (size_t)S::VEC + S::NS * sizeof(uint64_t);
 }
 
-template <int n, bool PCG, int DM>
-__global__ void __launch_bounds__(TmaShape<n>::NT)
+template <int n, bool PCG, int DM, int V>
+__global__ void __launch_bounds__(TmaShape<n, V>::NT)
     ax_tma_kernel(const float* __restrict__ uin, float* __restrict__ wout,
                   const float* __restrict__ G, const float* __restrict__ Dg,
                   const uint8_t* __restrict__ faces, int64_t E, const float* __restrict__ rr,
                   const float* __restrict__ minv, float* pp, PcgScalars* __restrict__ scal,
                   double* __restrict__ partials, int* __restrict__ err) {
-  using S = TmaShape<n>;
-  constexpr int n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  using S = TmaShape<n, V>;
+  constexpr int n2 = S::n2, n3 = S::n3, EPB = S::EPB, NS = S::NS;
   constexpr int NV = PCG ? 3 : 1;
   constexpr int SV = EPB * n3;                 // floats of one vector per stage
   constexpr int STAGE = (NV + 6) * SV;         // floats per stage
   extern __shared__ __align__(128) float smem_f[];
   float* const stage0 = smem_f;
-  float* const sr = smem_f + 2 * STAGE;
+  float* const sr = smem_f + NS * STAGE;
   float* const ss = sr + SV;
   uint64_t* const bar = reinterpret_cast<uint64_t*>(ss + SV);
   __shared__ float sD[n][n + 1];
@@ -81,15 +87,16 @@ __global__ void __launch_bounds__(TmaShape<n>::NT)
   };
 
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
     fence_mbar_init();
   }
   for (int q = tid; q < n2; q += blockDim.x) sD[q / n][q % n] = Dg[q];
   __syncthreads();
   if (tid == 0) {
-    if ((int64_t)blockIdx.x < ngroups) issue(0, blockIdx.x);
-    if ((int64_t)blockIdx.x + gridDim.x < ngroups) issue(1, (int64_t)blockIdx.x + gridDim.x);
+    for (int q = 0; q < NS; ++q) {
+      const int64_t g0 = (int64_t)blockIdx.x + (int64_t)q * gridDim.x;
+      if (g0 < ngroups) issue(q, g0);
+    }
   }
   float Di[n], Dj[n], DiT[n], DjT[n];
 #pragma unroll
@@ -103,15 +110,15 @@ __global__ void __launch_bounds__(TmaShape<n>::NT)
   DotAcc<float, DM> acc;
   bool aborted = false;
   int t = 0;
-  int waited[2] = {0, 0};   // completed phases per stage
+  // group t of this block lives on stage t % NS and is that stage's
+  // (t / NS)-th use, so its barrier phase parity is (t / NS) & 1
   for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, ++t) {
-    const int st = t & 1;
-    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)(waited[st] & 1));
+    const int st = t % NS;
+    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((t / NS) & 1));
     if (__syncthreads_or(!ok)) {
       aborted = true;
       break;
     }
-    ++waited[st];
     float* const sb = stage0 + st * STAGE;
     float* const su = PCG ? sb + 2 * SV : sb;   // p (formed in place) or u
     const float* const Gs = sb + NV * SV + ler * 6 * n3 + ij;
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(TmaShape<n>::NT)
     }
     __syncthreads();   // stage st and sr/ss are free again
     if (tid == 0) {
-      const int64_t gn = g + 2 * (int64_t)gridDim.x;
+      const int64_t gn = g + NS * (int64_t)gridDim.x;
       if (gn < ngroups) {
         fence_proxy_async_smem();
         issue(st, gn);
@@ -195,9 +202,11 @@ __global__ void __launch_bounds__(TmaShape<n>::NT)
     if (tid == 0) {
       atomicExch(err, 1);
       const int64_t g_abort = blockIdx.x + (int64_t)t * gridDim.x;
-      for (int s2 = 0; s2 < 2; ++s2) {
-        const int64_t g_out = g_abort + (int64_t)((s2 - (t & 1) + 2) & 1) * gridDim.x;
-        if (g_out < ngroups) mbar_wait_bounded(&bar[s2], (uint32_t)(waited[s2] & 1));
+      for (int s2 = 0; s2 < NS; ++s2) {
+        // the group outstanding on stage s2 is the next one mapped to it
+        const int64_t g_out = g_abort + (int64_t)((s2 - t % NS + NS) % NS) * gridDim.x;
+        const int done_uses = t > s2 ? (t - 1 - s2) / NS + 1 : 0;
+        if (g_out < ngroups) mbar_wait_bounded(&bar[s2], (uint32_t)(done_uses & 1));
       }
     }
     return;
@@ -223,11 +232,11 @@ __global__ void __launch_bounds__(TmaShape<n>::NT)
   }
 }
 
-template <int n, bool PCG, int DM>
+template <int n, bool PCG, int DM, int V>
 int ax_tma_launch(Handle& h, const float* u, float* w, const AxPrologue* pro) {
-  using S = TmaShape<n>;
-  auto kern = ax_tma_kernel<n, PCG, DM>;
-  constexpr size_t smem = tma_smem_bytes<n, PCG>();
+  using S = TmaShape<n, V>;
+  auto kern = ax_tma_kernel<n, PCG, DM, V>;
+  constexpr size_t smem = tma_smem_bytes<n, PCG, V>();
   SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::NT, smem));

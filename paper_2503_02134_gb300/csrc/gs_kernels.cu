@@ -59,49 +59,81 @@ struct GsSum<float, kGsTwoSum> {
 
 constexpr int kGsThreads = 256;
 constexpr int kGsRegCopies = 8;   // copies kept in registers; longer segments reload indices
+constexpr int kGsChunks = 4;      // chunks a warp works on at once (loads in flight per lane)
 
+template <typename T, int ACC>
+__device__ __forceinline__ void gs_chunk_generic(T* __restrict__ v, const int* sl, int m) {
+  GsSum<T, ACC> acc;
+  for (int q = 0; q < m; ++q) {
+    const int i = __ldg(sl + 32 * q);
+    if (i >= 0) acc.add(v[i]);
+  }
+  const T out = acc.result();
+  for (int q = 0; q < m; ++q) {
+    const int i = __ldg(sl + 32 * q);
+    if (i >= 0) v[i] = out;
+  }
+}
+
+// A warp takes kGsChunks consecutive chunks (32 segments each, neighbours in
+// global-id order) and issues all their index loads, then all their value
+// gathers, before summing: up to 32 independent loads per lane in flight.
 template <typename T, int ACC>
 __global__ void __launch_bounds__(kGsThreads)
     gs_bucket_kernel(T* __restrict__ v, const int2* __restrict__ chunks, int64_t nchunks,
                      const int* __restrict__ slots) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nwarps) {
-    const int2 d = __ldg(chunks + c);
-    const int m = d.x;
-    const int* sl = slots + d.y + lane;
-    GsSum<T, ACC> acc;
-    if (m <= kGsRegCopies) {
-      int id[kGsRegCopies];
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t c0 = warp * kGsChunks; c0 < nchunks; c0 += nwarps * kGsChunks) {
+    int m[kGsChunks];
+    const int* sl[kGsChunks];
+    bool small = true;
 #pragma unroll
-      for (int q = 0; q < kGsRegCopies; ++q) {
-        id[q] = q < m ? __ldg(sl + 32 * q) : -1;
+    for (int u = 0; u < kGsChunks; ++u) {
+      if (c0 + u < nchunks) {
+        const int2 d = __ldg(chunks + c0 + u);
+        m[u] = d.x;
+        sl[u] = slots + d.y + lane;
+      } else {
+        m[u] = 0;
+        sl[u] = slots;
       }
+      small = small && m[u] <= kGsRegCopies;
+    }
+    if (small) {
+      int id[kGsChunks][kGsRegCopies];
+      T val[kGsChunks][kGsRegCopies];
 #pragma unroll
-      for (int q = 0; q < kGsRegCopies; ++q)
-        if (id[q] >= 0) acc.add(v[id[q]]);
-      const T out = acc.result();
+      for (int u = 0; u < kGsChunks; ++u)
 #pragma unroll
-      for (int q = 0; q < kGsRegCopies; ++q)
-        if (id[q] >= 0) v[id[q]] = out;
+        for (int q = 0; q < kGsRegCopies; ++q) id[u][q] = q < m[u] ? __ldg(sl[u] + 32 * q) : -1;
+#pragma unroll
+      for (int u = 0; u < kGsChunks; ++u)
+#pragma unroll
+        for (int q = 0; q < kGsRegCopies; ++q) val[u][q] = id[u][q] >= 0 ? v[id[u][q]] : T(0);
+#pragma unroll
+      for (int u = 0; u < kGsChunks; ++u) {
+        GsSum<T, ACC> acc;
+#pragma unroll
+        for (int q = 0; q < kGsRegCopies; ++q)
+          if (id[u][q] >= 0) acc.add(val[u][q]);
+        const T out = acc.result();
+#pragma unroll
+        for (int q = 0; q < kGsRegCopies; ++q)
+          if (id[u][q] >= 0) v[id[u][q]] = out;
+      }
     } else {
-      for (int q = 0; q < m; ++q) {
-        const int i = __ldg(sl + 32 * q);
-        if (i >= 0) acc.add(v[i]);
-      }
-      const T out = acc.result();
-      for (int q = 0; q < m; ++q) {
-        const int i = __ldg(sl + 32 * q);
-        if (i >= 0) v[i] = out;
-      }
+      for (int u = 0; u < kGsChunks; ++u)
+        if (m[u] > 0) gs_chunk_generic<T, ACC>(v, sl[u], m[u]);
     }
   }
 }
 
 int launch_gs_acc(Handle& h, sem_precision p, void* v, int acc) {
   if (h.n_chunks == 0) return 0;
-  const int64_t warps_per_block = kGsThreads / 32;
-  int64_t g = (h.n_chunks + warps_per_block - 1) / warps_per_block;
+  const int64_t chunks_per_block = kGsThreads / 32 * kGsChunks;
+  int64_t g = (h.n_chunks + chunks_per_block - 1) / chunks_per_block;
   int64_t cap = (int64_t)h.num_sms * 8;
   const int grid = (int)(g < cap ? g : cap);
   if (p == SEM_FP64) {

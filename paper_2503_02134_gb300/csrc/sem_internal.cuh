@@ -68,6 +68,7 @@ struct Handle {
   double* mult64 = nullptr;    // L
   double* c64 = nullptr;       // L   mask / multiplicity
   float* c32 = nullptr;
+  uint8_t* cw8 = nullptr;      // L: multiplicity on interior nodes, 0 on the Dirichlet boundary
   int* seg_off = nullptr;      // n_segments + 1
   int* perm = nullptr;         // n_shared local indices grouped by global node
   int64_t n_segments = 0, n_shared = 0;
@@ -75,6 +76,9 @@ struct Handle {
   int2* gs_chunks = nullptr;   // per 32-segment chunk: {copies m, first slot}
   int64_t n_chunks = 0, n_slots = 0;
   bool use_tma = true;         // FP32 operator: bulk-copy staged kernel where it applies
+  int ax_variant = 0;          // launch variant of the staged FP32 operator (plain / PCG mode)
+  int ax_variant_pcg = 0;
+  float ax_tune_ms[2][4] = {};  // autotuner timings [plain, PCG][variant]
   int gs_acc = 2;              // mixed-path accumulation: 2 TwoSum (default), 0 FP64, 1 FP32
 
   // Jacobi
@@ -144,6 +148,8 @@ struct AxPrologue {
   double* pap_partials = nullptr;
 };
 int launch_ax_local(Handle& h, sem_precision p, const void* u, void* w, const AxPrologue* pro);
+
+int autotune_ax32(Handle& h);
 
 // gs_kernels.cu
 int launch_gs(Handle& h, sem_precision p, void* v);

@@ -454,14 +454,16 @@ __global__ void sort_segments(const int* seg_off, int64_t nseg, int* perm) {
 }
 
 __global__ void mult_and_weights(const int* gid, const int* cnt, const double* mask, int64_t L,
-                                 double* mult, double* c64, float* c32) {
+                                 double* mult, double* c64, float* c32, uint8_t* cw8) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
        l += (int64_t)gridDim.x * blockDim.x) {
-    double m = (double)cnt[gid[l]];
+    const int mi = cnt[gid[l]];
+    double m = (double)mi;
     mult[l] = m;
     double c = mask[l] / m;
     c64[l] = c;
     c32[l] = (float)c;
+    cw8[l] = mask[l] != 0.0 ? (uint8_t)(mi < 255 ? mi : 255) : (uint8_t)0;
   }
 }
 
@@ -497,7 +499,7 @@ int launch_gs_map(Handle& h) {
   sort_segments<<<grid_for(h, h.n_segments, 256), 256, 0, h.stream>>>(h.seg_off, h.n_segments,
                                                                         h.perm);
   mult_and_weights<<<grid_for(h, h.L, 256), 256, 0, h.stream>>>(h.gid, cnt, h.mask64, h.L,
-                                                                 h.mult64, h.c64, h.c32);
+                                                                 h.mult64, h.c64, h.c32, h.cw8);
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
   SEM_CUDA(cudaFreeAsync(cursor, h.stream));

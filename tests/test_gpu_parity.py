@@ -323,3 +323,62 @@ def test_graph_and_plain_launch_agree(sem):
         assert i1["iters"] == i2["iters"]
         assert torch.equal(x1, x2)   # deterministic reductions: bitwise equal
     S.close()
+
+
+def test_launch_variants_agree(sem):
+    """Every staged-operator launch variant and the unstaged kernel give the
+    same FP32 result (identical arithmetic per element); the set-up
+    autotuner's choice is readable."""
+    P = so.Problem(5, 4, 3, 7, deform=True)
+    S = sem.Solver(5, 4, 3, 7, deform=True)
+    for key in ("ax_variant", "ax_variant_pcg"):
+        assert sem.sem_get_option(S.h, key) in (0, 1, 2)
+    assert sem.sem_get_option(S.h, "ax_tune_ms_plain_0") > 0
+    u = cu(sem_inputs.uniform_local(P.L, seed=31, dtype=np.float32), torch.float32)
+    outs = []
+    for v in range(3):
+        sem.sem_set_option(S.h, "ax_variant", v)
+        w = torch.empty_like(u)
+        sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)
+        outs.append(w)
+    sem.sem_set_option(S.h, "use_tma", 0)
+    w = torch.empty_like(u)
+    sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)
+    outs.append(w)
+    for o in outs[1:]:
+        assert rel_maxerr(o.cpu(), outs[0].cpu()) < 1e-6
+    ref = P.mask * P.ax_local(u.cpu().numpy().astype(np.float64))
+    assert rel_maxerr(outs[0].cpu(), ref) < 1e-5
+    # PCG mode through a solve: every variant converges to the same answer
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 4, b)
+    sem.sem_set_option(S.h, "use_tma", 1)
+    xs = []
+    for v in range(3):
+        sem.sem_set_option(S.h, "ax_variant_pcg", v)
+        x, info = S.solve(b, tol=1e-9, maxit=3000, precision=sem.SEM_MIXED_FP32)
+        assert info["rc"] == 0 and info["relres_true"] <= 1e-9
+        xs.append(x)
+    for x in xs[1:]:
+        assert rel_maxerr(x.cpu(), xs[0].cpu()) < 1e-7
+    S.close()
+
+
+def test_gs_accumulation_modes(sem):
+    P = so.Problem(4, 3, 3, 5, deform=True)
+    S = sem.Solver(4, 3, 3, 5, deform=True)
+    v32 = sem_inputs.uniform_local(P.L, seed=41, dtype=np.float32)
+    ref = P.dssum(v32.astype(np.float64)).astype(np.float32)
+    ulp = np.spacing(np.abs(ref).astype(np.float32))
+    res = {}
+    for mode in (0, 1, 2):
+        sem.sem_set_option(S.h, "gs_acc", mode)
+        t = cu(v32, torch.float32)
+        sem.sem_gs(S.h, t, sem.SEM_MIXED_FP32)
+        res[mode] = t.cpu().numpy()
+    np.testing.assert_array_equal(res[0], ref)          # FP64 sums, rounded once
+    assert np.all(np.abs(res[2] - ref) <= ulp)          # error-free TwoSum
+    assert np.all(np.abs(res[1] - ref) <= 8 * ulp)      # plain FP32: up to m-1 roundings
+    with pytest.raises(sem.SemError):
+        sem.sem_set_option(S.h, "gs_acc", 7)
+    S.close()
