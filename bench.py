@@ -176,13 +176,16 @@ def main():
         return info
 
     if args.profile:
-        S.solve(b, fixed_iters=3, precision=sem.SEM_MIXED_FP32, x=x, use_graph=False)
         with torch.cuda.stream(stream):
             u = torch.rand(L, dtype=torch.float32, device="cuda")
             w = torch.empty_like(u)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bench_profile")
+        S.solve(b, fixed_iters=3, precision=sem.SEM_MIXED_FP32, x=x, use_graph=False)
         for _ in range(2):
             sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         S.close()
         print(json.dumps({"profile_run": "ok"}))
         return 0

@@ -107,7 +107,7 @@ typedef struct {
 
 typedef struct {
   int iters;             /* PCG iterations (inner iterations summed) */
-  int refinements;       /* FP64 outer residual evaluations after the first */
+  int refinements;       /* FP64 residual replacements (mode 0) or restarts (mode 1) */
   int status;            /* 0, SEM_MAXIT, SEM_STAGNATED or SEM_BREAKDOWN */
   double relres;         /* final recursive ||r||_c/||b||_c of the last (inner) solve, relative to b */
   double relres_true;    /* ||b - A x||_c/||b||_c recomputed in FP64 */
@@ -128,6 +128,11 @@ typedef struct {
   int chunk;             /* iterations per convergence poll (default 32) */
   int precond;           /* 1 Jacobi (default), -1 identity */
   double* history;       /* optional host array of maxit+1 recursive residuals (or NULL) */
+  int refine_mode;       /* mixed only: 0 reliable updates (default): the FP64 true residual
+                            replaces the FP32 one each time it fell by replace_factor, CG
+                            continues with the same search direction; 1 restarted refinement:
+                            a new inner solve of A d = r64 per FP64 cycle */
+  double replace_factor; /* mixed, refine_mode 0: residual drop between replacements (1e-2) */
 } sem_solve_opts;
 
 /* Set up a problem: GLL nodes/weights and the derivative matrix

@@ -61,7 +61,8 @@ class sem_solve_opts(ctypes.Structure):
                 ("fixed_iters", ctypes.c_int), ("no_refine", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("chunk", ctypes.c_int), ("precond", ctypes.c_int),
-                ("history", ctypes.POINTER(ctypes.c_double))]
+                ("history", ctypes.POINTER(ctypes.c_double)), ("refine_mode", ctypes.c_int),
+                ("replace_factor", ctypes.c_double)]
 
 
 def _load():
@@ -252,7 +253,7 @@ class Solver:
 
     def solve(self, f, x0=None, tol=1e-8, maxit=1000, precision=SEM_FP64, fixed_iters=0,
               no_refine=False, history=False, use_graph=True, chunk=0, inner_tol=0.0,
-              precond=True, x=None):
+              precond=True, x=None, refine_mode=0, replace_factor=0.0):
         import torch
         if x is None:
             x = torch.empty_like(f)
@@ -264,6 +265,8 @@ class Solver:
         o.chunk = chunk
         o.inner_tol = inner_tol
         o.precond = 1 if precond else -1
+        o.refine_mode = refine_mode
+        o.replace_factor = replace_factor
         hist = None
         if history:
             hist = np.zeros((fixed_iters or maxit) + 1)

@@ -59,7 +59,7 @@ struct GsSum<float, kGsTwoSum> {
 
 constexpr int kGsThreads = 256;
 constexpr int kGsRegCopies = 8;   // copies kept in registers; longer segments reload indices
-constexpr int kGsChunks = 4;      // chunks a warp works on at once (loads in flight per lane)
+constexpr int kGsChunks = 1;      // chunks a warp works on at once (more costs occupancy)
 
 template <typename T, int ACC>
 __device__ __forceinline__ void gs_chunk_generic(T* __restrict__ v, const int* sl, int m) {

@@ -19,6 +19,9 @@ int launch_cast32to64(Handle& h, const float* a, double* b);
 int launch_add32to64(Handle& h, double* x, const float* d);
 int launch_masked_copy64(Handle& h, const double* src, double* dst);
 int launch_masked_copy32(Handle& h, const double* src, float* dst);
+int launch_cg_replace32(Handle& h, int dm, const double* r64, float* r32, const float* minv,
+                        double tol, PcgScalars* s);
+int launch_set_bnorm(Handle& h, PcgScalars* s, double bnorm, double* hist);
 int launch_scal_setup(Handle& h, PcgScalars* s, double tol, int maxit, int fixed, int stag_window);
 
 }  // namespace sem

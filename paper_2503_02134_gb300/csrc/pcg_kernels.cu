@@ -182,6 +182,53 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
+// Residual replacement (reliable update) of the FP32 recursion: r32 takes
+// the FP64 true residual r64 rounded once, rtz/rtr are recomputed from it,
+// beta is recomputed from the new rtz, and the search direction p is kept,
+// so CG continues instead of restarting.
+template <int DM>
+__global__ void __launch_bounds__(kVecThreads)
+    cg_replace_kernel(const double* __restrict__ r64, float* __restrict__ r32,
+                      const float* __restrict__ c, const float* __restrict__ minv, int64_t L,
+                      double tol, PcgScalars* __restrict__ s, double* __restrict__ partials) {
+  __shared__ double sh[kVecThreads / 32];
+  DotAcc<float, DM> a_rr, a_rz;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const float rv = (float)r64[l];
+    r32[l] = rv;
+    const float cr = c[l] * rv;
+    a_rr.add(cr, rv);
+    a_rz.add(cr, minv[l] * rv);
+  }
+  const double v0 = block_sum<DM>(a_rr.value(), sh);
+  const double v1 = block_sum<DM>(a_rz.value(), sh);
+  const double vals[2] = {v0, v1};
+  if (publish_and_elect(vals, 2, partials, &s->counter[2])) {
+    const double rtr = reduce_partials<DM>(partials, 0, sh);
+    const double rtz = reduce_partials<DM>(partials, 1, sh);
+    if (threadIdx.x == 0) {
+      s->rtr = rtr;
+      s->relres = sqrt(rtr) / s->bnorm;
+      s->beta = s->iter > 0 ? rtz / s->rtz_old : 0.0;
+      s->rtz = rtz;
+      s->tol = tol;
+      s->best_rtr = rtr;
+      s->best_it = s->iter;
+      s->status = 0;
+      s->done = s->iter >= s->maxit ? 1 : 0;
+      s->counter[2] = 0u;
+    }
+  }
+}
+
+__global__ void set_bnorm_kernel(PcgScalars* s, double bnorm, double* hist) {
+  s->bnorm = bnorm;
+  s->relres = bnorm > 0.0 ? sqrt(s->rtr) / bnorm : 0.0;
+  if (hist) hist[s->iter] = s->relres;
+  s->done = (bnorm == 0.0) || (!s->fixed && s->relres <= s->tol) || s->maxit <= 0;
+}
+
 template <typename T, int DM>
 __global__ void __launch_bounds__(kVecThreads)
     glsc3_kernel(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ c,
@@ -340,6 +387,26 @@ int launch_glsc3(Handle& h, sem_precision p, const void* a, const void* b, doubl
   else
     glsc3_kernel<float, kDotDot2><<<grid, kVecThreads, 0, h.stream>>>(
         (const float*)a, (const float*)b, h.c32, h.L, h.partials_aux, counter, out_dev);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int launch_cg_replace32(Handle& h, int dm, const double* r64, float* r32, const float* minv,
+                        double tol, PcgScalars* s) {
+  if (dm == kDotFP32)
+    cg_replace_kernel<kDotFP32><<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(
+        r64, r32, h.c32, minv, h.L, tol, s, h.partials);
+  else
+    cg_replace_kernel<kDotDot2><<<vec_grid(h, h.L), kVecThreads, 0, h.stream>>>(
+        r64, r32, h.c32, minv, h.L, tol, s, h.partials);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int launch_set_bnorm(Handle& h, PcgScalars* s, double bnorm, double* hist) {
+  set_bnorm_kernel<<<1, 1, 0, h.stream>>>(s, bnorm, hist);
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
   return 0;

@@ -134,8 +134,10 @@ int ensure_history(Handle& h, int maxit) {
   return 0;
 }
 
-// r64 = f - A64 x64 in FP64; returns ||r64||_c / ||f||_c through *relres.
-int fp64_residual(Handle& h, const double* f, bool x_is_zero, double* relres) {
+// r64 = f - A64 x64 in FP64; returns ||r64||_c / ||f||_c through *relres
+// (and ||f||_c through *bnorm when asked).
+int fp64_residual(Handle& h, const double* f, bool x_is_zero, double* relres,
+                  double* bnorm = nullptr) {
   int rc;
   if ((rc = launch_scal_setup(h, h.scal_aux, 0.0, 1, 1, 0))) return rc;
   if (!x_is_zero) {
@@ -150,6 +152,7 @@ int fp64_residual(Handle& h, const double* f, bool x_is_zero, double* relres) {
   PcgScalars s;
   if ((rc = read_scalars(h, h.scal_aux, &s))) return rc;
   *relres = s.relres;
+  if (bnorm) *bnorm = s.bnorm;
   return 0;
 }
 
@@ -226,6 +229,60 @@ int pcg_solve(Handle& h, const double* f, const double* x0, double* x, const sem
     }
     SEM_CUDA(cudaEventRecord(h.ev1, h.stream));
     if ((rc = fp64_residual(h, f, false, &res.relres_true))) { restore(); return rc; }
+  } else if (prec != SEM_FP32_ALL && !o.no_refine && !fixed && o.refine_mode == 0) {
+    // Mixed with reliable updates: one FP32 CG recursion for A x = f with
+    // x = x64 + x32.  Each time its residual has fallen by `delta` the
+    // correction is folded into x64, the FP64 true residual is recomputed and
+    // replaces r32, and the recursion continues with the same p.
+    const double delta = o.replace_factor > 0 ? o.replace_factor : 1e-2;
+    if ((rc = launch_masked_copy64(h, x0, h.x64))) { restore(); return rc; }
+    double relres_true = 1.0, bnorm = 0.0;
+    if ((rc = fp64_residual(h, f, x0 == nullptr, &relres_true, &bnorm))) { restore(); return rc; }
+    res.status = 0;
+    int replacements = 0, slow = 0;
+    PcgScalars fin{};
+    if (bnorm > 0.0 && relres_true > tol) {
+      SEM_CUDA(cudaMemsetAsync(h.x32, 0, sizeof(float) * h.L, h.stream));
+      SEM_CUDA(cudaMemsetAsync(h.p32, 0, sizeof(float) * h.L, h.stream));
+      if ((rc = launch_cast64to32(h, h.r64, h.b32))) { restore(); return rc; }
+      double seg_tol = std::max(tol, delta * relres_true);
+      if ((rc = launch_scal_setup(h, h.scal, seg_tol, maxit, 0, 0))) { restore(); return rc; }
+      if ((rc = launch_cg_init32(h, kDotDot2, h.r32, h.b32, nullptr, h.minv32, h.scal,
+                                 h.hist_dev))) {
+        restore();
+        return rc;
+      }
+      if ((rc = launch_set_bnorm(h, h.scal, bnorm, h.hist_dev))) { restore(); return rc; }
+      for (;;) {
+        if ((rc = read_scalars(h, h.scal, &fin))) { restore(); return rc; }
+        if (!fin.done && (rc = iterate(h, kGMixed, chunk, use_graph, &fin))) { restore(); return rc; }
+        if ((rc = launch_add32to64(h, h.x64, h.x32))) { restore(); return rc; }
+        SEM_CUDA(cudaMemsetAsync(h.x32, 0, sizeof(float) * h.L, h.stream));
+        const double prev = relres_true;
+        if ((rc = fp64_residual(h, f, false, &relres_true))) { restore(); return rc; }
+        if (relres_true <= tol) break;
+        if (fin.status == SEM_BREAKDOWN) { res.status = SEM_BREAKDOWN; break; }
+        if (fin.iter >= maxit) { res.status = SEM_MAXIT; break; }
+        slow = relres_true > 0.5 * prev ? slow + 1 : 0;
+        if (slow >= 3 || replacements >= 4 * max_cycles) { res.status = SEM_STAGNATED; break; }
+        seg_tol = std::max(tol, delta * relres_true);
+        if ((rc = launch_cg_replace32(h, kDotDot2, h.r64, h.r32, h.minv32, seg_tol, h.scal))) {
+          restore();
+          return rc;
+        }
+        ++replacements;
+      }
+      if (o.history) {
+        hist_host.resize(fin.iter + 1);
+        SEM_CUDA(cudaMemcpy(hist_host.data(), h.hist_dev, sizeof(double) * (fin.iter + 1),
+                            cudaMemcpyDeviceToHost));
+      }
+    }
+    res.iters = fin.iter;
+    res.refinements = replacements;
+    res.relres = fin.relres;
+    res.relres_true = relres_true;
+    SEM_CUDA(cudaEventRecord(h.ev1, h.stream));
   } else {
     const bool all32 = prec == SEM_FP32_ALL;
     const bool refine = !all32 && !o.no_refine && !fixed;

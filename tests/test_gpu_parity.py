@@ -378,7 +378,31 @@ def test_gs_accumulation_modes(sem):
         res[mode] = t.cpu().numpy()
     np.testing.assert_array_equal(res[0], ref)          # FP64 sums, rounded once
     assert np.all(np.abs(res[2] - ref) <= ulp)          # error-free TwoSum
-    assert np.all(np.abs(res[1] - ref) <= 8 * ulp)      # plain FP32: up to m-1 roundings
+    # plain FP32: m-1 roundings, each bounded by eps32 * (sum of |copies|)
+    bound = 8 * 2.0 ** -24 * P.dssum(np.abs(v32.astype(np.float64)))
+    assert np.all(np.abs(res[1].astype(np.float64) - ref.astype(np.float64)) <= bound)
     with pytest.raises(sem.SemError):
         sem.sem_set_option(S.h, "gs_acc", 7)
+    S.close()
+
+
+def test_reliable_updates_and_restarts_both_converge(sem):
+    """Mixed precision with residual replacement (CG keeps its search
+    direction) and with restarted refinement both reach the FP64 target and
+    the oracle solution; replacement needs no more iterations than restarts."""
+    P = so.Problem(8, 6, 5, 7, deform=True)
+    b = P.rhs_uniform(seed=9)
+    xo, ito, _ = P.pcg(b, tol=1e-12, maxit=4000)
+    S = sem.Solver(8, 6, 5, 7, deform=True)
+    res = {}
+    for mode in (0, 1):
+        x, info = S.solve(cu(b), tol=1e-8, maxit=4000, precision=sem.SEM_MIXED_FP32,
+                          refine_mode=mode, history=True)
+        assert info["rc"] == 0 and info["relres_true"] <= 1e-8, info
+        assert rel_maxerr(x.cpu(), xo) < 1e-7
+        assert P.true_relres(b, x.cpu().numpy()) <= 1.05e-8
+        res[mode] = info
+    assert res[0]["iters"] <= res[1]["iters"]
+    h = res[0]["history"]
+    assert h[0] == pytest.approx(1.0, rel=1e-6) and h[-1] <= 1e-8
     S.close()
