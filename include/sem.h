@@ -189,6 +189,25 @@ int sem_pcg_solve(sem_handle h, const double* f, const double* x0, double* x,
 int sem_pcg_solve_ex(sem_handle h, const double* f, const double* x0, double* x,
                      const sem_solve_opts* opts, sem_info* info);
 
+/* Allocation-free weighted dot product: *result = sum_i a_i c_i b_i over n
+ * FP64 values, the same quantity as sem_glsc3 with the weights passed in.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (no cudaMalloc allowed: an allocation-free
+ * section of a host application, a sandbox with a fixed memory budget).  It
+ * needs no handle and allocates nothing: its block partial sums live in a
+ * static device array of 4096 doubles (32 KiB) that every GPU loading this
+ * library holds until the process exits, so n may not exceed 33,554,432
+ * (larger n returns SEM_EINVAL and changes nothing).  a, b, c: device
+ * pointers to n doubles; result: device pointer to one double; stream: a
+ * cudaStream_t (NULL = legacy default stream); the call is asynchronous.
+ * The first call on a device looks up the array's device address on the
+ * current device; make that first call before any stream capture.  All calls
+ * share the one array (the call zeroes its counter first), so calls that
+ * overlap on the GPU -- on different streams, or from several threads --
+ * race and must be serialised by the caller. */
+int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t n,
+                      double* result, void* stream);
+
 /* Tuning knobs and diagnostics of the implementation (the paper has no
  * counterpart; they never change results beyond rounding).  Keys:
  *   "ax_variant", "ax_variant_pcg"  launch variant (0..2) of the bulk-copy

@@ -86,6 +86,7 @@ def _load():
         "sem_pcg_solve_ex": (i, [h, vp, vp, vp, ctypes.POINTER(sem_solve_opts),
                                  ctypes.POINTER(sem_info)]),
         "sem_set_option": (i, [h, ctypes.c_char_p, ctypes.c_int64]),
+        "sem_glsc3_noalloc": (i, [vp, vp, vp, ctypes.c_int64, vp, vp]),
         "sem_get_option": (i, [h, ctypes.c_char_p, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
@@ -98,7 +99,7 @@ def _load():
 _lib = _load()
 EXPORTED = ("sem_setup", "sem_destroy", "sem_last_error", "sem_get_sizes", "sem_ax",
             "sem_ax_local", "sem_gs", "sem_glsc3", "sem_get_field", "sem_rhs", "sem_pcg_solve",
-            "sem_pcg_solve_ex", "sem_set_option", "sem_get_option")
+            "sem_pcg_solve_ex", "sem_set_option", "sem_get_option", "sem_glsc3_noalloc")
 
 
 class SemError(RuntimeError):
@@ -188,6 +189,12 @@ def sem_pcg_solve_ex(h, f, x0, x, opts: sem_solve_opts):
     rc = _check(_lib.sem_pcg_solve_ex(h, _ptr(f), _ptr(x0), _ptr(x), ctypes.byref(opts),
                                       ctypes.byref(info)), "sem_pcg_solve_ex")
     return rc, info
+
+
+def sem_glsc3_noalloc(a, b, c, n, result, stream=None):
+    """Allocation-free sum_i a_i c_i b_i into the device double `result`."""
+    return _check(_lib.sem_glsc3_noalloc(_ptr(a), _ptr(b), _ptr(c), int(n), _ptr(result), stream),
+                  "sem_glsc3_noalloc")
 
 
 def sem_set_option(h, key: str, value: int):
