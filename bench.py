@@ -114,6 +114,63 @@ def cpu_baseline(sample=CPU_SAMPLE):
                       f"{dt:.2f} s; GDOF/s = local DOFs x iterations / time"}
 
 
+def batched_leg(sem, torch):
+    """64 independent deformed problems, k ~ U{8..24}, N ~ U{5,7,9} (seed 1),
+    mixed precision to 1e-8: one batched solve (persistent launches, CUDA
+    graph, autotuned) against the same problems solved one after another."""
+    import sem_inputs
+    cases = sem_inputs.batched_cases()
+    meshes = [sem.box_mesh(k, k, k, deform=True) for k, _ in cases]
+    t0 = time.perf_counter()
+    b = sem.sem_batch_setup(meshes, [N for _, N in cases])
+    setup_s = time.perf_counter() - t0
+    fs, xs, hs = [], [], []
+    for i in range(len(cases)):
+        h = sem.sem_batch_problem(b, i)
+        L = sem.sem_get_sizes(h).L
+        f = torch.empty(L, dtype=torch.float64, device="cuda")
+        sem.sem_rhs(h, sem.RHS_UNIFORM, 1000 + i, f)
+        fs.append(f)
+        xs.append(torch.zeros_like(f))
+        hs.append(h)
+    torch.cuda.synchronize()
+    o = sem.sem_solve_opts()
+    o.tol, o.maxit, o.precision = 1e-8, 5000, sem.SEM_MIXED_FP32
+    sem.sem_batch_pcg_solve(b, fs, xs, o)   # warm-up (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, infos = sem.sem_batch_pcg_solve(b, fs, xs, o)
+    torch.cuda.synchronize()
+    batched_s = time.perf_counter() - t0
+    # the same problems, one standalone solve after another
+    for i in range(len(cases)):
+        sem.sem_pcg_solve_ex(hs[i], fs[i], None, xs[i], o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_iters = 0
+    seq_ok = True
+    for i in range(len(cases)):
+        rci, inf = sem.sem_pcg_solve_ex(hs[i], fs[i], None, xs[i], o)
+        seq_iters += inf.iters
+        seq_ok = seq_ok and rci == 0
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    total_L = sum(sem.sem_get_sizes(h).L for h in hs)
+    it = [i["iters"] for i in infos]
+    out = {"problems": len(cases), "local_dofs": total_L, "orders": sorted(set(N for _, N in cases)),
+           "k_range": [min(k for k, _ in cases), max(k for k, _ in cases)],
+           "batched_ms": batched_s * 1e3, "sequential_ms": seq_s * 1e3,
+           "speedup_vs_sequential": seq_s / batched_s, "setup_s": setup_s,
+           "iterations_min_max": [min(it), max(it)], "all_converged": rc == 0 and seq_ok,
+           "max_relres_true": max(i["relres_true"] for i in infos),
+           "gdofs": total_L * sum(it) / len(it) / batched_s / 1e9,
+           "stages": sem.sem_batch_get_option(b, "stages"),
+           "grid": sem.sem_batch_get_option(b, "grid"),
+           "launches_per_solve": infos[0]["launches"]}
+    sem.sem_batch_destroy(b)
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -142,6 +199,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched leg")
     ap.add_argument("--profile", action="store_true",
                     help="small run for ncu captures: 3 fixed mixed iterations + 2 FP32 operator calls")
     args = ap.parse_args()
@@ -299,6 +357,8 @@ def main():
                           "ax_tune_ms_pcg_2")},
             "gpu_launches": launches,
         }
+        if not args.no_batched:
+            line["batched"] = batched_leg(sem, torch)
         if not args.no_cpu and world >= 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))

@@ -189,6 +189,28 @@ int sem_pcg_solve(sem_handle h, const double* f, const double* x0, double* x,
 int sem_pcg_solve_ex(sem_handle h, const double* f, const double* x0, double* x,
                      const sem_solve_opts* opts, sem_info* info);
 
+/* ---- Batched solves: many independent problems of uneven E and N ----
+ * sem_batch_setup builds one sub-handle per problem (meshes[i], Ns[i]; odd
+ * N in 1..9), all on one stream, and the work lists of the batched kernels:
+ * each phase of a PCG iteration (operator, gather-scatter, update + dots) is
+ * ONE persistent launch over every problem's work items, and chunks of
+ * iterations are replayed as a CUDA graph.  A project autotuner picks the
+ * operator's pipeline depth and grid at set-up.  The solve is the mixed
+ * path with reliable updates (as sem_pcg_solve_ex, refine_mode 0), per
+ * problem; f[i], x[i] are device pointers to problem i's FP64 vectors,
+ * infos[i] receives problem i's outcome.  sem_batch_problem returns the
+ * sub-handle of problem i (owned by the batch) for sem_rhs, sem_ax, ...
+ * Returns the worst per-problem status (0 when all converged). */
+typedef struct sem_batch_s* sem_batch;
+int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count, void* stream,
+                    sem_batch* out);
+int sem_batch_problem(sem_batch b, int i, sem_handle* out);
+int sem_batch_pcg_solve(sem_batch b, const double* const* f, double* const* x,
+                        const sem_solve_opts* opts, sem_info* infos);
+/* keys: "stages", "grid", "work_items", "launches", "tune_ms_s<2|3>_b<1..4>" */
+int sem_batch_get_option(sem_batch b, const char* key, double* value);
+void sem_batch_destroy(sem_batch b);
+
 /* Allocation-free weighted dot product: *result = sum_i a_i c_i b_i over n
  * FP64 values, the same quantity as sem_glsc3 with the weights passed in.
  * The paper has no counterpart: this entry point exists for callers that

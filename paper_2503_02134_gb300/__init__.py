@@ -87,6 +87,13 @@ def _load():
                                  ctypes.POINTER(sem_info)]),
         "sem_set_option": (i, [h, ctypes.c_char_p, ctypes.c_int64]),
         "sem_glsc3_noalloc": (i, [vp, vp, vp, ctypes.c_int64, vp, vp]),
+        "sem_batch_setup": (i, [ctypes.POINTER(sem_mesh), ctypes.POINTER(i), i, vp,
+                                ctypes.POINTER(h)]),
+        "sem_batch_problem": (i, [h, i, ctypes.POINTER(h)]),
+        "sem_batch_pcg_solve": (i, [h, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(sem_solve_opts), ctypes.POINTER(sem_info)]),
+        "sem_batch_get_option": (i, [h, ctypes.c_char_p, ctypes.POINTER(d)]),
+        "sem_batch_destroy": (None, [h]),
         "sem_get_option": (i, [h, ctypes.c_char_p, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
@@ -99,7 +106,9 @@ def _load():
 _lib = _load()
 EXPORTED = ("sem_setup", "sem_destroy", "sem_last_error", "sem_get_sizes", "sem_ax",
             "sem_ax_local", "sem_gs", "sem_glsc3", "sem_get_field", "sem_rhs", "sem_pcg_solve",
-            "sem_pcg_solve_ex", "sem_set_option", "sem_get_option", "sem_glsc3_noalloc")
+            "sem_pcg_solve_ex", "sem_set_option", "sem_get_option", "sem_glsc3_noalloc",
+            "sem_batch_setup", "sem_batch_problem", "sem_batch_pcg_solve", "sem_batch_get_option",
+            "sem_batch_destroy")
 
 
 class SemError(RuntimeError):
@@ -195,6 +204,41 @@ def sem_glsc3_noalloc(a, b, c, n, result, stream=None):
     """Allocation-free sum_i a_i c_i b_i into the device double `result`."""
     return _check(_lib.sem_glsc3_noalloc(_ptr(a), _ptr(b), _ptr(c), int(n), _ptr(result), stream),
                   "sem_glsc3_noalloc")
+
+
+def sem_batch_setup(meshes, Ns, stream=None):
+    count = len(meshes)
+    arr = (sem_mesh * count)(*meshes)
+    ns = (ctypes.c_int * count)(*Ns)
+    b = ctypes.c_void_p()
+    _check(_lib.sem_batch_setup(arr, ns, count, stream, ctypes.byref(b)), "sem_batch_setup")
+    return b
+
+
+def sem_batch_problem(b, i):
+    h = ctypes.c_void_p()
+    _check(_lib.sem_batch_problem(b, i, ctypes.byref(h)), "sem_batch_problem")
+    return h
+
+
+def sem_batch_pcg_solve(b, fs, xs, opts: sem_solve_opts):
+    count = len(fs)
+    fa = (ctypes.c_void_p * count)(*[_ptr(t) for t in fs])
+    xa = (ctypes.c_void_p * count)(*[_ptr(t) for t in xs])
+    infos = (sem_info * count)()
+    rc = _check(_lib.sem_batch_pcg_solve(b, fa, xa, ctypes.byref(opts), infos),
+                "sem_batch_pcg_solve")
+    return rc, [infos[i].as_dict() for i in range(count)]
+
+
+def sem_batch_get_option(b, key: str) -> float:
+    out = ctypes.c_double()
+    _check(_lib.sem_batch_get_option(b, key.encode(), ctypes.byref(out)), "sem_batch_get_option")
+    return out.value
+
+
+def sem_batch_destroy(b):
+    _lib.sem_batch_destroy(b)
 
 
 def sem_set_option(h, key: str, value: int):

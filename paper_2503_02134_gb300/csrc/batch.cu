@@ -1,0 +1,834 @@
+// Many independent SEM Poisson problems (uneven E and N) solved together:
+// every phase of a PCG iteration is ONE persistent launch over a work list
+// that spans all problems, and chunks of iterations are replayed as a CUDA
+// graph.  The per-iteration arithmetic is that of the single-problem mixed
+// path (the paper's CG loop, Sec. 3.1; FP32 operator with FP64-quality
+// gather-scatter sums and dots, Sec. 3.3 and 4.3): the batched operator
+// kernel runs the same element computation as ax_tma_kernel for whichever
+// order the item's problem has, the gather-scatter and update kernels run
+// the single-problem code per chunk / per item.  Reductions are per problem
+// (one partial per work item, summed in item order by the last item to
+// finish), so each problem's result does not depend on the batch it is in.
+#include <algorithm>
+#include <vector>
+
+#include "ax_tma.cuh"
+#include "pcg.cuh"
+
+namespace sem {
+
+int launch_gs(Handle& h, sem_precision p, void* v);
+
+struct BatchProb {
+  float* r;
+  const float* minv;
+  float* p;
+  float* w;
+  float* x;
+  const float* G;
+  const float* D;
+  const uint8_t* faces;
+  const uint8_t* cw;
+  const int* slots;
+  PcgScalars* scal;
+  double* ax_part;   // one partial per element group
+  double* up_part;   // two partials per update item
+  int64_t E, L;
+  int n, epb, ngroups, nupd;
+};
+
+constexpr int kBatchThreads = 128;
+constexpr int kBatchStageFloats = 9216;   // max over even n <= 10 of 9 * EPB * n^3
+constexpr int kBatchWorkFloats = 1024;    // max over even n <= 10 of EPB * n^3
+constexpr int kUpdItem4 = 1024;           // float4 per update work item (4096 values)
+
+template <int n>
+constexpr int batch_epb() {
+  return (kBatchThreads / (n * n)) > 0 ? kBatchThreads / (n * n) : 1;
+}
+
+inline int batch_epb_of(int n) { return std::max(1, kBatchThreads / (n * n)); }
+
+template <int NS>
+constexpr size_t batch_smem_bytes() {
+  return sizeof(float) * ((size_t)NS * kBatchStageFloats + 2 * kBatchWorkFloats) +
+         NS * sizeof(uint64_t);
+}
+
+// One element group of problem P in PCG mode, data staged in `sb`
+// (r | J^{-1} | p_old | G, each EPB*n^3 floats (G: 6x)).  Returns this
+// block's partial of pap = sum p (A_L p) (valid in thread 0).
+template <int n>
+__device__ double batch_group(const BatchProb& P, int64_t g, float* sb, float* sr, float* ss,
+                              float (*sD)[11], double* sh_red) {
+  constexpr int n2 = n * n, n3 = n * n * n, EPB = batch_epb<n>();
+  constexpr int SV = EPB * n3;
+  const int tid = threadIdx.x;
+  const int le = tid / n2;
+  const int ij = tid - le * n2;
+  const int i = ij % n, j = ij / n;
+  const bool lane_ok = le < EPB;
+  const int ir = lane_ok ? i : 0, jr = lane_ok ? j : 0, ler = lane_ok ? le : 0;
+  for (int q = tid; q < n2; q += blockDim.x) sD[q / n][q % n] = P.D[q];
+  __syncthreads();
+  float Di[n], Dj[n], DiT[n], DjT[n];
+#pragma unroll
+  for (int l = 0; l < n; ++l) {
+    Di[l] = sD[ir][l];
+    Dj[l] = sD[jr][l];
+    DiT[l] = sD[l][ir];
+    DjT[l] = sD[l][jr];
+  }
+  const float beta = (float)P.scal->beta;
+  float* const su_e = sb + 2 * SV + ler * n3;
+  const float* const Gs = sb + 3 * SV + ler * 6 * n3 + ij;
+  float* const sr_e = sr + ler * n3;
+  float* const ss_e = ss + ler * n3;
+  const int64_t e = g * EPB + le;
+  const bool act = lane_ok && e < P.E;
+  DotAcc<float, kDotDot2> acc;
+
+  float ureg[n];
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    const int si = k * n2 + ij;
+    const float v = sb[SV + ler * n3 + si] * sb[ler * n3 + si] + beta * su_e[si];
+    if (lane_ok) su_e[si] = v;
+    if (act) P.p[e * n3 + si] = v;
+    ureg[k] = v;
+  }
+  __syncthreads();
+  float wreg[n];
+#pragma unroll
+  for (int k = 0; k < n; ++k) wreg[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    float ur = 0.f, us = 0.f, ut = 0.f;
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+      ur += Di[l] * su_e[k * n2 + jr * n + l];
+      us += Dj[l] * su_e[k * n2 + l * n + ir];
+      ut += sD[k][l] * ureg[l];
+    }
+    const float g0 = Gs[0 * n3 + k * n2], g1 = Gs[1 * n3 + k * n2], g2 = Gs[2 * n3 + k * n2];
+    const float g3 = Gs[3 * n3 + k * n2], g4 = Gs[4 * n3 + k * n2], g5 = Gs[5 * n3 + k * n2];
+    const float vr = g0 * ur + g3 * us + g4 * ut;
+    const float vs = g3 * ur + g1 * us + g5 * ut;
+    const float vt = g4 * ur + g5 * us + g2 * ut;
+    if (lane_ok) {
+      sr_e[k * n2 + ij] = vr;
+      ss_e[k * n2 + ij] = vs;
+    }
+#pragma unroll
+    for (int kk = 0; kk < n; ++kk) wreg[kk] += sD[k][kk] * vt;
+  }
+  __syncthreads();
+  const uint8_t f = act ? P.faces[e] : uint8_t(0);
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    float wv = wreg[k];
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+      wv += DiT[l] * sr_e[k * n2 + jr * n + l];
+      wv += DjT[l] * ss_e[k * n2 + l * n + ir];
+    }
+    if (on_dirichlet(f, i, j, k, n - 1)) wv = 0.f;
+    if (act) {
+      P.w[e * n3 + k * n2 + ij] = wv;
+      acc.add(ureg[k], wv);
+    }
+  }
+  return block_sum<kDotDot2>(acc.value(), sh_red);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kBatchThreads)
+    batch_ax_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ items,
+                    int nitems, int* __restrict__ err) {
+  extern __shared__ __align__(128) float smem_f[];
+  float* const stage0 = smem_f;
+  float* const sr = smem_f + NS * kBatchStageFloats;
+  float* const ss = sr + kBatchWorkFloats;
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(ss + kBatchWorkFloats);
+  __shared__ float sD[10][11];
+  __shared__ double sh_red[kBatchThreads / 32];
+  __shared__ int s_item[NS];    // work item staged on each stage, -1 = none
+  __shared__ int s_phase[NS];   // completed barrier phases per stage
+  __shared__ bool s_last;
+  const int tid = threadIdx.x;
+
+  auto issue = [&](int st, int it) {   // thread 0 only
+    const int2 itm = items[it];
+    const BatchProb& P = probs[itm.x];
+    if (P.scal->done) {
+      s_item[st] = -1;
+      return;
+    }
+    const int n3 = P.n * P.n * P.n;
+    const int64_t e0 = (int64_t)itm.y * P.epb;
+    const int64_t cnt = P.E - e0 < P.epb ? P.E - e0 : P.epb;
+    const uint32_t vb = (uint32_t)(cnt * n3 * 4);
+    const int SV = P.epb * n3;
+    float* dst = stage0 + st * kBatchStageFloats;
+    s_item[st] = it;
+    mbar_arrive_expect_tx(&bar[st], 9 * vb);
+    bulk_load(dst, P.r + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + SV, P.minv + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + 2 * SV, P.p + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + 3 * SV, P.G + e0 * 6 * n3, 6 * vb, &bar[st]);
+  };
+
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(&bar[q], 1);
+      s_phase[q] = 0;
+    }
+    fence_mbar_init();
+    for (int q = 0; q < NS; ++q) {
+      const int it = blockIdx.x + q * gridDim.x;
+      if (it < nitems) issue(q, it); else s_item[q] = -1;
+    }
+  }
+  __syncthreads();
+
+  int t = 0;
+  bool aborted = false;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++t) {
+    const int st = t % NS;
+    const int mine = s_item[st];
+    bool ok = true;
+    if (mine >= 0) ok = mbar_wait_bounded(&bar[st], (uint32_t)(s_phase[st] & 1));
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    if (mine >= 0) {
+      const int2 itm = items[mine];
+      const BatchProb& P = probs[itm.x];
+      float* sb = stage0 + st * kBatchStageFloats;
+      double part = 0.0;
+      switch (P.n) {
+        case 2: part = batch_group<2>(P, itm.y, sb, sr, ss, sD, sh_red); break;
+        case 4: part = batch_group<4>(P, itm.y, sb, sr, ss, sD, sh_red); break;
+        case 6: part = batch_group<6>(P, itm.y, sb, sr, ss, sD, sh_red); break;
+        case 8: part = batch_group<8>(P, itm.y, sb, sr, ss, sD, sh_red); break;
+        default: part = batch_group<10>(P, itm.y, sb, sr, ss, sD, sh_red); break;
+      }
+      if (tid == 0) {
+        P.ax_part[itm.y] = part;
+        __threadfence();
+        const unsigned int c = atomicAdd(&P.scal->counter[0], 1u);
+        s_last = (c == (unsigned int)P.ngroups - 1u);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        double s = 0.0;
+        for (int b = tid; b < P.ngroups; b += blockDim.x) s += __ldcg(P.ax_part + b);
+        const double pap = block_sum<kDotDot2>(s, sh_red);
+        if (tid == 0) {
+          P.scal->pap = pap;
+          if (!(pap > 0.0) || !isfinite(pap)) {
+            // the update kernel ends the solve of this problem
+            P.scal->status = SEM_BREAKDOWN;
+            P.scal->alpha = 0.0;
+          } else {
+            P.scal->alpha = P.scal->rtz / pap;
+          }
+          P.scal->counter[0] = 0u;
+        }
+      }
+    }
+    __syncthreads();   // stage st, sr/ss and sD are free again
+    if (tid == 0) {
+      if (mine >= 0) ++s_phase[st];
+      const int next = it + NS * gridDim.x;
+      if (next < nitems) {
+        fence_proxy_async_smem();
+        issue(st, next);
+      } else {
+        s_item[st] = -1;
+      }
+    }
+    __syncthreads();
+  }
+  if (aborted && tid == 0) {
+    atomicExch(err, 1);
+    for (int q = 0; q < NS; ++q)
+      if (s_item[q] >= 0) mbar_wait_bounded(&bar[q], (uint32_t)(s_phase[q] & 1));
+  }
+}
+
+// Gather-scatter of every problem's chunks (same arithmetic as
+// gs_bucket_kernel with error-free TwoSum accumulation).
+__global__ void __launch_bounds__(256)
+    batch_gs_kernel(const BatchProb* __restrict__ probs, const int* __restrict__ chunk_prob,
+                    const int2* __restrict__ chunk_desc, int64_t nchunks) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks;
+       c += nwarps) {
+    const BatchProb& P = probs[__ldg(chunk_prob + c)];
+    if (P.scal->done) continue;
+    const int2 d = __ldg(chunk_desc + c);
+    const int m = d.x;
+    const int* sl = P.slots + d.y + lane;
+    float* v = P.w;
+    float s = 0.f, cc = 0.f;
+    for (int q = 0; q < m; ++q) {
+      const int id = __ldg(sl + 32 * q);
+      if (id >= 0) {
+        const float x = v[id];
+        const float t = __fadd_rn(s, x);
+        const float z = __fsub_rn(t, s);
+        cc = __fadd_rn(cc, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+        s = t;
+      }
+    }
+    const float out = __fadd_rn(s, cc);
+    for (int q = 0; q < m; ++q) {
+      const int id = __ldg(sl + 32 * q);
+      if (id >= 0) v[id] = out;
+    }
+  }
+}
+
+__device__ __forceinline__ float batch_weight(uint8_t m) { return m ? __frcp_rn((float)m) : 0.f; }
+
+// add2s2 x 2 + glsc3(r,c,r) + glsc3(r,c,z) for one range of every problem.
+__global__ void __launch_bounds__(256)
+    batch_update_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ uitems,
+                        int nuitems) {
+  __shared__ double sh[8];
+  __shared__ bool s_last;
+  for (int ui = blockIdx.x; ui < nuitems; ui += gridDim.x) {
+    const int2 itm = uitems[ui];
+    const BatchProb& P = probs[itm.x];
+    if (P.scal->done) continue;   // uniform for the block
+    const float alpha = (float)P.scal->alpha;
+    const int64_t n4 = P.L >> 2;
+    const int64_t q0 = (int64_t)itm.y * kUpdItem4;
+    const int64_t q1 = q0 + kUpdItem4 < n4 ? q0 + kUpdItem4 : n4;
+    DotAcc<float, kDotDot2> a_rr, a_rz;
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+      float4 xv = reinterpret_cast<float4*>(P.x)[q];
+      float4 rv = reinterpret_cast<float4*>(P.r)[q];
+      const float4 pv = reinterpret_cast<const float4*>(P.p)[q];
+      const float4 wv = reinterpret_cast<const float4*>(P.w)[q];
+      const float4 mv = __ldg(reinterpret_cast<const float4*>(P.minv) + q);
+      const uchar4 cv = __ldg(reinterpret_cast<const uchar4*>(P.cw) + q);
+      xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
+      rv.x -= alpha * wv.x; rv.y -= alpha * wv.y; rv.z -= alpha * wv.z; rv.w -= alpha * wv.w;
+      reinterpret_cast<float4*>(P.x)[q] = xv;
+      reinterpret_cast<float4*>(P.r)[q] = rv;
+      float c;
+      c = batch_weight(cv.x) * rv.x; a_rr.add(c, rv.x); a_rz.add(c, mv.x * rv.x);
+      c = batch_weight(cv.y) * rv.y; a_rr.add(c, rv.y); a_rz.add(c, mv.y * rv.y);
+      c = batch_weight(cv.z) * rv.z; a_rr.add(c, rv.z); a_rz.add(c, mv.z * rv.z);
+      c = batch_weight(cv.w) * rv.w; a_rr.add(c, rv.w); a_rz.add(c, mv.w * rv.w);
+    }
+    const double v0 = block_sum<kDotDot2>(a_rr.value(), sh);
+    const double v1 = block_sum<kDotDot2>(a_rz.value(), sh);
+    if (threadIdx.x == 0) {
+      P.up_part[2 * itm.y] = v0;
+      P.up_part[2 * itm.y + 1] = v1;
+      __threadfence();
+      const unsigned int c = atomicAdd(&P.scal->counter[1], 1u);
+      s_last = (c == (unsigned int)P.nupd - 1u);
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      double a = 0.0, b = 0.0;
+      for (int q = threadIdx.x; q < P.nupd; q += blockDim.x) {
+        a += __ldcg(P.up_part + 2 * q);
+        b += __ldcg(P.up_part + 2 * q + 1);
+      }
+      const double rtr = block_sum<kDotDot2>(a, sh);
+      const double rtz = block_sum<kDotDot2>(b, sh);
+      if (threadIdx.x == 0) {
+        if (P.scal->status == SEM_BREAKDOWN) {
+          P.scal->done = 1;
+        } else {
+          finish_iteration(P.scal, rtr, rtz, nullptr);
+        }
+        P.scal->counter[1] = 0u;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void batch_gather_scalars(const BatchProb* probs, int count, PcgScalars* out) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < count; p += gridDim.x * blockDim.x)
+    out[p] = *probs[p].scal;
+}
+
+}  // namespace sem
+
+// ------------------------------------------------------------------ host side
+struct sem_batch_s {
+  std::vector<sem_handle_s*> subs;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int count = 0;
+  sem::BatchProb* d_probs = nullptr;
+  int2* d_items = nullptr;
+  int nitems = 0;
+  int* d_chunk_prob = nullptr;
+  int2* d_chunk_desc = nullptr;
+  int64_t nchunks = 0;
+  int2* d_uitems = nullptr;
+  int nuitems = 0;
+  double* d_part = nullptr;
+  sem::PcgScalars* d_scal_all = nullptr;
+  sem::PcgScalars* h_scal_all = nullptr;
+  int* d_err = nullptr;
+  int ns = 2;            // pipeline stages of the batched operator (autotuned)
+  int grid_ax = 0;       // blocks of the batched operator (autotuned)
+  float tune_ms[2][4] = {};
+  cudaGraphExec_t graph = nullptr;
+  int graph_chunk = 0;
+  int64_t graph_nodes = 0;
+  int64_t launches = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace sem {
+
+static int batch_launch_ax(sem_batch_s& b, int ns, int grid) {
+  if (ns == 3) {
+    batch_ax_kernel<3><<<grid, kBatchThreads, batch_smem_bytes<3>(), b.stream>>>(
+        b.d_probs, b.d_items, b.nitems, b.d_err);
+  } else {
+    batch_ax_kernel<2><<<grid, kBatchThreads, batch_smem_bytes<2>(), b.stream>>>(
+        b.d_probs, b.d_items, b.nitems, b.d_err);
+  }
+  ++b.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+static int batch_enqueue_iteration(sem_batch_s& b) {
+  int rc = batch_launch_ax(b, b.ns, b.grid_ax);
+  if (rc) return rc;
+  int num_sms = b.subs[0]->num_sms;
+  const int64_t gs_blocks = std::min<int64_t>((b.nchunks + 7) / 8, (int64_t)num_sms * 8);
+  if (b.nchunks > 0) {
+    batch_gs_kernel<<<(int)std::max<int64_t>(gs_blocks, 1), 256, 0, b.stream>>>(
+        b.d_probs, b.d_chunk_prob, b.d_chunk_desc, b.nchunks);
+    ++b.launches;
+    SEM_CUDA(cudaGetLastError());
+  }
+  const int up_blocks = std::min(b.nuitems, num_sms * 8);
+  batch_update_kernel<<<std::max(up_blocks, 1), 256, 0, b.stream>>>(b.d_probs, b.d_uitems,
+                                                                     b.nuitems);
+  ++b.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+static int batch_run_chunk(sem_batch_s& b, int chunk, bool use_graph) {
+  if (!use_graph) {
+    for (int q = 0; q < chunk; ++q) {
+      int rc = batch_enqueue_iteration(b);
+      if (rc) return rc;
+    }
+    return 0;
+  }
+  if (!b.graph || b.graph_chunk != chunk) {
+    if (b.graph) cudaGraphExecDestroy(b.graph);
+    b.graph = nullptr;
+    cudaGraph_t g = nullptr;
+    const int64_t before = b.launches;
+    SEM_CUDA(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    for (int q = 0; q < chunk && !rc; ++q) rc = batch_enqueue_iteration(b);
+    cudaError_t e = cudaStreamEndCapture(b.stream, &g);
+    b.graph_nodes = b.launches - before;
+    b.launches = before;
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    b.graph_chunk = chunk;
+  }
+  SEM_CUDA(cudaGraphLaunch(b.graph, b.stream));
+  b.launches += b.graph_nodes;
+  return 0;
+}
+
+static int batch_read_scalars(sem_batch_s& b) {
+  batch_gather_scalars<<<(b.count + 63) / 64, 64, 0, b.stream>>>(b.d_probs, b.count, b.d_scal_all);
+  ++b.launches;
+  SEM_CUDA(cudaGetLastError());
+  SEM_CUDA(cudaMemcpyAsync(b.h_scal_all, b.d_scal_all, sizeof(PcgScalars) * b.count,
+                           cudaMemcpyDeviceToHost, b.stream));
+  SEM_CUDA(cudaStreamSynchronize(b.stream));
+  return 0;
+}
+
+// Project autotuner of the batched operator: pipeline stages x blocks per SM,
+// timed with CUDA events on the batch's own work list.
+static int batch_autotune(sem_batch_s& b) {
+  int num_sms = b.subs[0]->num_sms;
+  cudaEvent_t e0, e1;
+  SEM_CUDA(cudaEventCreate(&e0));
+  SEM_CUDA(cudaEventCreate(&e1));
+  for (int p = 0; p < b.count; ++p) {
+    Handle& h = *b.subs[p];
+    SEM_CUDA(cudaMemsetAsync(h.r32, 0x3f, sizeof(float) * h.L, b.stream));
+    SEM_CUDA(cudaMemsetAsync(h.p32, 0x3f, sizeof(float) * h.L, b.stream));
+    int rc = launch_scal_setup(h, h.scal, 0.0, 1, 0, 0);
+    if (rc) return rc;
+  }
+  float best = 1e30f;
+  int best_ns = 2, best_grid = num_sms;
+  for (int nsv = 0; nsv < 2; ++nsv) {
+    const int ns = nsv == 0 ? 2 : 3;
+    auto kern = ns == 2 ? batch_ax_kernel<2> : batch_ax_kernel<3>;
+    const size_t smem = ns == 2 ? batch_smem_bytes<2>() : batch_smem_bytes<3>();
+    SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem));
+    per_sm = std::max(per_sm, 1);
+    for (int bps = 1; bps <= std::min(per_sm, 4); ++bps) {
+      const int grid = std::min(num_sms * bps, std::max(b.nitems, 1));
+      int rc = batch_launch_ax(b, ns, grid);
+      if (rc) return rc;
+      SEM_CUDA(cudaEventRecord(e0, b.stream));
+      for (int q = 0; q < 2 && !rc; ++q) rc = batch_launch_ax(b, ns, grid);
+      if (rc) return rc;
+      SEM_CUDA(cudaEventRecord(e1, b.stream));
+      SEM_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      SEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ms *= 0.5f;
+      if (bps <= 4) b.tune_ms[nsv][bps - 1] = ms;
+      if (ms < best) {
+        best = ms;
+        best_ns = ns;
+        best_grid = grid;
+      }
+    }
+  }
+  b.ns = best_ns;
+  b.grid_ax = best_grid;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int p = 0; p < b.count; ++p) {
+    int rc = launch_scal_setup(*b.subs[p], b.subs[p]->scal, 0.0, 1, 0, 0);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+static void batch_free(sem_batch_s* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto* s : b->subs) sem_destroy(s);
+  void* ptrs[] = {b->d_probs, b->d_items, b->d_chunk_prob, b->d_chunk_desc, b->d_uitems,
+                  b->d_part, b->d_scal_all, b->d_err};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (b->h_scal_all) cudaFreeHost(b->h_scal_all);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count, void* stream,
+                               sem_batch* out) {
+  if (!meshes || !Ns || !out || count < 1) {
+    set_error("sem_batch_setup: null argument or count < 1");
+    return SEM_EINVAL;
+  }
+  *out = nullptr;
+  for (int p = 0; p < count; ++p) {
+    if (Ns[p] < 1 || Ns[p] > 9 || Ns[p] % 2 == 0) {
+      set_error("sem_batch_setup: the batched solver takes odd N in 1..9 (even n <= 10)");
+      return SEM_EINVAL;
+    }
+  }
+  sem_batch_s* b = new sem_batch_s();
+  auto fail = [&](int code) {
+    batch_free(b);
+    return code;
+  };
+  cudaError_t ce;
+  if (stream == nullptr) {
+    if ((ce = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return fail(cuda_fail(ce, "cudaStreamCreate"));
+    b->own_stream = true;
+  } else {
+    b->stream = (cudaStream_t)stream;
+  }
+  b->count = count;
+  int rc;
+  for (int p = 0; p < count; ++p) {
+    sem_handle h = nullptr;
+    if ((rc = sem_setup(&meshes[p], Ns[p], 0, b->stream, &h))) return fail(rc);
+    b->subs.push_back(h);
+  }
+  // work lists
+  std::vector<BatchProb> probs(count);
+  std::vector<int2> items, uitems;
+  std::vector<int> chunk_prob;
+  std::vector<int64_t> ax_off(count), up_off(count);
+  int64_t part_total = 0;
+  for (int p = 0; p < count; ++p) {
+    Handle& h = *b->subs[p];
+    BatchProb& P = probs[p];
+    P.r = h.r32;
+    P.minv = h.minv32;
+    P.p = h.p32;
+    P.w = h.w32;
+    P.x = h.x32;
+    P.G = h.G32;
+    P.D = h.D32;
+    P.faces = h.bfaces;
+    P.cw = h.cw8;
+    P.slots = h.gs_slots;
+    P.scal = h.scal;
+    P.E = h.E;
+    P.L = h.L;
+    P.n = h.n;
+    P.epb = batch_epb_of(h.n);
+    P.ngroups = (int)((h.E + P.epb - 1) / P.epb);
+    P.nupd = (int)(((h.L >> 2) + kUpdItem4 - 1) / kUpdItem4);
+    ax_off[p] = part_total;
+    part_total += P.ngroups;
+    up_off[p] = part_total;
+    part_total += 2 * (int64_t)P.nupd;
+    b->nchunks += h.n_chunks;
+  }
+  // interleave problems in the work lists so every launch spreads over all of them
+  {
+    std::vector<int> next_g(count, 0), next_u(count, 0);
+    bool more = true;
+    while (more) {
+      more = false;
+      for (int p = 0; p < count; ++p) {
+        for (int q = 0; q < 8 && next_g[p] < probs[p].ngroups; ++q) items.push_back(make_int2(p, next_g[p]++));
+        for (int q = 0; q < 2 && next_u[p] < probs[p].nupd; ++q) uitems.push_back(make_int2(p, next_u[p]++));
+        more = more || next_g[p] < probs[p].ngroups || next_u[p] < probs[p].nupd;
+      }
+    }
+  }
+  b->nitems = (int)items.size();
+  b->nuitems = (int)uitems.size();
+  if ((ce = cudaMalloc((void**)&b->d_part, sizeof(double) * std::max<int64_t>(part_total, 1))) !=
+          cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_probs, sizeof(BatchProb) * count)) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_items, sizeof(int2) * std::max(b->nitems, 1))) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_uitems, sizeof(int2) * std::max(b->nuitems, 1))) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_chunk_prob, sizeof(int) * std::max<int64_t>(b->nchunks, 1))) !=
+          cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_chunk_desc, sizeof(int2) * std::max<int64_t>(b->nchunks, 1))) !=
+          cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_scal_all, sizeof(PcgScalars) * count)) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_err, sizeof(int))) != cudaSuccess ||
+      (ce = cudaMallocHost((void**)&b->h_scal_all, sizeof(PcgScalars) * count)) != cudaSuccess ||
+      (ce = cudaEventCreate(&b->ev0)) != cudaSuccess || (ce = cudaEventCreate(&b->ev1)) != cudaSuccess)
+    return fail(cuda_fail(ce, "sem_batch_setup"));
+  for (int p = 0; p < count; ++p) {
+    probs[p].ax_part = b->d_part + ax_off[p];
+    probs[p].up_part = b->d_part + up_off[p];
+  }
+  // concatenated gather-scatter chunk list (device to device, per problem)
+  {
+    int64_t off = 0;
+    std::vector<int> cp;
+    cp.reserve((size_t)b->nchunks);
+    for (int p = 0; p < count; ++p) {
+      Handle& h = *b->subs[p];
+      if (h.n_chunks > 0 &&
+          (ce = cudaMemcpyAsync(b->d_chunk_desc + off, h.gs_chunks, sizeof(int2) * h.n_chunks,
+                                cudaMemcpyDeviceToDevice, b->stream)) != cudaSuccess)
+        return fail(cuda_fail(ce, "cudaMemcpyAsync"));
+      for (int64_t c = 0; c < h.n_chunks; ++c) cp.push_back(p);
+      off += h.n_chunks;
+    }
+    if (b->nchunks > 0 &&
+        (ce = cudaMemcpyAsync(b->d_chunk_prob, cp.data(), sizeof(int) * cp.size(),
+                              cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
+      return fail(cuda_fail(ce, "cudaMemcpyAsync"));
+    if ((ce = cudaMemcpyAsync(b->d_probs, probs.data(), sizeof(BatchProb) * count,
+                              cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * b->nitems,
+                              cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(b->d_uitems, uitems.data(), sizeof(int2) * b->nuitems,
+                              cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream)) != cudaSuccess ||
+        (ce = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+      return fail(cuda_fail(ce, "sem_batch_setup"));
+  }
+  if ((rc = batch_autotune(*b))) return fail(rc);
+  *out = b;
+  return SEM_OK;
+}
+
+extern "C" void sem_batch_destroy(sem_batch b) { batch_free(b); }
+
+extern "C" int sem_batch_problem(sem_batch b, int i, sem_handle* out) {
+  if (!b || !out || i < 0 || i >= b->count) {
+    set_error("sem_batch_problem: invalid argument");
+    return SEM_EINVAL;
+  }
+  *out = b->subs[i];
+  return SEM_OK;
+}
+
+extern "C" int sem_batch_get_option(sem_batch b, const char* key, double* value) {
+  if (!b || !key || !value) {
+    set_error("sem_batch_get_option: null argument");
+    return SEM_EINVAL;
+  }
+  const std::string k(key);
+  if (k == "stages") *value = b->ns;
+  else if (k == "grid") *value = b->grid_ax;
+  else if (k == "work_items") *value = b->nitems;
+  else if (k == "launches") *value = (double)b->launches;
+  else if (k.rfind("tune_ms_s", 0) == 0 && k.size() == 13 && (k[9] == '2' || k[9] == '3') &&
+           k[10] == '_' && k[11] == 'b' && k[12] >= '1' && k[12] <= '4')
+    *value = b->tune_ms[k[9] - '2'][k[12] - '1'];
+  else {
+    set_error("sem_batch_get_option: unknown key: " + k);
+    return SEM_EINVAL;
+  }
+  return SEM_OK;
+}
+
+extern "C" int sem_batch_pcg_solve(sem_batch b, const double* const* f, double* const* x,
+                                   const sem_solve_opts* opts, sem_info* infos) {
+  if (!b || !f || !x || !opts) {
+    set_error("sem_batch_pcg_solve: null argument");
+    return SEM_EINVAL;
+  }
+  if (opts->precision != SEM_MIXED_FP32) {
+    set_error("sem_batch_pcg_solve: the batched solver runs the mixed precision path");
+    return SEM_EINVAL;
+  }
+  for (int p = 0; p < b->count; ++p) {
+    if (!f[p] || !x[p] || !is_device_ptr(f[p]) || !is_device_ptr(x[p])) {
+      set_error("sem_batch_pcg_solve: f[i] and x[i] must be device pointers");
+      return SEM_EINVAL;
+    }
+  }
+  const double tol = opts->tol > 0 ? opts->tol : 1e-8;
+  const int maxit = opts->maxit > 0 ? opts->maxit : 1000;
+  const int chunk = opts->chunk > 0 ? opts->chunk : 16;
+  const bool use_graph = opts->use_graph >= 0;
+  const double delta = opts->replace_factor > 0 ? opts->replace_factor : 1e-2;
+  const int P = b->count;
+  int rc;
+  const int64_t launches0 = b->launches;
+  std::vector<int> finished(P, 0), status(P, 0), repl(P, 0), slow(P, 0);
+  std::vector<double> relres_true(P, 1.0), bnorm(P, 0.0);
+  SEM_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+  SEM_CUDA(cudaEventRecord(b->ev0, b->stream));
+  int64_t sub_launch0 = 0;
+  for (int p = 0; p < P; ++p) sub_launch0 += b->subs[p]->launches;
+  // start every problem: FP64 residual, FP32 copy, scalars (x0 = 0)
+  for (int p = 0; p < P; ++p) {
+    Handle& h = *b->subs[p];
+    if ((rc = launch_masked_copy64(h, nullptr, h.x64))) return rc;
+    if ((rc = fp64_residual(h, f[p], true, &relres_true[p], &bnorm[p]))) return rc;
+    SEM_CUDA(cudaMemsetAsync(h.x32, 0, sizeof(float) * h.L, b->stream));
+    SEM_CUDA(cudaMemsetAsync(h.p32, 0, sizeof(float) * h.L, b->stream));
+    if (bnorm[p] == 0.0 || relres_true[p] <= tol) {
+      finished[p] = 1;
+      if ((rc = launch_scal_setup(h, h.scal, tol, 0, 0, 0))) return rc;
+      if ((rc = launch_set_bnorm(h, h.scal, 1.0, nullptr))) return rc;   // done = 1
+      continue;
+    }
+    if ((rc = launch_cast64to32(h, h.r64, h.b32))) return rc;
+    if ((rc = launch_scal_setup(h, h.scal, std::max(tol, delta * relres_true[p]), maxit, 0, 0)))
+      return rc;
+    if ((rc = launch_cg_init32(h, kDotDot2, h.r32, h.b32, nullptr, h.minv32, h.scal, nullptr)))
+      return rc;
+    if ((rc = launch_set_bnorm(h, h.scal, bnorm[p], nullptr))) return rc;
+  }
+  for (;;) {
+    int left = 0;
+    for (int p = 0; p < P; ++p) left += !finished[p];
+    if (!left) break;
+    if ((rc = batch_run_chunk(*b, chunk, use_graph))) return rc;
+    if ((rc = batch_read_scalars(*b))) return rc;
+    int err = 0;
+    SEM_CUDA(cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      set_error("sem_batch_pcg_solve: a bounded device wait gave up");
+      return SEM_ETIMEOUT;
+    }
+    for (int p = 0; p < P; ++p) {
+      if (finished[p] || !b->h_scal_all[p].done) continue;
+      Handle& h = *b->subs[p];
+      const PcgScalars& s = b->h_scal_all[p];
+      // fold the FP32 correction into x64 and replace the residual in FP64
+      if ((rc = launch_add32to64(h, h.x64, h.x32))) return rc;
+      SEM_CUDA(cudaMemsetAsync(h.x32, 0, sizeof(float) * h.L, b->stream));
+      const double prev = relres_true[p];
+      if ((rc = fp64_residual(h, f[p], false, &relres_true[p]))) return rc;
+      bool stop = false;
+      if (relres_true[p] <= tol) {
+        stop = true;
+      } else if (s.status == SEM_BREAKDOWN) {
+        status[p] = SEM_BREAKDOWN;
+        stop = true;
+      } else if (s.iter >= maxit) {
+        status[p] = SEM_MAXIT;
+        stop = true;
+      } else {
+        slow[p] = relres_true[p] > 0.5 * prev ? slow[p] + 1 : 0;
+        if (slow[p] >= 3 || repl[p] >= 80) {
+          status[p] = SEM_STAGNATED;
+          stop = true;
+        }
+      }
+      if (stop) {
+        finished[p] = 1;   // its scalars keep done = 1
+        continue;
+      }
+      if ((rc = launch_cg_replace32(h, kDotDot2, h.r64, h.r32, h.minv32,
+                                    std::max(tol, delta * relres_true[p]), h.scal)))
+        return rc;
+      ++repl[p];
+    }
+  }
+  SEM_CUDA(cudaEventRecord(b->ev1, b->stream));
+  if ((rc = batch_read_scalars(*b))) return rc;
+  float ms = 0.f;
+  SEM_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  int64_t sub_launch1 = 0;
+  for (int p = 0; p < P; ++p) sub_launch1 += b->subs[p]->launches;
+  int worst = 0;
+  for (int p = 0; p < P; ++p) {
+    Handle& h = *b->subs[p];
+    SEM_CUDA(cudaMemcpyAsync(x[p], h.x64, sizeof(double) * h.L, cudaMemcpyDeviceToDevice,
+                             b->stream));
+    if (infos) {
+      sem_info& in = infos[p];
+      in.iters = b->h_scal_all[p].iter;
+      in.refinements = repl[p];
+      in.status = status[p];
+      in.relres = b->h_scal_all[p].relres;
+      in.relres_true = relres_true[p];
+      in.solve_ms = ms;
+      in.launches = (b->launches - launches0) + (sub_launch1 - sub_launch0);
+    }
+    if (status[p] > worst) worst = status[p];
+  }
+  SEM_CUDA(cudaStreamSynchronize(b->stream));
+  return worst;
+}

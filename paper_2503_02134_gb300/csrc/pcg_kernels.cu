@@ -10,37 +10,6 @@ namespace sem {
 
 constexpr int kVecThreads = 256;
 
-// Scalars update after the reductions of an iteration (one thread).
-__device__ void finish_iteration(PcgScalars* s, double rtr, double rtz_new, double* hist) {
-  s->iter += 1;
-  s->rtr = rtr;
-  const double relres = sqrt(rtr) / s->bnorm;
-  s->relres = relres;
-  if (hist) hist[s->iter] = relres;
-  if (!isfinite(relres)) {
-    s->status = SEM_BREAKDOWN;
-    s->done = 1;
-  } else if (s->fixed) {
-    if (s->iter >= s->maxit) s->done = 1;
-  } else if (relres <= s->tol) {
-    s->done = 1;
-  } else if (s->iter >= s->maxit) {
-    s->status = SEM_MAXIT;
-    s->done = 1;
-  } else if (s->stag_window > 0) {
-    if (rtr < 0.81 * s->best_rtr) {   // ||r|| fell by 10 %
-      s->best_rtr = rtr;
-      s->best_it = s->iter;
-    } else if (s->iter - s->best_it >= s->stag_window) {
-      s->status = SEM_STAGNATED;
-      s->done = 1;
-    }
-  }
-  s->beta = rtz_new / s->rtz;
-  s->rtz_old = s->rtz;
-  s->rtz = rtz_new;
-}
-
 template <typename T, int DM>
 __global__ void __launch_bounds__(kVecThreads)
     cg_update_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,

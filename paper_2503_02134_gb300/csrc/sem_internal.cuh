@@ -160,6 +160,9 @@ int build_gs_buckets(Handle& h);
 int launch_glsc3(Handle& h, sem_precision p, const void* a, const void* b, double* out_dev);
 
 // solver.cu
+int read_scalars(Handle& h, PcgScalars* dev, PcgScalars* out);
+int fp64_residual(Handle& h, const double* f, bool x_is_zero, double* relres,
+                  double* bnorm = nullptr);
 int pcg_solve(Handle& h, const double* f, const double* x0, double* x, const sem_solve_opts& o,
               sem_info* info);
 

@@ -32,6 +32,36 @@ int launch_ax_local(Handle& h, sem_precision p, const void* u, void* w, const Ax
   return ax_dispatch_fp32(h, (const float*)u, (float*)w, pro, dm);
 }
 
+int read_scalars(Handle& h, PcgScalars* dev, PcgScalars* out) {
+  SEM_CUDA(cudaMemcpyAsync(h.scal_host, dev, sizeof(PcgScalars), cudaMemcpyDeviceToHost, h.stream));
+  SEM_CUDA(cudaStreamSynchronize(h.stream));
+  *out = *h.scal_host;
+  return 0;
+}
+
+// r64 = f - A64 x64 in FP64; returns ||r64||_c / ||f||_c through *relres
+// (and ||f||_c through *bnorm when asked).
+int fp64_residual(Handle& h, const double* f, bool x_is_zero, double* relres,
+                  double* bnorm) {
+  int rc;
+  if ((rc = launch_scal_setup(h, h.scal_aux, 0.0, 1, 1, 0))) return rc;
+  if (!x_is_zero) {
+    if ((rc = ax_dispatch_fp64(h, h.x64, h.w64, nullptr))) return rc;
+    if ((rc = launch_gs(h, SEM_FP64, h.w64))) return rc;
+  }
+  double* saved = h.partials;
+  h.partials = h.partials_aux;
+  rc = launch_cg_init64(h, h.r64, f, x_is_zero ? nullptr : h.w64, h.minv64, h.scal_aux, nullptr);
+  h.partials = saved;
+  if (rc) return rc;
+  PcgScalars s;
+  if ((rc = read_scalars(h, h.scal_aux, &s))) return rc;
+  *relres = s.relres;
+  if (bnorm) *bnorm = s.bnorm;
+  return 0;
+}
+
+
 namespace {
 
 // A restart of the inner FP32 recursion is forced when its residual has not
@@ -98,13 +128,6 @@ int run_chunk(Handle& h, GraphKind kind, int chunk, bool use_graph) {
   return 0;
 }
 
-int read_scalars(Handle& h, PcgScalars* dev, PcgScalars* out) {
-  SEM_CUDA(cudaMemcpyAsync(h.scal_host, dev, sizeof(PcgScalars), cudaMemcpyDeviceToHost, h.stream));
-  SEM_CUDA(cudaStreamSynchronize(h.stream));
-  *out = *h.scal_host;
-  return 0;
-}
-
 // Iterate until the device says done; returns 0 or an error.
 int iterate(Handle& h, GraphKind kind, int chunk, bool use_graph, PcgScalars* fin) {
   for (;;) {
@@ -131,28 +154,6 @@ int ensure_history(Handle& h, int maxit) {
     if (h.graph_exec[q]) cudaGraphExecDestroy(h.graph_exec[q]);
     h.graph_exec[q] = nullptr;
   }
-  return 0;
-}
-
-// r64 = f - A64 x64 in FP64; returns ||r64||_c / ||f||_c through *relres
-// (and ||f||_c through *bnorm when asked).
-int fp64_residual(Handle& h, const double* f, bool x_is_zero, double* relres,
-                  double* bnorm = nullptr) {
-  int rc;
-  if ((rc = launch_scal_setup(h, h.scal_aux, 0.0, 1, 1, 0))) return rc;
-  if (!x_is_zero) {
-    if ((rc = ax_dispatch_fp64(h, h.x64, h.w64, nullptr))) return rc;
-    if ((rc = launch_gs(h, SEM_FP64, h.w64))) return rc;
-  }
-  double* saved = h.partials;
-  h.partials = h.partials_aux;
-  rc = launch_cg_init64(h, h.r64, f, x_is_zero ? nullptr : h.w64, h.minv64, h.scal_aux, nullptr);
-  h.partials = saved;
-  if (rc) return rc;
-  PcgScalars s;
-  if ((rc = read_scalars(h, h.scal_aux, &s))) return rc;
-  *relres = s.relres;
-  if (bnorm) *bnorm = s.bnorm;
   return 0;
 }
 

@@ -70,3 +70,13 @@ def uniform_matrix(rows: int, cols: int, seed: int, scale: float = 1.0) -> np.nd
     """rows x cols values uniform in [-scale, scale) from PCG64(seed)."""
     g = np.random.Generator(np.random.PCG64(seed))
     return scale * (2.0 * g.random((rows, cols)) - 1.0)
+
+
+def batched_cases(count: int = 64, seed: int = 1, kmin: int = 8, kmax: int = 24,
+                  orders=(5, 7, 9)):
+    """Box sizes k (E = k^3) and orders N of a batch of independent problems,
+    drawn from PCG64(seed); problem i's right-hand side uses seed 1000 + i."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    ks = g.integers(kmin, kmax + 1, size=count)
+    Ns = g.choice(np.asarray(orders), size=count)
+    return [(int(k), int(N)) for k, N in zip(ks, Ns)]
