@@ -144,7 +144,8 @@ __device__ double batch_group(const BatchProb& P, int64_t g, float* sb, float* s
 template <int NS>
 __global__ void __launch_bounds__(kBatchThreads)
     batch_ax_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ items,
-                    int nitems, int* __restrict__ err) {
+                    const int* __restrict__ nitems_dev, int* __restrict__ err) {
+  const int nitems = *nitems_dev;   // active work items (compacted as problems finish)
   extern __shared__ __align__(128) float smem_f[];
   float* const stage0 = smem_f;
   float* const sr = smem_f + NS * kBatchStageFloats;
@@ -263,7 +264,8 @@ __global__ void __launch_bounds__(kBatchThreads)
 // gs_bucket_kernel with error-free TwoSum accumulation).
 __global__ void __launch_bounds__(256)
     batch_gs_kernel(const BatchProb* __restrict__ probs, const int* __restrict__ chunk_prob,
-                    const int2* __restrict__ chunk_desc, int64_t nchunks) {
+                    const int2* __restrict__ chunk_desc, const int* __restrict__ nchunks_dev) {
+  const int64_t nchunks = *nchunks_dev;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks;
@@ -298,7 +300,8 @@ __device__ __forceinline__ float batch_weight(uint8_t m) { return m ? __frcp_rn(
 // add2s2 x 2 + glsc3(r,c,r) + glsc3(r,c,z) for one range of every problem.
 __global__ void __launch_bounds__(256)
     batch_update_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ uitems,
-                        int nuitems) {
+                        const int* __restrict__ nuitems_dev) {
+  const int nuitems = *nuitems_dev;
   __shared__ double sh[8];
   __shared__ bool s_last;
   for (int ui = blockIdx.x; ui < nuitems; ui += gridDim.x) {
@@ -381,6 +384,13 @@ struct sem_batch_s {
   int2* d_uitems = nullptr;
   int nuitems = 0;
   double* d_part = nullptr;
+  int* d_counts = nullptr;   // active {work items, gs chunks, update items}
+  int* h_counts = nullptr;   // pinned staging of the above
+  int2* h_items = nullptr;   // pinned staging of the compacted lists
+  int2* h_uitems = nullptr;
+  int* h_chunk_prob = nullptr;
+  int2* h_chunk_desc = nullptr;
+  std::vector<std::vector<int2>> items_of, uitems_of, chunks_of;   // per problem
   sem::PcgScalars* d_scal_all = nullptr;
   sem::PcgScalars* h_scal_all = nullptr;
   int* d_err = nullptr;
@@ -399,10 +409,10 @@ namespace sem {
 static int batch_launch_ax(sem_batch_s& b, int ns, int grid) {
   if (ns == 3) {
     batch_ax_kernel<3><<<grid, kBatchThreads, batch_smem_bytes<3>(), b.stream>>>(
-        b.d_probs, b.d_items, b.nitems, b.d_err);
+        b.d_probs, b.d_items, b.d_counts, b.d_err);
   } else {
     batch_ax_kernel<2><<<grid, kBatchThreads, batch_smem_bytes<2>(), b.stream>>>(
-        b.d_probs, b.d_items, b.nitems, b.d_err);
+        b.d_probs, b.d_items, b.d_counts, b.d_err);
   }
   ++b.launches;
   SEM_CUDA(cudaGetLastError());
@@ -416,13 +426,13 @@ static int batch_enqueue_iteration(sem_batch_s& b) {
   const int64_t gs_blocks = std::min<int64_t>((b.nchunks + 7) / 8, (int64_t)num_sms * 8);
   if (b.nchunks > 0) {
     batch_gs_kernel<<<(int)std::max<int64_t>(gs_blocks, 1), 256, 0, b.stream>>>(
-        b.d_probs, b.d_chunk_prob, b.d_chunk_desc, b.nchunks);
+        b.d_probs, b.d_chunk_prob, b.d_chunk_desc, b.d_counts + 1);
     ++b.launches;
     SEM_CUDA(cudaGetLastError());
   }
   const int up_blocks = std::min(b.nuitems, num_sms * 8);
   batch_update_kernel<<<std::max(up_blocks, 1), 256, 0, b.stream>>>(b.d_probs, b.d_uitems,
-                                                                     b.nuitems);
+                                                                     b.d_counts + 2);
   ++b.launches;
   SEM_CUDA(cudaGetLastError());
   return 0;
@@ -459,6 +469,49 @@ static int batch_run_chunk(sem_batch_s& b, int chunk, bool use_graph) {
   }
   SEM_CUDA(cudaGraphLaunch(b.graph, b.stream));
   b.launches += b.graph_nodes;
+  return 0;
+}
+
+// Upload the work lists of the problems still being solved (in the same
+// interleaved order as at set-up).  Kernels read the counts from device
+// memory, so captured graphs stay valid.
+static int batch_compact(sem_batch_s& b, const std::vector<int>& active) {
+  int ni = 0, nu = 0, nc = 0;
+  const int P = b.count;
+  std::vector<size_t> gi(P, 0), ui(P, 0);
+  bool more = true;
+  while (more) {
+    more = false;
+    for (int p = 0; p < P; ++p) {
+      if (!active[p]) continue;
+      for (int q = 0; q < 8 && gi[p] < b.items_of[p].size(); ++q) b.h_items[ni++] = b.items_of[p][gi[p]++];
+      for (int q = 0; q < 2 && ui[p] < b.uitems_of[p].size(); ++q) b.h_uitems[nu++] = b.uitems_of[p][ui[p]++];
+      more = more || gi[p] < b.items_of[p].size() || ui[p] < b.uitems_of[p].size();
+    }
+  }
+  for (int p = 0; p < P; ++p) {
+    if (!active[p]) continue;
+    for (const int2& c : b.chunks_of[p]) {
+      b.h_chunk_desc[nc] = c;
+      b.h_chunk_prob[nc] = p;
+      ++nc;
+    }
+  }
+  b.h_counts[0] = ni;
+  b.h_counts[1] = nc;
+  b.h_counts[2] = nu;
+  SEM_CUDA(cudaMemcpyAsync(b.d_items, b.h_items, sizeof(int2) * std::max(ni, 1),
+                           cudaMemcpyHostToDevice, b.stream));
+  SEM_CUDA(cudaMemcpyAsync(b.d_uitems, b.h_uitems, sizeof(int2) * std::max(nu, 1),
+                           cudaMemcpyHostToDevice, b.stream));
+  SEM_CUDA(cudaMemcpyAsync(b.d_chunk_desc, b.h_chunk_desc, sizeof(int2) * std::max(nc, 1),
+                           cudaMemcpyHostToDevice, b.stream));
+  SEM_CUDA(cudaMemcpyAsync(b.d_chunk_prob, b.h_chunk_prob, sizeof(int) * std::max(nc, 1),
+                           cudaMemcpyHostToDevice, b.stream));
+  SEM_CUDA(cudaMemcpyAsync(b.d_counts, b.h_counts, sizeof(int) * 3, cudaMemcpyHostToDevice,
+                           b.stream));
+  // the pinned staging buffers are reused: wait for the copies
+  SEM_CUDA(cudaStreamSynchronize(b.stream));
   return 0;
 }
 
@@ -533,10 +586,13 @@ static void batch_free(sem_batch_s* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (auto* s : b->subs) sem_destroy(s);
   void* ptrs[] = {b->d_probs, b->d_items, b->d_chunk_prob, b->d_chunk_desc, b->d_uitems,
-                  b->d_part, b->d_scal_all, b->d_err};
+                  b->d_part, b->d_scal_all, b->d_err, b->d_counts};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  if (b->h_scal_all) cudaFreeHost(b->h_scal_all);
+  void* hptrs[] = {b->h_scal_all, b->h_counts, b->h_items, b->h_uitems, b->h_chunk_prob,
+                   b->h_chunk_desc};
+  for (void* p : hptrs)
+    if (p) cudaFreeHost(p);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -582,8 +638,6 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
   }
   // work lists
   std::vector<BatchProb> probs(count);
-  std::vector<int2> items, uitems;
-  std::vector<int> chunk_prob;
   std::vector<int64_t> ax_off(count), up_off(count);
   int64_t part_total = 0;
   for (int p = 0; p < count; ++p) {
@@ -612,67 +666,52 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
     part_total += 2 * (int64_t)P.nupd;
     b->nchunks += h.n_chunks;
   }
-  // interleave problems in the work lists so every launch spreads over all of them
-  {
-    std::vector<int> next_g(count, 0), next_u(count, 0);
-    bool more = true;
-    while (more) {
-      more = false;
-      for (int p = 0; p < count; ++p) {
-        for (int q = 0; q < 8 && next_g[p] < probs[p].ngroups; ++q) items.push_back(make_int2(p, next_g[p]++));
-        for (int q = 0; q < 2 && next_u[p] < probs[p].nupd; ++q) uitems.push_back(make_int2(p, next_u[p]++));
-        more = more || next_g[p] < probs[p].ngroups || next_u[p] < probs[p].nupd;
-      }
-    }
+  // per-problem work lists (kept on the host; the active ones are uploaded
+  // interleaved, so every launch spreads over all unfinished problems)
+  b->items_of.resize(count);
+  b->uitems_of.resize(count);
+  b->chunks_of.resize(count);
+  for (int p = 0; p < count; ++p) {
+    Handle& h = *b->subs[p];
+    for (int g = 0; g < probs[p].ngroups; ++g) b->items_of[p].push_back(make_int2(p, g));
+    for (int q = 0; q < probs[p].nupd; ++q) b->uitems_of[p].push_back(make_int2(p, q));
+    b->chunks_of[p].resize((size_t)h.n_chunks);
+    if (h.n_chunks > 0 &&
+        (ce = cudaMemcpy(b->chunks_of[p].data(), h.gs_chunks, sizeof(int2) * h.n_chunks,
+                         cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return fail(cuda_fail(ce, "cudaMemcpy"));
+    b->nitems += probs[p].ngroups;
+    b->nuitems += probs[p].nupd;
   }
-  b->nitems = (int)items.size();
-  b->nuitems = (int)uitems.size();
+  const size_t nit = std::max(b->nitems, 1), nut = std::max(b->nuitems, 1);
+  const size_t nch = (size_t)std::max<int64_t>(b->nchunks, 1);
   if ((ce = cudaMalloc((void**)&b->d_part, sizeof(double) * std::max<int64_t>(part_total, 1))) !=
           cudaSuccess ||
       (ce = cudaMalloc((void**)&b->d_probs, sizeof(BatchProb) * count)) != cudaSuccess ||
-      (ce = cudaMalloc((void**)&b->d_items, sizeof(int2) * std::max(b->nitems, 1))) != cudaSuccess ||
-      (ce = cudaMalloc((void**)&b->d_uitems, sizeof(int2) * std::max(b->nuitems, 1))) != cudaSuccess ||
-      (ce = cudaMalloc((void**)&b->d_chunk_prob, sizeof(int) * std::max<int64_t>(b->nchunks, 1))) !=
-          cudaSuccess ||
-      (ce = cudaMalloc((void**)&b->d_chunk_desc, sizeof(int2) * std::max<int64_t>(b->nchunks, 1))) !=
-          cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_items, sizeof(int2) * nit)) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_uitems, sizeof(int2) * nut)) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_chunk_prob, sizeof(int) * nch)) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_chunk_desc, sizeof(int2) * nch)) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_counts, sizeof(int) * 4)) != cudaSuccess ||
       (ce = cudaMalloc((void**)&b->d_scal_all, sizeof(PcgScalars) * count)) != cudaSuccess ||
       (ce = cudaMalloc((void**)&b->d_err, sizeof(int))) != cudaSuccess ||
       (ce = cudaMallocHost((void**)&b->h_scal_all, sizeof(PcgScalars) * count)) != cudaSuccess ||
+      (ce = cudaMallocHost((void**)&b->h_counts, sizeof(int) * 4)) != cudaSuccess ||
+      (ce = cudaMallocHost((void**)&b->h_items, sizeof(int2) * nit)) != cudaSuccess ||
+      (ce = cudaMallocHost((void**)&b->h_uitems, sizeof(int2) * nut)) != cudaSuccess ||
+      (ce = cudaMallocHost((void**)&b->h_chunk_prob, sizeof(int) * nch)) != cudaSuccess ||
+      (ce = cudaMallocHost((void**)&b->h_chunk_desc, sizeof(int2) * nch)) != cudaSuccess ||
       (ce = cudaEventCreate(&b->ev0)) != cudaSuccess || (ce = cudaEventCreate(&b->ev1)) != cudaSuccess)
     return fail(cuda_fail(ce, "sem_batch_setup"));
   for (int p = 0; p < count; ++p) {
     probs[p].ax_part = b->d_part + ax_off[p];
     probs[p].up_part = b->d_part + up_off[p];
   }
-  // concatenated gather-scatter chunk list (device to device, per problem)
-  {
-    int64_t off = 0;
-    std::vector<int> cp;
-    cp.reserve((size_t)b->nchunks);
-    for (int p = 0; p < count; ++p) {
-      Handle& h = *b->subs[p];
-      if (h.n_chunks > 0 &&
-          (ce = cudaMemcpyAsync(b->d_chunk_desc + off, h.gs_chunks, sizeof(int2) * h.n_chunks,
-                                cudaMemcpyDeviceToDevice, b->stream)) != cudaSuccess)
-        return fail(cuda_fail(ce, "cudaMemcpyAsync"));
-      for (int64_t c = 0; c < h.n_chunks; ++c) cp.push_back(p);
-      off += h.n_chunks;
-    }
-    if (b->nchunks > 0 &&
-        (ce = cudaMemcpyAsync(b->d_chunk_prob, cp.data(), sizeof(int) * cp.size(),
-                              cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
-      return fail(cuda_fail(ce, "cudaMemcpyAsync"));
-    if ((ce = cudaMemcpyAsync(b->d_probs, probs.data(), sizeof(BatchProb) * count,
-                              cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
-        (ce = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * b->nitems,
-                              cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
-        (ce = cudaMemcpyAsync(b->d_uitems, uitems.data(), sizeof(int2) * b->nuitems,
-                              cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
-        (ce = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream)) != cudaSuccess ||
-        (ce = cudaStreamSynchronize(b->stream)) != cudaSuccess)
-      return fail(cuda_fail(ce, "sem_batch_setup"));
-  }
+  if ((ce = cudaMemcpyAsync(b->d_probs, probs.data(), sizeof(BatchProb) * count,
+                            cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+      (ce = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream)) != cudaSuccess)
+    return fail(cuda_fail(ce, "sem_batch_setup"));
+  if ((rc = batch_compact(*b, std::vector<int>(count, 1)))) return fail(rc);
   if ((rc = batch_autotune(*b))) return fail(rc);
   *out = b;
   return SEM_OK;
@@ -727,7 +766,7 @@ extern "C" int sem_batch_pcg_solve(sem_batch b, const double* const* f, double* 
   }
   const double tol = opts->tol > 0 ? opts->tol : 1e-8;
   const int maxit = opts->maxit > 0 ? opts->maxit : 1000;
-  const int chunk = opts->chunk > 0 ? opts->chunk : 16;
+  const int chunk = opts->chunk > 0 ? opts->chunk : 8;
   const bool use_graph = opts->use_graph >= 0;
   const double delta = opts->replace_factor > 0 ? opts->replace_factor : 1e-2;
   const int P = b->count;
@@ -759,10 +798,20 @@ extern "C" int sem_batch_pcg_solve(sem_batch b, const double* const* f, double* 
       return rc;
     if ((rc = launch_set_bnorm(h, h.scal, bnorm[p], nullptr))) return rc;
   }
+  std::vector<int> active(P);
+  for (int p = 0; p < P; ++p) active[p] = !finished[p];
+  if ((rc = batch_compact(*b, active))) return rc;
   for (;;) {
-    int left = 0;
-    for (int p = 0; p < P; ++p) left += !finished[p];
+    int left = 0, newly = 0;
+    for (int p = 0; p < P; ++p) {
+      left += !finished[p];
+      if (finished[p] && active[p]) {
+        active[p] = 0;
+        ++newly;
+      }
+    }
     if (!left) break;
+    if (newly && (rc = batch_compact(*b, active))) return rc;
     if ((rc = batch_run_chunk(*b, chunk, use_graph))) return rc;
     if ((rc = batch_read_scalars(*b))) return rc;
     int err = 0;
