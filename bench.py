@@ -202,6 +202,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched leg")
     ap.add_argument("--profile", action="store_true",
                     help="small run for ncu captures: 3 fixed mixed iterations + 2 FP32 operator calls")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="ncu run of the 64-problem batch: one solve inside an NVTX range")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -218,6 +220,29 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     import paper_2503_02134_gb300 as sem
+
+    if args.profile_batched:
+        import sem_inputs
+        cases = sem_inputs.batched_cases()
+        b = sem.sem_batch_setup([sem.box_mesh(k, k, k, deform=True) for k, _ in cases],
+                                [N for _, N in cases])
+        fs, xs = [], []
+        for i in range(len(cases)):
+            h = sem.sem_batch_problem(b, i)
+            f = torch.empty(sem.sem_get_sizes(h).L, dtype=torch.float64, device="cuda")
+            sem.sem_rhs(h, sem.RHS_UNIFORM, 1000 + i, f)
+            fs.append(f)
+            xs.append(torch.zeros_like(f))
+        o = sem.sem_solve_opts()
+        o.tol, o.maxit, o.precision = 1e-8, 5000, sem.SEM_MIXED_FP32
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bench_profile_batched")
+        sem.sem_batch_pcg_solve(b, fs, xs, o)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        sem.sem_batch_destroy(b)
+        print(json.dumps({"profile_batched": "ok"}))
+        return 0
 
     stream = torch.cuda.Stream()
     W = WORKLOAD

@@ -56,8 +56,10 @@ constexpr size_t batch_smem_bytes() {
 }
 
 // One element group of problem P in PCG mode, data staged in `sb`
-// (r | J^{-1} | p_old | G, each EPB*n^3 floats (G: 6x)).  Returns this
-// block's partial of pap = sum p (A_L p) (valid in thread 0).
+// (r | J^{-1} | p_old | G, each EPB*n^3 floats (G: 6x)); P and D (in sD)
+// are the block's shared copies.  Returns this block's partial of
+// pap = sum p (A_L p) (valid in thread 0); on return every thread is done
+// with the stage buffer.
 template <int n>
 __device__ double batch_group(const BatchProb& P, int64_t g, float* sb, float* sr, float* ss,
                               float (*sD)[11], double* sh_red) {
@@ -69,8 +71,6 @@ __device__ double batch_group(const BatchProb& P, int64_t g, float* sb, float* s
   const int i = ij % n, j = ij / n;
   const bool lane_ok = le < EPB;
   const int ir = lane_ok ? i : 0, jr = lane_ok ? j : 0, ler = lane_ok ? le : 0;
-  for (int q = tid; q < n2; q += blockDim.x) sD[q / n][q % n] = P.D[q];
-  __syncthreads();
   float Di[n], Dj[n], DiT[n], DjT[n];
 #pragma unroll
   for (int l = 0; l < n; ++l) {
@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kBatchThreads)
   __shared__ int s_item[NS];    // work item staged on each stage, -1 = none
   __shared__ int s_phase[NS];   // completed barrier phases per stage
   __shared__ bool s_last;
+  __shared__ BatchProb sP;      // the current item's problem
   const int tid = threadIdx.x;
 
   auto issue = [&](int st, int it) {   // thread 0 only
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(kBatchThreads)
 
   int t = 0;
   bool aborted = false;
+  int cur_prob = -1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++t) {
     const int st = t % NS;
     const int mine = s_item[st];
@@ -203,55 +205,67 @@ __global__ void __launch_bounds__(kBatchThreads)
       aborted = true;
       break;
     }
+    const int next = it + NS * gridDim.x;
     if (mine >= 0) {
       const int2 itm = items[mine];
-      const BatchProb& P = probs[itm.x];
+      if (itm.x != cur_prob) {   // block-uniform: refresh the shared problem copy and D
+        cur_prob = itm.x;
+        const int* src = reinterpret_cast<const int*>(probs + itm.x);
+        for (int q = tid; q < (int)(sizeof(BatchProb) / sizeof(int)); q += blockDim.x)
+          reinterpret_cast<int*>(&sP)[q] = src[q];
+        __syncthreads();
+        const int nn = sP.n;
+        for (int q = tid; q < nn * nn; q += blockDim.x) sD[q / nn][q % nn] = sP.D[q];
+        __syncthreads();
+      }
       float* sb = stage0 + st * kBatchStageFloats;
       double part = 0.0;
-      switch (P.n) {
-        case 2: part = batch_group<2>(P, itm.y, sb, sr, ss, sD, sh_red); break;
-        case 4: part = batch_group<4>(P, itm.y, sb, sr, ss, sD, sh_red); break;
-        case 6: part = batch_group<6>(P, itm.y, sb, sr, ss, sD, sh_red); break;
-        case 8: part = batch_group<8>(P, itm.y, sb, sr, ss, sD, sh_red); break;
-        default: part = batch_group<10>(P, itm.y, sb, sr, ss, sD, sh_red); break;
+      switch (sP.n) {
+        case 2: part = batch_group<2>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
+        case 4: part = batch_group<4>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
+        case 6: part = batch_group<6>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
+        case 8: part = batch_group<8>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
+        default: part = batch_group<10>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
       }
+      // the reduction's barriers guarantee the stage is no longer read
       if (tid == 0) {
-        P.ax_part[itm.y] = part;
+        sP.ax_part[itm.y] = part;
         __threadfence();
-        const unsigned int c = atomicAdd(&P.scal->counter[0], 1u);
-        s_last = (c == (unsigned int)P.ngroups - 1u);
+        const unsigned int c = atomicAdd(&sP.scal->counter[0], 1u);
+        s_last = (c == (unsigned int)sP.ngroups - 1u);
+        ++s_phase[st];
+        if (next < nitems) {
+          fence_proxy_async_smem();
+          issue(st, next);
+        } else {
+          s_item[st] = -1;
+        }
       }
       __syncthreads();
       if (s_last) {
         __threadfence();
         double s = 0.0;
-        for (int b = tid; b < P.ngroups; b += blockDim.x) s += __ldcg(P.ax_part + b);
+        for (int b = tid; b < sP.ngroups; b += blockDim.x) s += __ldcg(sP.ax_part + b);
         const double pap = block_sum<kDotDot2>(s, sh_red);
         if (tid == 0) {
-          P.scal->pap = pap;
+          sP.scal->pap = pap;
           if (!(pap > 0.0) || !isfinite(pap)) {
             // the update kernel ends the solve of this problem
-            P.scal->status = SEM_BREAKDOWN;
-            P.scal->alpha = 0.0;
+            sP.scal->status = SEM_BREAKDOWN;
+            sP.scal->alpha = 0.0;
           } else {
-            P.scal->alpha = P.scal->rtz / pap;
+            sP.scal->alpha = sP.scal->rtz / pap;
           }
-          P.scal->counter[0] = 0u;
+          sP.scal->counter[0] = 0u;
         }
+        __syncthreads();
       }
-    }
-    __syncthreads();   // stage st, sr/ss and sD are free again
-    if (tid == 0) {
-      if (mine >= 0) ++s_phase[st];
-      const int next = it + NS * gridDim.x;
-      if (next < nitems) {
-        fence_proxy_async_smem();
-        issue(st, next);
-      } else {
-        s_item[st] = -1;
+    } else {
+      if (tid == 0) {
+        if (next < nitems) issue(st, next); else s_item[st] = -1;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
   if (aborted && tid == 0) {
     atomicExch(err, 1);
@@ -479,14 +493,26 @@ static int batch_compact(sem_batch_s& b, const std::vector<int>& active) {
   int ni = 0, nu = 0, nc = 0;
   const int P = b.count;
   std::vector<size_t> gi(P, 0), ui(P, 0);
+  // operator items: grouped by order n (one code path at a time per SM),
+  // problems of the same order interleaved 8 groups at a time
+  for (int nval = 2; nval <= 10; nval += 2) {
+    bool more = true;
+    while (more) {
+      more = false;
+      for (int p = 0; p < P; ++p) {
+        if (!active[p] || b.subs[p]->n != nval) continue;
+        for (int q = 0; q < 8 && gi[p] < b.items_of[p].size(); ++q) b.h_items[ni++] = b.items_of[p][gi[p]++];
+        more = more || gi[p] < b.items_of[p].size();
+      }
+    }
+  }
   bool more = true;
   while (more) {
     more = false;
     for (int p = 0; p < P; ++p) {
       if (!active[p]) continue;
-      for (int q = 0; q < 8 && gi[p] < b.items_of[p].size(); ++q) b.h_items[ni++] = b.items_of[p][gi[p]++];
       for (int q = 0; q < 2 && ui[p] < b.uitems_of[p].size(); ++q) b.h_uitems[nu++] = b.uitems_of[p][ui[p]++];
-      more = more || gi[p] < b.items_of[p].size() || ui[p] < b.uitems_of[p].size();
+      more = more || ui[p] < b.uitems_of[p].size();
     }
   }
   for (int p = 0; p < P; ++p) {
