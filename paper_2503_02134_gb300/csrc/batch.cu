@@ -153,31 +153,45 @@ __global__ void __launch_bounds__(kBatchThreads)
   uint64_t* const bar = reinterpret_cast<uint64_t*>(ss + kBatchWorkFloats);
   __shared__ float sD[10][11];
   __shared__ double sh_red[kBatchThreads / 32];
-  __shared__ int s_item[NS];    // work item staged on each stage, -1 = none
+  __shared__ int2 s_item[NS];   // work item staged on each stage ({-1, -1} = none)
   __shared__ int s_phase[NS];   // completed barrier phases per stage
   __shared__ bool s_last;
-  __shared__ BatchProb sP;      // the current item's problem
+  __shared__ BatchProb sP;      // the problem of the item being computed
   const int tid = threadIdx.x;
 
-  auto issue = [&](int st, int it) {   // thread 0 only
+  // every block owns one contiguous range of the work list
+  const int per = (nitems + gridDim.x - 1) / gridDim.x;
+  const int it0 = blockIdx.x * per;
+  const int it1 = min(nitems, it0 + per);
+
+  // issuing side (thread 0 only): the issuing problem's descriptor and its
+  // done flag (constant during a launch) are kept in registers
+  int ip = -1;
+  bool ip_done = true;
+  BatchProb IP;
+  auto issue = [&](int st, int it) {
     const int2 itm = items[it];
-    const BatchProb& P = probs[itm.x];
-    if (P.scal->done) {
-      s_item[st] = -1;
+    if (itm.x != ip) {
+      ip = itm.x;
+      IP = probs[ip];
+      ip_done = IP.scal->done != 0;
+    }
+    if (ip_done) {
+      s_item[st] = make_int2(-1, -1);
       return;
     }
-    const int n3 = P.n * P.n * P.n;
-    const int64_t e0 = (int64_t)itm.y * P.epb;
-    const int64_t cnt = P.E - e0 < P.epb ? P.E - e0 : P.epb;
+    const int n3 = IP.n * IP.n * IP.n;
+    const int64_t e0 = (int64_t)itm.y * IP.epb;
+    const int64_t cnt = IP.E - e0 < IP.epb ? IP.E - e0 : IP.epb;
     const uint32_t vb = (uint32_t)(cnt * n3 * 4);
-    const int SV = P.epb * n3;
+    const int SV = IP.epb * n3;
     float* dst = stage0 + st * kBatchStageFloats;
-    s_item[st] = it;
+    s_item[st] = itm;
     mbar_arrive_expect_tx(&bar[st], 9 * vb);
-    bulk_load(dst, P.r + e0 * n3, vb, &bar[st]);
-    bulk_load(dst + SV, P.minv + e0 * n3, vb, &bar[st]);
-    bulk_load(dst + 2 * SV, P.p + e0 * n3, vb, &bar[st]);
-    bulk_load(dst + 3 * SV, P.G + e0 * 6 * n3, 6 * vb, &bar[st]);
+    bulk_load(dst, IP.r + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + SV, IP.minv + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + 2 * SV, IP.p + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + 3 * SV, IP.G + e0 * 6 * n3, 6 * vb, &bar[st]);
   };
 
   if (tid == 0) {
@@ -187,27 +201,24 @@ __global__ void __launch_bounds__(kBatchThreads)
     }
     fence_mbar_init();
     for (int q = 0; q < NS; ++q) {
-      const int it = blockIdx.x + q * gridDim.x;
-      if (it < nitems) issue(q, it); else s_item[q] = -1;
+      if (it0 + q < it1) issue(q, it0 + q); else s_item[q] = make_int2(-1, -1);
     }
   }
   __syncthreads();
 
-  int t = 0;
   bool aborted = false;
   int cur_prob = -1;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++t) {
+  for (int it = it0, t = 0; it < it1; ++it, ++t) {
     const int st = t % NS;
-    const int mine = s_item[st];
+    const int2 itm = s_item[st];
     bool ok = true;
-    if (mine >= 0) ok = mbar_wait_bounded(&bar[st], (uint32_t)(s_phase[st] & 1));
+    if (itm.x >= 0) ok = mbar_wait_bounded(&bar[st], (uint32_t)(s_phase[st] & 1));
     if (__syncthreads_or(!ok)) {
       aborted = true;
       break;
     }
-    const int next = it + NS * gridDim.x;
-    if (mine >= 0) {
-      const int2 itm = items[mine];
+    const int next = it + NS;
+    if (itm.x >= 0) {
       if (itm.x != cur_prob) {   // block-uniform: refresh the shared problem copy and D
         cur_prob = itm.x;
         const int* src = reinterpret_cast<const int*>(probs + itm.x);
@@ -234,11 +245,11 @@ __global__ void __launch_bounds__(kBatchThreads)
         const unsigned int c = atomicAdd(&sP.scal->counter[0], 1u);
         s_last = (c == (unsigned int)sP.ngroups - 1u);
         ++s_phase[st];
-        if (next < nitems) {
+        if (next < it1) {
           fence_proxy_async_smem();
           issue(st, next);
         } else {
-          s_item[st] = -1;
+          s_item[st] = make_int2(-1, -1);
         }
       }
       __syncthreads();
@@ -262,7 +273,7 @@ __global__ void __launch_bounds__(kBatchThreads)
       }
     } else {
       if (tid == 0) {
-        if (next < nitems) issue(st, next); else s_item[st] = -1;
+        if (next < it1) issue(st, next); else s_item[st] = make_int2(-1, -1);
       }
       __syncthreads();
     }
@@ -270,7 +281,7 @@ __global__ void __launch_bounds__(kBatchThreads)
   if (aborted && tid == 0) {
     atomicExch(err, 1);
     for (int q = 0; q < NS; ++q)
-      if (s_item[q] >= 0) mbar_wait_bounded(&bar[q], (uint32_t)(s_phase[q] & 1));
+      if (s_item[q].x >= 0) mbar_wait_bounded(&bar[q], (uint32_t)(s_phase[q] & 1));
   }
 }
 
@@ -493,19 +504,15 @@ static int batch_compact(sem_batch_s& b, const std::vector<int>& active) {
   int ni = 0, nu = 0, nc = 0;
   const int P = b.count;
   std::vector<size_t> gi(P, 0), ui(P, 0);
-  // operator items: grouped by order n (one code path at a time per SM),
-  // problems of the same order interleaved 8 groups at a time
-  for (int nval = 2; nval <= 10; nval += 2) {
-    bool more = true;
-    while (more) {
-      more = false;
-      for (int p = 0; p < P; ++p) {
-        if (!active[p] || b.subs[p]->n != nval) continue;
-        for (int q = 0; q < 8 && gi[p] < b.items_of[p].size(); ++q) b.h_items[ni++] = b.items_of[p][gi[p]++];
-        more = more || gi[p] < b.items_of[p].size();
-      }
+  // operator items: ordered by order n, then problem, then element group,
+  // and split into one contiguous range per block: a block switches code
+  // path and problem descriptor rarely
+  for (int nval = 2; nval <= 10; nval += 2)
+    for (int p = 0; p < P; ++p) {
+      if (!active[p] || b.subs[p]->n != nval) continue;
+      for (const int2& itm : b.items_of[p]) b.h_items[ni++] = itm;
     }
-  }
+  (void)gi;
   bool more = true;
   while (more) {
     more = false;
