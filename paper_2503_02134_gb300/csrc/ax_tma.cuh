@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     float* const ss_e = ss + ler * n3;
     const int64_t e = g * EPB + le;
     const bool act = lane_ok && e < E;
+    const uint8_t f = act ? faces[e] : uint8_t(0);   // issued early, used in the epilogue
 
     float ureg[n];
 #pragma unroll
@@ -170,7 +171,6 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     }
     __syncthreads();
 
-    const uint8_t f = act ? faces[e] : uint8_t(0);
 #pragma unroll
     for (int k = 0; k < n; ++k) {
       float wv = wreg[k];

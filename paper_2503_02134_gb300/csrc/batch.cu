@@ -62,7 +62,7 @@ constexpr size_t batch_smem_bytes() {
 // with the stage buffer.
 template <int n>
 __device__ double batch_group(const BatchProb& P, int64_t g, float* sb, float* sr, float* ss,
-                              float (*sD)[11], double* sh_red) {
+                              float (*sD)[11], double* sh_red, float beta) {
   constexpr int n2 = n * n, n3 = n * n * n, EPB = batch_epb<n>();
   constexpr int SV = EPB * n3;
   const int tid = threadIdx.x;
@@ -79,13 +79,13 @@ __device__ double batch_group(const BatchProb& P, int64_t g, float* sb, float* s
     DiT[l] = sD[l][ir];
     DjT[l] = sD[l][jr];
   }
-  const float beta = (float)P.scal->beta;
   float* const su_e = sb + 2 * SV + ler * n3;
   const float* const Gs = sb + 3 * SV + ler * 6 * n3 + ij;
   float* const sr_e = sr + ler * n3;
   float* const ss_e = ss + ler * n3;
   const int64_t e = g * EPB + le;
   const bool act = lane_ok && e < P.E;
+  const uint8_t f = act ? P.faces[e] : uint8_t(0);   // issued early, used in the epilogue
   DotAcc<float, kDotDot2> acc;
 
   float ureg[n];
@@ -123,7 +123,6 @@ __device__ double batch_group(const BatchProb& P, int64_t g, float* sb, float* s
     for (int kk = 0; kk < n; ++kk) wreg[kk] += sD[k][kk] * vt;
   }
   __syncthreads();
-  const uint8_t f = act ? P.faces[e] : uint8_t(0);
 #pragma unroll
   for (int k = 0; k < n; ++k) {
     float wv = wreg[k];
@@ -157,6 +156,7 @@ __global__ void __launch_bounds__(kBatchThreads)
   __shared__ int s_phase[NS];   // completed barrier phases per stage
   __shared__ bool s_last;
   __shared__ BatchProb sP;      // the problem of the item being computed
+  __shared__ float s_beta;      // its beta (constant during a launch)
   const int tid = threadIdx.x;
 
   // every block owns one contiguous range of the work list
@@ -227,16 +227,17 @@ __global__ void __launch_bounds__(kBatchThreads)
         __syncthreads();
         const int nn = sP.n;
         for (int q = tid; q < nn * nn; q += blockDim.x) sD[q / nn][q % nn] = sP.D[q];
+        if (tid == 0) s_beta = (float)sP.scal->beta;
         __syncthreads();
       }
       float* sb = stage0 + st * kBatchStageFloats;
       double part = 0.0;
       switch (sP.n) {
-        case 2: part = batch_group<2>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
-        case 4: part = batch_group<4>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
-        case 6: part = batch_group<6>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
-        case 8: part = batch_group<8>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
-        default: part = batch_group<10>(sP, itm.y, sb, sr, ss, sD, sh_red); break;
+        case 2: part = batch_group<2>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
+        case 4: part = batch_group<4>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
+        case 6: part = batch_group<6>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
+        case 8: part = batch_group<8>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
+        default: part = batch_group<10>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
       }
       // the reduction's barriers guarantee the stage is no longer read
       if (tid == 0) {
