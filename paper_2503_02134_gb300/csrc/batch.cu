@@ -7,8 +7,9 @@
 // kernel runs the same element computation as ax_tma_kernel for whichever
 // order the item's problem has, the gather-scatter and update kernels run
 // the single-problem code per chunk / per item.  Reductions are per problem
-// (one partial per work item, summed in item order by the last item to
-// finish), so each problem's result does not depend on the batch it is in.
+// (one partial per work item, summed in item order by a per-problem
+// finaliser launched after each phase), so each problem's result does not
+// depend on the batch it is in.
 #include <algorithm>
 #include <vector>
 
@@ -154,7 +155,6 @@ __global__ void __launch_bounds__(kBatchThreads)
   __shared__ double sh_red[kBatchThreads / 32];
   __shared__ int2 s_item[NS];   // work item staged on each stage ({-1, -1} = none)
   __shared__ int s_phase[NS];   // completed barrier phases per stage
-  __shared__ bool s_last;
   __shared__ BatchProb sP;      // the problem of the item being computed
   __shared__ float s_beta;      // its beta (constant during a launch)
   const int tid = threadIdx.x;
@@ -239,12 +239,10 @@ __global__ void __launch_bounds__(kBatchThreads)
         case 8: part = batch_group<8>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
         default: part = batch_group<10>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
       }
-      // the reduction's barriers guarantee the stage is no longer read
+      // the reduction's barriers guarantee the stage is no longer read; the
+      // partial is summed by batch_finalize_pap after the launch
       if (tid == 0) {
         sP.ax_part[itm.y] = part;
-        __threadfence();
-        const unsigned int c = atomicAdd(&sP.scal->counter[0], 1u);
-        s_last = (c == (unsigned int)sP.ngroups - 1u);
         ++s_phase[st];
         if (next < it1) {
           fence_proxy_async_smem();
@@ -254,24 +252,6 @@ __global__ void __launch_bounds__(kBatchThreads)
         }
       }
       __syncthreads();
-      if (s_last) {
-        __threadfence();
-        double s = 0.0;
-        for (int b = tid; b < sP.ngroups; b += blockDim.x) s += __ldcg(sP.ax_part + b);
-        const double pap = block_sum<kDotDot2>(s, sh_red);
-        if (tid == 0) {
-          sP.scal->pap = pap;
-          if (!(pap > 0.0) || !isfinite(pap)) {
-            // the update kernel ends the solve of this problem
-            sP.scal->status = SEM_BREAKDOWN;
-            sP.scal->alpha = 0.0;
-          } else {
-            sP.scal->alpha = sP.scal->rtz / pap;
-          }
-          sP.scal->counter[0] = 0u;
-        }
-        __syncthreads();
-      }
     } else {
       if (tid == 0) {
         if (next < it1) issue(st, next); else s_item[st] = make_int2(-1, -1);
@@ -329,7 +309,6 @@ __global__ void __launch_bounds__(256)
                         const int* __restrict__ nuitems_dev) {
   const int nuitems = *nuitems_dev;
   __shared__ double sh[8];
-  __shared__ bool s_last;
   for (int ui = blockIdx.x; ui < nuitems; ui += gridDim.x) {
     const int2 itm = uitems[ui];
     const BatchProb& P = probs[itm.x];
@@ -361,28 +340,55 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x == 0) {
       P.up_part[2 * itm.y] = v0;
       P.up_part[2 * itm.y + 1] = v1;
-      __threadfence();
-      const unsigned int c = atomicAdd(&P.scal->counter[1], 1u);
-      s_last = (c == (unsigned int)P.nupd - 1u);
+    }
+  }
+}
+
+// One block per problem: pap = sum of the operator's item partials (item
+// order), alpha = rtz / pap (or the breakdown flag).  Runs after the
+// operator launch, so no partial needs a fence or an election.
+__global__ void __launch_bounds__(256)
+    batch_finalize_pap(const BatchProb* __restrict__ probs, int count) {
+  __shared__ double sh[8];
+  for (int p = blockIdx.x; p < count; p += gridDim.x) {
+    const BatchProb& P = probs[p];
+    if (P.scal->done) continue;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < P.ngroups; b += blockDim.x) s += P.ax_part[b];
+    const double pap = block_sum<kDotDot2>(s, sh);
+    if (threadIdx.x == 0) {
+      P.scal->pap = pap;
+      if (!(pap > 0.0) || !isfinite(pap)) {
+        P.scal->status = SEM_BREAKDOWN;   // the update finaliser ends this problem
+        P.scal->alpha = 0.0;
+      } else {
+        P.scal->alpha = P.scal->rtz / pap;
+      }
     }
     __syncthreads();
-    if (s_last) {
-      __threadfence();
-      double a = 0.0, b = 0.0;
-      for (int q = threadIdx.x; q < P.nupd; q += blockDim.x) {
-        a += __ldcg(P.up_part + 2 * q);
-        b += __ldcg(P.up_part + 2 * q + 1);
-      }
-      const double rtr = block_sum<kDotDot2>(a, sh);
-      const double rtz = block_sum<kDotDot2>(b, sh);
-      if (threadIdx.x == 0) {
-        if (P.scal->status == SEM_BREAKDOWN) {
-          P.scal->done = 1;
-        } else {
-          finish_iteration(P.scal, rtr, rtz, nullptr);
-        }
-        P.scal->counter[1] = 0u;
-      }
+  }
+}
+
+// One block per problem: rtr, rtz from the update's item partials, then the
+// convergence test and the scalar recurrences of the iteration.
+__global__ void __launch_bounds__(256)
+    batch_finalize_update(const BatchProb* __restrict__ probs, int count) {
+  __shared__ double sh[8];
+  for (int p = blockIdx.x; p < count; p += gridDim.x) {
+    const BatchProb& P = probs[p];
+    if (P.scal->done) continue;
+    double a = 0.0, c = 0.0;
+    for (int q = threadIdx.x; q < P.nupd; q += blockDim.x) {
+      a += P.up_part[2 * q];
+      c += P.up_part[2 * q + 1];
+    }
+    const double rtr = block_sum<kDotDot2>(a, sh);
+    const double rtz = block_sum<kDotDot2>(c, sh);
+    if (threadIdx.x == 0) {
+      if (P.scal->status == SEM_BREAKDOWN)
+        P.scal->done = 1;
+      else
+        finish_iteration(P.scal, rtr, rtz, nullptr);
     }
     __syncthreads();
   }
@@ -449,6 +455,9 @@ static int batch_enqueue_iteration(sem_batch_s& b) {
   int rc = batch_launch_ax(b, b.ns, b.grid_ax);
   if (rc) return rc;
   int num_sms = b.subs[0]->num_sms;
+  batch_finalize_pap<<<b.count, 256, 0, b.stream>>>(b.d_probs, b.count);
+  ++b.launches;
+  SEM_CUDA(cudaGetLastError());
   const int64_t gs_blocks = std::min<int64_t>((b.nchunks + 7) / 8, (int64_t)num_sms * 8);
   if (b.nchunks > 0) {
     batch_gs_kernel<<<(int)std::max<int64_t>(gs_blocks, 1), 256, 0, b.stream>>>(
@@ -459,6 +468,9 @@ static int batch_enqueue_iteration(sem_batch_s& b) {
   const int up_blocks = std::min(b.nuitems, num_sms * 8);
   batch_update_kernel<<<std::max(up_blocks, 1), 256, 0, b.stream>>>(b.d_probs, b.d_uitems,
                                                                      b.d_counts + 2);
+  ++b.launches;
+  SEM_CUDA(cudaGetLastError());
+  batch_finalize_update<<<b.count, 256, 0, b.stream>>>(b.d_probs, b.count);
   ++b.launches;
   SEM_CUDA(cudaGetLastError());
   return 0;
