@@ -164,8 +164,9 @@ def batched_leg(sem, torch):
            "iterations_min_max": [min(it), max(it)], "all_converged": rc == 0 and seq_ok,
            "max_relres_true": max(i["relres_true"] for i in infos),
            "gdofs": total_L * sum(it) / len(it) / batched_s / 1e9,
-           "stages": sem.sem_batch_get_option(b, "stages"),
-           "grid": sem.sem_batch_get_option(b, "grid"),
+           "autotune": {f"n{N + 1}": {"variant": sem.sem_batch_get_option(b, f"variant_n{N + 1}"),
+                                      "grid": sem.sem_batch_get_option(b, f"grid_n{N + 1}")}
+                        for N in sorted(set(N for _, N in cases))},
            "launches_per_solve": infos[0]["launches"]}
     sem.sem_batch_destroy(b)
     return out
@@ -204,6 +205,8 @@ def main():
                     help="small run for ncu captures: 3 fixed mixed iterations + 2 FP32 operator calls")
     ap.add_argument("--profile-batched", action="store_true",
                     help="ncu run of the 64-problem batch: one solve inside an NVTX range")
+    ap.add_argument("--profile-batched-small", action="store_true",
+                    help="as --profile-batched on 16 problems with k <= 14 (a few GB, for ncu --set full)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -221,9 +224,10 @@ def main():
         dist.init_process_group("nccl")
     import paper_2503_02134_gb300 as sem
 
-    if args.profile_batched:
+    if args.profile_batched or args.profile_batched_small:
         import sem_inputs
-        cases = sem_inputs.batched_cases()
+        cases = (sem_inputs.batched_cases(count=16, kmax=14) if args.profile_batched_small
+                 else sem_inputs.batched_cases())
         b = sem.sem_batch_setup([sem.box_mesh(k, k, k, deform=True) for k, _ in cases],
                                 [N for _, N in cases])
         fs, xs = [], []

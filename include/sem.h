@@ -207,7 +207,8 @@ int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count, void* stre
 int sem_batch_problem(sem_batch b, int i, sem_handle* out);
 int sem_batch_pcg_solve(sem_batch b, const double* const* f, double* const* x,
                         const sem_solve_opts* opts, sem_info* infos);
-/* keys: "stages", "grid", "work_items", "launches", "tune_ms_s<2|3>_b<1..4>" */
+/* keys: "work_items", "launches", and per GLL points per direction n (2..10,
+ * even): "variant_n<n>", "grid_n<n>" (autotuned launch), "tune_ms_n<n>_v<0..2>" */
 int sem_batch_get_option(sem_batch b, const char* key, double* value);
 void sem_batch_destroy(sem_batch b);
 

@@ -10,7 +10,10 @@
 // (one partial per work item, summed in item order by a per-problem
 // finaliser launched after each phase), so each problem's result does not
 // depend on the batch it is in.
+#include <stdlib.h>
+
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "ax_tma.cuh"
@@ -38,134 +41,48 @@ struct BatchProb {
   int n, epb, ngroups, nupd;
 };
 
-constexpr int kBatchThreads = 128;
-constexpr int kBatchStageFloats = 9216;   // max over even n <= 10 of 9 * EPB * n^3
-constexpr int kBatchWorkFloats = 1024;    // max over even n <= 10 of EPB * n^3
 constexpr int kUpdItem4 = 1024;           // float4 per update work item (4096 values)
+constexpr int kBatchOrders = 5;           // n = 2, 4, 6, 8, 10 (odd N <= 9)
+inline int order_slot(int n) { return n / 2 - 1; }
 
-template <int n>
-constexpr int batch_epb() {
-  return (kBatchThreads / (n * n)) > 0 ? kBatchThreads / (n * n) : 1;
-}
-
-inline int batch_epb_of(int n) { return std::max(1, kBatchThreads / (n * n)); }
-
-template <int NS>
-constexpr size_t batch_smem_bytes() {
-  return sizeof(float) * ((size_t)NS * kBatchStageFloats + 2 * kBatchWorkFloats) +
-         NS * sizeof(uint64_t);
-}
-
-// One element group of problem P in PCG mode, data staged in `sb`
-// (r | J^{-1} | p_old | G, each EPB*n^3 floats (G: 6x)); P and D (in sD)
-// are the block's shared copies.  Returns this block's partial of
-// pap = sum p (A_L p) (valid in thread 0); on return every thread is done
-// with the stage buffer.
-template <int n>
-__device__ double batch_group(const BatchProb& P, int64_t g, float* sb, float* sr, float* ss,
-                              float (*sD)[11], double* sh_red, float beta) {
-  constexpr int n2 = n * n, n3 = n * n * n, EPB = batch_epb<n>();
-  constexpr int SV = EPB * n3;
+// Batched operator for the problems of one order n: the PCG-mode element
+// computation of ax_tma_kernel (same arithmetic, same launch shape TmaShape
+// <n, V>), applied to a work list of (problem, element group) items.  Every
+// block owns one contiguous range of the list; the bulk copies of the next
+// NS items are in flight while the block computes.  Each item stores its
+// partial of pap = sum p (A_L p); batch_finalize_pap sums them per problem.
+template <int n, int V>
+__global__ void __launch_bounds__(TmaShape<n, V>::NT)
+    batch_ax_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ items,
+                    const int* __restrict__ seg, int* __restrict__ err) {
+  using S = TmaShape<n, V>;
+  constexpr int n2 = S::n2, n3 = S::n3, EPB = S::EPB, NS = S::NS;
+  constexpr int SV = EPB * n3;       // floats of one vector per stage
+  constexpr int STAGE = 9 * SV;      // r | J^{-1} | p_old | G1..G6
+  const int off = seg[0], nitems = seg[1];
+  extern __shared__ __align__(128) float smem_f[];
+  float* const stage0 = smem_f;
+  float* const sr = smem_f + NS * STAGE;
+  float* const ss = sr + SV;
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(ss + SV);
+  __shared__ float sD[n][n + 1];
+  __shared__ double sh_red[S::NT / 32];
+  __shared__ int2 s_item[NS];   // item staged on each stage ({-1, -1} = none)
+  __shared__ int s_phase[NS];   // completed barrier phases per stage
+  __shared__ BatchProb sP;      // the problem of the item being computed
+  __shared__ float s_beta;
   const int tid = threadIdx.x;
   const int le = tid / n2;
   const int ij = tid - le * n2;
   const int i = ij % n, j = ij / n;
   const bool lane_ok = le < EPB;
   const int ir = lane_ok ? i : 0, jr = lane_ok ? j : 0, ler = lane_ok ? le : 0;
-  float Di[n], Dj[n], DiT[n], DjT[n];
-#pragma unroll
-  for (int l = 0; l < n; ++l) {
-    Di[l] = sD[ir][l];
-    Dj[l] = sD[jr][l];
-    DiT[l] = sD[l][ir];
-    DjT[l] = sD[l][jr];
-  }
-  float* const su_e = sb + 2 * SV + ler * n3;
-  const float* const Gs = sb + 3 * SV + ler * 6 * n3 + ij;
-  float* const sr_e = sr + ler * n3;
-  float* const ss_e = ss + ler * n3;
-  const int64_t e = g * EPB + le;
-  const bool act = lane_ok && e < P.E;
-  const uint8_t f = act ? P.faces[e] : uint8_t(0);   // issued early, used in the epilogue
-  DotAcc<float, kDotDot2> acc;
 
-  float ureg[n];
-#pragma unroll
-  for (int k = 0; k < n; ++k) {
-    const int si = k * n2 + ij;
-    const float v = sb[SV + ler * n3 + si] * sb[ler * n3 + si] + beta * su_e[si];
-    if (lane_ok) su_e[si] = v;
-    if (act) P.p[e * n3 + si] = v;
-    ureg[k] = v;
-  }
-  __syncthreads();
-  float wreg[n];
-#pragma unroll
-  for (int k = 0; k < n; ++k) wreg[k] = 0.f;
-#pragma unroll
-  for (int k = 0; k < n; ++k) {
-    float ur = 0.f, us = 0.f, ut = 0.f;
-#pragma unroll
-    for (int l = 0; l < n; ++l) {
-      ur += Di[l] * su_e[k * n2 + jr * n + l];
-      us += Dj[l] * su_e[k * n2 + l * n + ir];
-      ut += sD[k][l] * ureg[l];
-    }
-    const float g0 = Gs[0 * n3 + k * n2], g1 = Gs[1 * n3 + k * n2], g2 = Gs[2 * n3 + k * n2];
-    const float g3 = Gs[3 * n3 + k * n2], g4 = Gs[4 * n3 + k * n2], g5 = Gs[5 * n3 + k * n2];
-    const float vr = g0 * ur + g3 * us + g4 * ut;
-    const float vs = g3 * ur + g1 * us + g5 * ut;
-    const float vt = g4 * ur + g5 * us + g2 * ut;
-    if (lane_ok) {
-      sr_e[k * n2 + ij] = vr;
-      ss_e[k * n2 + ij] = vs;
-    }
-#pragma unroll
-    for (int kk = 0; kk < n; ++kk) wreg[kk] += sD[k][kk] * vt;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < n; ++k) {
-    float wv = wreg[k];
-#pragma unroll
-    for (int l = 0; l < n; ++l) {
-      wv += DiT[l] * sr_e[k * n2 + jr * n + l];
-      wv += DjT[l] * ss_e[k * n2 + l * n + ir];
-    }
-    if (on_dirichlet(f, i, j, k, n - 1)) wv = 0.f;
-    if (act) {
-      P.w[e * n3 + k * n2 + ij] = wv;
-      acc.add(ureg[k], wv);
-    }
-  }
-  return block_sum<kDotDot2>(acc.value(), sh_red);
-}
-
-template <int NS>
-__global__ void __launch_bounds__(kBatchThreads)
-    batch_ax_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ items,
-                    const int* __restrict__ nitems_dev, int* __restrict__ err) {
-  const int nitems = *nitems_dev;   // active work items (compacted as problems finish)
-  extern __shared__ __align__(128) float smem_f[];
-  float* const stage0 = smem_f;
-  float* const sr = smem_f + NS * kBatchStageFloats;
-  float* const ss = sr + kBatchWorkFloats;
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(ss + kBatchWorkFloats);
-  __shared__ float sD[10][11];
-  __shared__ double sh_red[kBatchThreads / 32];
-  __shared__ int2 s_item[NS];   // work item staged on each stage ({-1, -1} = none)
-  __shared__ int s_phase[NS];   // completed barrier phases per stage
-  __shared__ BatchProb sP;      // the problem of the item being computed
-  __shared__ float s_beta;      // its beta (constant during a launch)
-  const int tid = threadIdx.x;
-
-  // every block owns one contiguous range of the work list
   const int per = (nitems + gridDim.x - 1) / gridDim.x;
-  const int it0 = blockIdx.x * per;
-  const int it1 = min(nitems, it0 + per);
+  const int it0 = off + blockIdx.x * per;
+  const int it1 = off + min(nitems, (int)(blockIdx.x + 1) * per);
 
-  // issuing side (thread 0 only): the issuing problem's descriptor and its
-  // done flag (constant during a launch) are kept in registers
+  // issuing side (thread 0): descriptor and done flag of the issuing problem
   int ip = -1;
   bool ip_done = true;
   BatchProb IP;
@@ -180,12 +97,10 @@ __global__ void __launch_bounds__(kBatchThreads)
       s_item[st] = make_int2(-1, -1);
       return;
     }
-    const int n3 = IP.n * IP.n * IP.n;
-    const int64_t e0 = (int64_t)itm.y * IP.epb;
-    const int64_t cnt = IP.E - e0 < IP.epb ? IP.E - e0 : IP.epb;
+    const int64_t e0 = (int64_t)itm.y * EPB;
+    const int64_t cnt = IP.E - e0 < EPB ? IP.E - e0 : EPB;
     const uint32_t vb = (uint32_t)(cnt * n3 * 4);
-    const int SV = IP.epb * n3;
-    float* dst = stage0 + st * kBatchStageFloats;
+    float* dst = stage0 + st * STAGE;
     s_item[st] = itm;
     mbar_arrive_expect_tx(&bar[st], 9 * vb);
     bulk_load(dst, IP.r + e0 * n3, vb, &bar[st]);
@@ -208,6 +123,7 @@ __global__ void __launch_bounds__(kBatchThreads)
 
   bool aborted = false;
   int cur_prob = -1;
+  float Di[n], Dj[n], DiT[n], DjT[n];
   for (int it = it0, t = 0; it < it1; ++it, ++t) {
     const int st = t % NS;
     const int2 itm = s_item[st];
@@ -219,28 +135,86 @@ __global__ void __launch_bounds__(kBatchThreads)
     }
     const int next = it + NS;
     if (itm.x >= 0) {
-      if (itm.x != cur_prob) {   // block-uniform: refresh the shared problem copy and D
+      if (itm.x != cur_prob) {   // block-uniform: refresh the problem copy, D and beta
         cur_prob = itm.x;
         const int* src = reinterpret_cast<const int*>(probs + itm.x);
         for (int q = tid; q < (int)(sizeof(BatchProb) / sizeof(int)); q += blockDim.x)
           reinterpret_cast<int*>(&sP)[q] = src[q];
         __syncthreads();
-        const int nn = sP.n;
-        for (int q = tid; q < nn * nn; q += blockDim.x) sD[q / nn][q % nn] = sP.D[q];
+        for (int q = tid; q < n2; q += blockDim.x) sD[q / n][q % n] = sP.D[q];
         if (tid == 0) s_beta = (float)sP.scal->beta;
         __syncthreads();
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          Di[l] = sD[ir][l];
+          Dj[l] = sD[jr][l];
+          DiT[l] = sD[l][ir];
+          DjT[l] = sD[l][jr];
+        }
       }
-      float* sb = stage0 + st * kBatchStageFloats;
-      double part = 0.0;
-      switch (sP.n) {
-        case 2: part = batch_group<2>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
-        case 4: part = batch_group<4>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
-        case 6: part = batch_group<6>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
-        case 8: part = batch_group<8>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
-        default: part = batch_group<10>(sP, itm.y, sb, sr, ss, sD, sh_red, s_beta); break;
+      const float beta = s_beta;
+      float* const sb = stage0 + st * STAGE;
+      float* const su_e = sb + 2 * SV + ler * n3;
+      const float* const Gs = sb + 3 * SV + ler * 6 * n3 + ij;
+      float* const sr_e = sr + ler * n3;
+      float* const ss_e = ss + ler * n3;
+      const int64_t e = (int64_t)itm.y * EPB + le;
+      const bool act = lane_ok && e < sP.E;
+      const uint8_t f = act ? sP.faces[e] : uint8_t(0);
+      float* const pg = sP.p;
+      float* const wg = sP.w;
+      DotAcc<float, kDotDot2> acc;
+      float ureg[n];
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        const int si = k * n2 + ij;
+        const float v = sb[SV + ler * n3 + si] * sb[ler * n3 + si] + beta * su_e[si];
+        if (lane_ok) su_e[si] = v;
+        if (act) pg[e * n3 + si] = v;
+        ureg[k] = v;
       }
-      // the reduction's barriers guarantee the stage is no longer read; the
-      // partial is summed by batch_finalize_pap after the launch
+      __syncthreads();
+      float wreg[n];
+#pragma unroll
+      for (int k = 0; k < n; ++k) wreg[k] = 0.f;
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        float ur = 0.f, us = 0.f, ut = 0.f;
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          ur += Di[l] * su_e[k * n2 + jr * n + l];
+          us += Dj[l] * su_e[k * n2 + l * n + ir];
+          ut += sD[k][l] * ureg[l];
+        }
+        const float g0 = Gs[0 * n3 + k * n2], g1 = Gs[1 * n3 + k * n2], g2 = Gs[2 * n3 + k * n2];
+        const float g3 = Gs[3 * n3 + k * n2], g4 = Gs[4 * n3 + k * n2], g5 = Gs[5 * n3 + k * n2];
+        const float vr = g0 * ur + g3 * us + g4 * ut;
+        const float vs = g3 * ur + g1 * us + g5 * ut;
+        const float vt = g4 * ur + g5 * us + g2 * ut;
+        if (lane_ok) {
+          sr_e[k * n2 + ij] = vr;
+          ss_e[k * n2 + ij] = vs;
+        }
+#pragma unroll
+        for (int kk = 0; kk < n; ++kk) wreg[kk] += sD[k][kk] * vt;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        float wv = wreg[k];
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          wv += DiT[l] * sr_e[k * n2 + jr * n + l];
+          wv += DjT[l] * ss_e[k * n2 + l * n + ir];
+        }
+        if (on_dirichlet(f, i, j, k, n - 1)) wv = 0.f;
+        if (act) {
+          wg[e * n3 + k * n2 + ij] = wv;
+          acc.add(ureg[k], wv);
+        }
+      }
+      // the reduction's barriers guarantee the stage is no longer read
+      const double part = block_sum<kDotDot2>(acc.value(), sh_red);
       if (tid == 0) {
         sP.ax_part[itm.y] = part;
         ++s_phase[st];
@@ -263,6 +237,76 @@ __global__ void __launch_bounds__(kBatchThreads)
     atomicExch(err, 1);
     for (int q = 0; q < NS; ++q)
       if (s_item[q].x >= 0) mbar_wait_bounded(&bar[q], (uint32_t)(s_phase[q] & 1));
+  }
+}
+
+template <int n, int V>
+constexpr size_t batch_smem_bytes() {
+  using S = TmaShape<n, V>;
+  return sizeof(float) * ((size_t)S::NS * 9 * S::EPB * S::n3 + 2 * S::EPB * S::n3) +
+         S::NS * sizeof(uint64_t);
+}
+
+template <int n, int V>
+int batch_ax_launch(cudaStream_t st, int grid, const BatchProb* probs, const int2* items,
+                    const int* seg, int* err) {
+  auto kern = batch_ax_kernel<n, V>;
+  constexpr size_t smem = batch_smem_bytes<n, V>();
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, TmaShape<n, V>::NT, smem, st>>>(probs, items, seg, err);
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+template <int n, int V>
+int batch_ax_occupancy(int* per_sm) {
+  auto kern = batch_ax_kernel<n, V>;
+  constexpr size_t smem = batch_smem_bytes<n, V>();
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, TmaShape<n, V>::NT, smem));
+  return 0;
+}
+
+template <int n>
+int batch_ax_dispatch(int V, cudaStream_t st, int grid, const BatchProb* probs, const int2* items,
+                      const int* seg, int* err) {
+  switch (V) {
+    case 1: return batch_ax_launch<n, 1>(st, grid, probs, items, seg, err);
+    case 2: return batch_ax_launch<n, 2>(st, grid, probs, items, seg, err);
+    default: return batch_ax_launch<n, 0>(st, grid, probs, items, seg, err);
+  }
+}
+
+int batch_ax_any(int n, int V, cudaStream_t st, int grid, const BatchProb* probs,
+                 const int2* items, const int* seg, int* err) {
+  switch (n) {
+    case 2: return batch_ax_dispatch<2>(V, st, grid, probs, items, seg, err);
+    case 4: return batch_ax_dispatch<4>(V, st, grid, probs, items, seg, err);
+    case 6: return batch_ax_dispatch<6>(V, st, grid, probs, items, seg, err);
+    case 8: return batch_ax_dispatch<8>(V, st, grid, probs, items, seg, err);
+    default: return batch_ax_dispatch<10>(V, st, grid, probs, items, seg, err);
+  }
+}
+
+int batch_ax_occupancy_any(int n, int V, int* per_sm) {
+#define SEM_OCC(NN)                                              \
+  if (n == NN) {                                                 \
+    if (V == 1) return batch_ax_occupancy<NN, 1>(per_sm);        \
+    if (V == 2) return batch_ax_occupancy<NN, 2>(per_sm);        \
+    return batch_ax_occupancy<NN, 0>(per_sm);                    \
+  }
+  SEM_OCC(2) SEM_OCC(4) SEM_OCC(6) SEM_OCC(8) SEM_OCC(10)
+#undef SEM_OCC
+  return SEM_EINVAL;
+}
+
+int batch_epb_of(int n, int V) {
+  switch (n) {
+    case 2: return V == 0 ? TmaShape<2, 0>::EPB : TmaShape<2, 1>::EPB;
+    case 4: return V == 0 ? TmaShape<4, 0>::EPB : TmaShape<4, 1>::EPB;
+    case 6: return V == 0 ? TmaShape<6, 0>::EPB : TmaShape<6, 1>::EPB;
+    case 8: return V == 0 ? TmaShape<8, 0>::EPB : TmaShape<8, 1>::EPB;
+    default: return V == 0 ? TmaShape<10, 0>::EPB : TmaShape<10, 1>::EPB;
   }
 }
 
@@ -416,7 +460,7 @@ struct sem_batch_s {
   int2* d_uitems = nullptr;
   int nuitems = 0;
   double* d_part = nullptr;
-  int* d_counts = nullptr;   // active {work items, gs chunks, update items}
+  int* d_counts = nullptr;   // per order q: {offset, count} at [2q], then gs chunks, update items
   int* h_counts = nullptr;   // pinned staging of the above
   int2* h_items = nullptr;   // pinned staging of the compacted lists
   int2* h_uitems = nullptr;
@@ -426,9 +470,12 @@ struct sem_batch_s {
   sem::PcgScalars* d_scal_all = nullptr;
   sem::PcgScalars* h_scal_all = nullptr;
   int* d_err = nullptr;
-  int ns = 2;            // pipeline stages of the batched operator (autotuned)
-  int grid_ax = 0;       // blocks of the batched operator (autotuned)
-  float tune_ms[2][4] = {};
+  // per order slot q (n = 2q + 2): present, autotuned launch variant and grid
+  bool present[sem::kBatchOrders] = {};
+  int variant[sem::kBatchOrders] = {};
+  int grid[sem::kBatchOrders] = {};
+  float tune_ms[sem::kBatchOrders][3] = {};
+  std::vector<sem::BatchProb> probs_host;
   cudaGraphExec_t graph = nullptr;
   int graph_chunk = 0;
   int64_t graph_nodes = 0;
@@ -438,21 +485,19 @@ struct sem_batch_s {
 
 namespace sem {
 
-static int batch_launch_ax(sem_batch_s& b, int ns, int grid) {
-  if (ns == 3) {
-    batch_ax_kernel<3><<<grid, kBatchThreads, batch_smem_bytes<3>(), b.stream>>>(
-        b.d_probs, b.d_items, b.d_counts, b.d_err);
-  } else {
-    batch_ax_kernel<2><<<grid, kBatchThreads, batch_smem_bytes<2>(), b.stream>>>(
-        b.d_probs, b.d_items, b.d_counts, b.d_err);
+static int batch_launch_ax(sem_batch_s& b) {
+  for (int q = 0; q < kBatchOrders; ++q) {
+    if (!b.present[q]) continue;
+    int rc = batch_ax_any(2 * q + 2, b.variant[q], b.stream, b.grid[q], b.d_probs, b.d_items,
+                          b.d_counts + 2 * q, b.d_err);
+    if (rc) return rc;
+    ++b.launches;
   }
-  ++b.launches;
-  SEM_CUDA(cudaGetLastError());
   return 0;
 }
 
 static int batch_enqueue_iteration(sem_batch_s& b) {
-  int rc = batch_launch_ax(b, b.ns, b.grid_ax);
+  int rc = batch_launch_ax(b);
   if (rc) return rc;
   int num_sms = b.subs[0]->num_sms;
   batch_finalize_pap<<<b.count, 256, 0, b.stream>>>(b.d_probs, b.count);
@@ -461,13 +506,13 @@ static int batch_enqueue_iteration(sem_batch_s& b) {
   const int64_t gs_blocks = std::min<int64_t>((b.nchunks + 7) / 8, (int64_t)num_sms * 8);
   if (b.nchunks > 0) {
     batch_gs_kernel<<<(int)std::max<int64_t>(gs_blocks, 1), 256, 0, b.stream>>>(
-        b.d_probs, b.d_chunk_prob, b.d_chunk_desc, b.d_counts + 1);
+        b.d_probs, b.d_chunk_prob, b.d_chunk_desc, b.d_counts + 2 * kBatchOrders);
     ++b.launches;
     SEM_CUDA(cudaGetLastError());
   }
   const int up_blocks = std::min(b.nuitems, num_sms * 8);
   batch_update_kernel<<<std::max(up_blocks, 1), 256, 0, b.stream>>>(b.d_probs, b.d_uitems,
-                                                                     b.d_counts + 2);
+                                                                     b.d_counts + 2 * kBatchOrders + 1);
   ++b.launches;
   SEM_CUDA(cudaGetLastError());
   batch_finalize_update<<<b.count, 256, 0, b.stream>>>(b.d_probs, b.count);
@@ -517,14 +562,18 @@ static int batch_compact(sem_batch_s& b, const std::vector<int>& active) {
   int ni = 0, nu = 0, nc = 0;
   const int P = b.count;
   std::vector<size_t> gi(P, 0), ui(P, 0);
-  // operator items: ordered by order n, then problem, then element group,
-  // and split into one contiguous range per block: a block switches code
-  // path and problem descriptor rarely
-  for (int nval = 2; nval <= 10; nval += 2)
+  // operator items: one segment per order n (each launched by its own
+  // kernel), problems in order inside a segment, each block of that kernel
+  // taking one contiguous range: a block rarely switches problem
+  for (int q = 0; q < kBatchOrders; ++q) {
+    const int start = ni;
     for (int p = 0; p < P; ++p) {
-      if (!active[p] || b.subs[p]->n != nval) continue;
+      if (!active[p] || order_slot(b.subs[p]->n) != q) continue;
       for (const int2& itm : b.items_of[p]) b.h_items[ni++] = itm;
     }
+    b.h_counts[2 * q] = start;
+    b.h_counts[2 * q + 1] = ni - start;
+  }
   (void)gi;
   bool more = true;
   while (more) {
@@ -543,9 +592,8 @@ static int batch_compact(sem_batch_s& b, const std::vector<int>& active) {
       ++nc;
     }
   }
-  b.h_counts[0] = ni;
-  b.h_counts[1] = nc;
-  b.h_counts[2] = nu;
+  b.h_counts[2 * kBatchOrders] = nc;
+  b.h_counts[2 * kBatchOrders + 1] = nu;
   SEM_CUDA(cudaMemcpyAsync(b.d_items, b.h_items, sizeof(int2) * std::max(ni, 1),
                            cudaMemcpyHostToDevice, b.stream));
   SEM_CUDA(cudaMemcpyAsync(b.d_uitems, b.h_uitems, sizeof(int2) * std::max(nu, 1),
@@ -554,8 +602,8 @@ static int batch_compact(sem_batch_s& b, const std::vector<int>& active) {
                            cudaMemcpyHostToDevice, b.stream));
   SEM_CUDA(cudaMemcpyAsync(b.d_chunk_prob, b.h_chunk_prob, sizeof(int) * std::max(nc, 1),
                            cudaMemcpyHostToDevice, b.stream));
-  SEM_CUDA(cudaMemcpyAsync(b.d_counts, b.h_counts, sizeof(int) * 3, cudaMemcpyHostToDevice,
-                           b.stream));
+  SEM_CUDA(cudaMemcpyAsync(b.d_counts, b.h_counts, sizeof(int) * (2 * kBatchOrders + 2),
+                           cudaMemcpyHostToDevice, b.stream));
   // the pinned staging buffers are reused: wait for the copies
   SEM_CUDA(cudaStreamSynchronize(b.stream));
   return 0;
@@ -571,10 +619,21 @@ static int batch_read_scalars(sem_batch_s& b) {
   return 0;
 }
 
-// Project autotuner of the batched operator: pipeline stages x blocks per SM,
-// timed with CUDA events on the batch's own work list.
+// Element groups of problem p at elements-per-group epb.
+static void batch_set_groups(sem_batch_s& b, int p, int epb) {
+  BatchProb& P = b.probs_host[p];
+  P.epb = epb;
+  P.ngroups = (int)((P.E + epb - 1) / epb);
+  b.items_of[p].clear();
+  for (int g = 0; g < P.ngroups; ++g) b.items_of[p].push_back(make_int2(p, g));
+}
+
+// Project autotuner of the batched operator: for every order present, each
+// launch variant (elements per block x pipeline stages, as the
+// single-problem kernel) and 1..4 blocks per SM, timed with CUDA events on
+// the batch's own work list; the fastest is kept.
 static int batch_autotune(sem_batch_s& b) {
-  int num_sms = b.subs[0]->num_sms;
+  const int num_sms = b.subs[0]->num_sms;
   cudaEvent_t e0, e1;
   SEM_CUDA(cudaEventCreate(&e0));
   SEM_CUDA(cudaEventCreate(&e1));
@@ -585,43 +644,56 @@ static int batch_autotune(sem_batch_s& b) {
     int rc = launch_scal_setup(h, h.scal, 0.0, 1, 0, 0);
     if (rc) return rc;
   }
-  float best = 1e30f;
-  int best_ns = 2, best_grid = num_sms;
-  for (int nsv = 0; nsv < 2; ++nsv) {
-    const int ns = nsv == 0 ? 2 : 3;
-    auto kern = ns == 2 ? batch_ax_kernel<2> : batch_ax_kernel<3>;
-    const size_t smem = ns == 2 ? batch_smem_bytes<2>() : batch_smem_bytes<3>();
-    SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem));
-    per_sm = std::max(per_sm, 1);
-    for (int bps = 1; bps <= std::min(per_sm, 4); ++bps) {
-      const int grid = std::min(num_sms * bps, std::max(b.nitems, 1));
-      int rc = batch_launch_ax(b, ns, grid);
-      if (rc) return rc;
-      SEM_CUDA(cudaEventRecord(e0, b.stream));
-      for (int q = 0; q < 2 && !rc; ++q) rc = batch_launch_ax(b, ns, grid);
-      if (rc) return rc;
-      SEM_CUDA(cudaEventRecord(e1, b.stream));
-      SEM_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      SEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      ms *= 0.5f;
-      if (bps <= 4) b.tune_ms[nsv][bps - 1] = ms;
-      if (ms < best) {
-        best = ms;
-        best_ns = ns;
-        best_grid = grid;
+  std::vector<int> all(b.count, 1);
+  int rc = 0;
+  for (int q = 0; q < kBatchOrders && !rc; ++q) {
+    if (!b.present[q]) continue;
+    const int n = 2 * q + 2;
+    float best = 1e30f;
+    for (int V = 0; V < 3 && !rc; ++V) {
+      for (int p = 0; p < b.count; ++p)
+        if (b.subs[p]->n == n) batch_set_groups(b, p, batch_epb_of(n, V));
+      SEM_CUDA(cudaMemcpyAsync(b.d_probs, b.probs_host.data(), sizeof(BatchProb) * b.count,
+                               cudaMemcpyHostToDevice, b.stream));
+      if ((rc = batch_compact(b, all))) break;
+      int per_sm = 0;
+      if ((rc = batch_ax_occupancy_any(n, V, &per_sm))) break;
+      per_sm = std::max(1, std::min(per_sm, 4));
+      float best_v = 1e30f;
+      for (int bps = 1; bps <= per_sm && !rc; ++bps) {
+        const int grid = num_sms * bps;
+        const int* seg = b.d_counts + 2 * q;
+        if ((rc = batch_ax_any(n, V, b.stream, grid, b.d_probs, b.d_items, seg, b.d_err))) break;
+        SEM_CUDA(cudaEventRecord(e0, b.stream));
+        for (int r = 0; r < 2 && !rc; ++r)
+          rc = batch_ax_any(n, V, b.stream, grid, b.d_probs, b.d_items, seg, b.d_err);
+        SEM_CUDA(cudaEventRecord(e1, b.stream));
+        SEM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms *= 0.5f;
+        best_v = std::min(best_v, ms);
+        if (ms < best) {
+          best = ms;
+          b.variant[q] = V;
+          b.grid[q] = grid;
+        }
       }
+      b.tune_ms[q][V] = best_v;
     }
+    // final grouping of this order
+    for (int p = 0; p < b.count; ++p)
+      if (b.subs[p]->n == n) batch_set_groups(b, p, batch_epb_of(n, b.variant[q]));
   }
-  b.ns = best_ns;
-  b.grid_ax = best_grid;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (rc) return rc;
+  SEM_CUDA(cudaMemcpyAsync(b.d_probs, b.probs_host.data(), sizeof(BatchProb) * b.count,
+                           cudaMemcpyHostToDevice, b.stream));
+  if ((rc = batch_compact(b, all))) return rc;
   for (int p = 0; p < b.count; ++p) {
-    int rc = launch_scal_setup(*b.subs[p], b.subs[p]->scal, 0.0, 1, 0, 0);
-    if (rc) return rc;
+    int r2 = launch_scal_setup(*b.subs[p], b.subs[p]->scal, 0.0, 1, 0, 0);
+    if (r2) return r2;
   }
   return 0;
 }
@@ -703,11 +775,12 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
     P.E = h.E;
     P.L = h.L;
     P.n = h.n;
-    P.epb = batch_epb_of(h.n);
-    P.ngroups = (int)((h.E + P.epb - 1) / P.epb);
+    P.epb = 1;
+    P.ngroups = (int)h.E;   // the most groups any variant makes
     P.nupd = (int)(((h.L >> 2) + kUpdItem4 - 1) / kUpdItem4);
+    b->present[order_slot(h.n)] = true;
     ax_off[p] = part_total;
-    part_total += P.ngroups;
+    part_total += h.E;
     up_off[p] = part_total;
     part_total += 2 * (int64_t)P.nupd;
     b->nchunks += h.n_chunks;
@@ -738,11 +811,11 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
       (ce = cudaMalloc((void**)&b->d_uitems, sizeof(int2) * nut)) != cudaSuccess ||
       (ce = cudaMalloc((void**)&b->d_chunk_prob, sizeof(int) * nch)) != cudaSuccess ||
       (ce = cudaMalloc((void**)&b->d_chunk_desc, sizeof(int2) * nch)) != cudaSuccess ||
-      (ce = cudaMalloc((void**)&b->d_counts, sizeof(int) * 4)) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&b->d_counts, sizeof(int) * (2 * kBatchOrders + 2))) != cudaSuccess ||
       (ce = cudaMalloc((void**)&b->d_scal_all, sizeof(PcgScalars) * count)) != cudaSuccess ||
       (ce = cudaMalloc((void**)&b->d_err, sizeof(int))) != cudaSuccess ||
       (ce = cudaMallocHost((void**)&b->h_scal_all, sizeof(PcgScalars) * count)) != cudaSuccess ||
-      (ce = cudaMallocHost((void**)&b->h_counts, sizeof(int) * 4)) != cudaSuccess ||
+      (ce = cudaMallocHost((void**)&b->h_counts, sizeof(int) * (2 * kBatchOrders + 2))) != cudaSuccess ||
       (ce = cudaMallocHost((void**)&b->h_items, sizeof(int2) * nit)) != cudaSuccess ||
       (ce = cudaMallocHost((void**)&b->h_uitems, sizeof(int2) * nut)) != cudaSuccess ||
       (ce = cudaMallocHost((void**)&b->h_chunk_prob, sizeof(int) * nch)) != cudaSuccess ||
@@ -753,6 +826,7 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
     probs[p].ax_part = b->d_part + ax_off[p];
     probs[p].up_part = b->d_part + up_off[p];
   }
+  b->probs_host = probs;
   if ((ce = cudaMemcpyAsync(b->d_probs, probs.data(), sizeof(BatchProb) * count,
                             cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
       (ce = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream)) != cudaSuccess)
@@ -780,13 +854,22 @@ extern "C" int sem_batch_get_option(sem_batch b, const char* key, double* value)
     return SEM_EINVAL;
   }
   const std::string k(key);
-  if (k == "stages") *value = b->ns;
-  else if (k == "grid") *value = b->grid_ax;
-  else if (k == "work_items") *value = b->nitems;
+  auto order_of = [&](const std::string& pre, int* q) {
+    if (k.rfind(pre, 0) != 0) return false;
+    const int n = std::atoi(k.c_str() + pre.size());
+    if (n < 2 || n > 10 || n % 2) return false;
+    *q = order_slot(n);
+    return true;
+  };
+  int q = 0;
+  if (k == "work_items") *value = b->nitems;
   else if (k == "launches") *value = (double)b->launches;
-  else if (k.rfind("tune_ms_s", 0) == 0 && k.size() == 13 && (k[9] == '2' || k[9] == '3') &&
-           k[10] == '_' && k[11] == 'b' && k[12] >= '1' && k[12] <= '4')
-    *value = b->tune_ms[k[9] - '2'][k[12] - '1'];
+  else if (order_of("variant_n", &q)) *value = b->present[q] ? b->variant[q] : -1;
+  else if (order_of("grid_n", &q)) *value = b->present[q] ? b->grid[q] : 0;
+  else if (k.rfind("tune_ms_n", 0) == 0 && k.size() >= 13 && k[k.size() - 2] == 'v' &&
+           k[k.size() - 1] >= '0' && k[k.size() - 1] <= '2' &&
+           order_of("tune_ms_n", &q))
+    *value = b->tune_ms[q][k[k.size() - 1] - '0'];
   else {
     set_error("sem_batch_get_option: unknown key: " + k);
     return SEM_EINVAL;

@@ -25,8 +25,10 @@ def test_batch_matches_standalone_and_oracle(sem):
     meshes = [sem.box_mesh(kx, ky, kz, deform=True) for kx, ky, kz, _ in CASES]
     Ns = [c[3] for c in CASES]
     b = sem.sem_batch_setup(meshes, Ns)
-    assert sem.sem_batch_get_option(b, "stages") in (2, 3)
-    assert sem.sem_batch_get_option(b, "grid") >= 1
+    for N in set(Ns):
+        assert sem.sem_batch_get_option(b, f"variant_n{N + 1}") in (0, 1, 2)
+        assert sem.sem_batch_get_option(b, f"grid_n{N + 1}") >= 1
+    assert sem.sem_batch_get_option(b, "variant_n4") == -1 or 3 in Ns
     fs, xs = [], []
     for i, c in enumerate(CASES):
         h = sem.sem_batch_problem(b, i)
