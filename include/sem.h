@@ -180,6 +180,13 @@ int sem_get_field(sem_handle h, int which, double* out);
  *         number g+1 of state `seed` (Steele-Lea-Flood 2014), masked. */
 int sem_rhs(sem_handle h, int kind, uint64_t seed, double* b);
 
+/* Random Fourier right-hand side b = mask QQ^T(B f) (FP64, L values):
+ * f = sum over k in {1..8}^3 of a_k sin(pi k1 x) sin(pi k2 y) sin(pi k3 z),
+ * a_k = xi_k / |k|^2, xi_k uniform in [-1,1) from SplitMix64 output number
+ * sample*512 + (k1-1) + 8(k2-1) + 64(k3-1) + 1 of state `seed`.  Training
+ * and test data of the learned initial guess. */
+int sem_rhs_fourier(sem_handle h, uint64_t seed, uint64_t sample, double* b);
+
 /* Jacobi PCG for A x = f (f assembled and masked, FP64).  x0 may be NULL
  * (zero initial guess).  x receives the FP64 solution.  Stopping test:
  * recursive ||r||_c/||b||_c <= tol (FP64 path) or the FP64 true residual
@@ -188,6 +195,38 @@ int sem_pcg_solve(sem_handle h, const double* f, const double* x0, double* x,
                   double tol, int maxit, sem_precision p, sem_info* info);
 int sem_pcg_solve_ex(sem_handle h, const double* f, const double* x0, double* x,
                      const sem_solve_opts* opts, sem_info* info);
+
+/* ---- Learned initial guess (the paper has no learned component) ----
+ * An element-local network (inputs: the element's b_L / s_e, the element
+ * mean and standard deviation of G1..G6, the mean of b_L over each face
+ * neighbour / s_e; s_e the RMS of b_L on the element; 530 inputs padded to
+ * 544 -> hidden -> hidden -> n^3, ReLU) predicts u_L / s_e; the guess is
+ * x0 = c * QQ^T(s_e * y) (continuity projection, c = mask / multiplicity),
+ * optionally scaled by the energy-optimal alpha = <b,c,x0>/<x0,c,A x0>,
+ * which never increases the A-norm error over x0 = 0.  Box meshes only.
+ * Weights: FP32 master + BF16 copies; products in BF16 with FP32
+ * accumulation; Adam (lr as given, betas 0.9/0.999, eps 1e-8).
+ * sem_x0_add_pair appends the E (features, x_L / s_e) rows of one solved
+ * pair (b, x: device FP64 vectors) to the model's training set;
+ * sem_x0_train runs `epochs` passes of shuffled mini-batches;
+ * sem_x0_predict writes x0 (device FP64).  sem_x0_params gets (set = 0) or
+ * sets (set = 1) the FP32 master parameters (host array laid out as
+ * sem_x0_param_count's offsets: W1 [544 x H], b1, W2 [H x H], b2, W3 [H x n^3],
+ * b3, row-major); sem_x0_gradients runs one forward/backward pass on `rows`
+ * host rows (X: rows x 544, T: rows x n^3, FP32) in BF16 (bf16_mode = 1) or
+ * FP32 arithmetic and returns the gradient of mean((y - T)^2) in the same
+ * layout; sem_x0_features writes the FP32 features (E x 544) and scales. */
+typedef struct sem_x0_model_s* sem_x0_model;
+int sem_x0_create(sem_handle h, int hidden, uint64_t seed, sem_x0_model* out);
+int sem_x0_param_count(sem_x0_model m, int64_t* sizes6, int64_t* offsets6);
+int sem_x0_params(sem_x0_model m, float* host, int set);
+int sem_x0_features(sem_x0_model m, const double* b, float* X, double* scale);
+int sem_x0_gradients(sem_x0_model m, const float* X, const float* T, int rows, int bf16_mode,
+                     float* grads, double* loss);
+int sem_x0_add_pair(sem_x0_model m, const double* b, const double* x);
+int sem_x0_train(sem_x0_model m, int epochs, int batch, float lr, uint64_t seed, double* final_loss);
+int sem_x0_predict(sem_x0_model m, const double* b, double* x0, int energy_scale);
+void sem_x0_destroy(sem_x0_model m);
 
 /* ---- Batched solves: many independent problems of uneven E and N ----
  * sem_batch_setup builds one sub-handle per problem (meshes[i], Ns[i]; odd

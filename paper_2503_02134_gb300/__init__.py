@@ -94,6 +94,16 @@ def _load():
                                     ctypes.POINTER(sem_solve_opts), ctypes.POINTER(sem_info)]),
         "sem_batch_get_option": (i, [h, ctypes.c_char_p, ctypes.POINTER(d)]),
         "sem_batch_destroy": (None, [h]),
+        "sem_rhs_fourier": (i, [h, ctypes.c_uint64, ctypes.c_uint64, vp]),
+        "sem_x0_create": (i, [h, i, ctypes.c_uint64, ctypes.POINTER(h)]),
+        "sem_x0_param_count": (i, [h, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "sem_x0_params": (i, [h, vp, i]),
+        "sem_x0_features": (i, [h, vp, vp, vp]),
+        "sem_x0_gradients": (i, [h, vp, vp, i, i, vp, ctypes.POINTER(d)]),
+        "sem_x0_add_pair": (i, [h, vp, vp]),
+        "sem_x0_train": (i, [h, i, i, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(d)]),
+        "sem_x0_predict": (i, [h, vp, vp, i]),
+        "sem_x0_destroy": (None, [h]),
         "sem_get_option": (i, [h, ctypes.c_char_p, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
@@ -108,7 +118,9 @@ EXPORTED = ("sem_setup", "sem_destroy", "sem_last_error", "sem_get_sizes", "sem_
             "sem_ax_local", "sem_gs", "sem_glsc3", "sem_get_field", "sem_rhs", "sem_pcg_solve",
             "sem_pcg_solve_ex", "sem_set_option", "sem_get_option", "sem_glsc3_noalloc",
             "sem_batch_setup", "sem_batch_problem", "sem_batch_pcg_solve", "sem_batch_get_option",
-            "sem_batch_destroy")
+            "sem_batch_destroy", "sem_rhs_fourier", "sem_x0_create", "sem_x0_param_count",
+            "sem_x0_params", "sem_x0_features", "sem_x0_gradients", "sem_x0_add_pair",
+            "sem_x0_train", "sem_x0_predict", "sem_x0_destroy")
 
 
 class SemError(RuntimeError):
@@ -239,6 +251,56 @@ def sem_batch_get_option(b, key: str) -> float:
 
 def sem_batch_destroy(b):
     _lib.sem_batch_destroy(b)
+
+
+def sem_rhs_fourier(h, seed, sample, b):
+    return _check(_lib.sem_rhs_fourier(h, seed, sample, _ptr(b)), "sem_rhs_fourier")
+
+
+def sem_x0_create(h, hidden=256, seed=0):
+    m = ctypes.c_void_p()
+    _check(_lib.sem_x0_create(h, hidden, seed, ctypes.byref(m)), "sem_x0_create")
+    return m
+
+
+def sem_x0_param_count(m):
+    sz = (ctypes.c_int64 * 6)()
+    off = (ctypes.c_int64 * 6)()
+    _check(_lib.sem_x0_param_count(m, sz, off), "sem_x0_param_count")
+    return list(sz), list(off)
+
+
+def sem_x0_params(m, host, set_=False):
+    return _check(_lib.sem_x0_params(m, _ptr(host), 1 if set_ else 0), "sem_x0_params")
+
+
+def sem_x0_features(m, b, X, scale=None):
+    return _check(_lib.sem_x0_features(m, _ptr(b), _ptr(X), _ptr(scale)), "sem_x0_features")
+
+
+def sem_x0_gradients(m, X, T, rows, bf16_mode, grads):
+    loss = ctypes.c_double()
+    _check(_lib.sem_x0_gradients(m, _ptr(X), _ptr(T), rows, bf16_mode, _ptr(grads), ctypes.byref(loss)),
+           "sem_x0_gradients")
+    return loss.value
+
+
+def sem_x0_add_pair(m, b, x):
+    return _check(_lib.sem_x0_add_pair(m, _ptr(b), _ptr(x)), "sem_x0_add_pair")
+
+
+def sem_x0_train(m, epochs, batch, lr, seed=0):
+    loss = ctypes.c_double()
+    _check(_lib.sem_x0_train(m, epochs, batch, lr, seed, ctypes.byref(loss)), "sem_x0_train")
+    return loss.value
+
+
+def sem_x0_predict(m, b, x0, energy_scale=True):
+    return _check(_lib.sem_x0_predict(m, _ptr(b), _ptr(x0), 1 if energy_scale else 0), "sem_x0_predict")
+
+
+def sem_x0_destroy(m):
+    _lib.sem_x0_destroy(m)
 
 
 def sem_set_option(h, key: str, value: int):

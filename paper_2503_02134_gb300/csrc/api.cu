@@ -217,6 +217,7 @@ int sem_setup(const sem_mesh* mesh, int N, int geom_flags, void* stream, sem_han
   if ((rc = launch_gll(*h))) return fail(rc);
   double* ucoords = nullptr;
   if (mesh->gid) {
+    h->gid_user = true;
     if ((rc = launch_user_connectivity(*h, mesh->gid, mesh->dirichlet_faces))) return fail(rc);
     if ((ce = cudaMalloc((void**)&ucoords, sizeof(double) * 3 * L)) != cudaSuccess)
       return fail(cuda_fail(ce, "cudaMalloc"));
@@ -376,6 +377,21 @@ int sem_rhs(sem_handle h, int kind, uint64_t seed, double* b) {
   if (is_device_ptr(b)) return launch_rhs(*h, kind, seed, b);
   if ((rc = ensure_stage(*h))) return rc;
   if ((rc = launch_rhs(*h, kind, seed, (double*)h->stage_a))) return rc;
+  SEM_CUDA(cudaMemcpyAsync(b, h->stage_a, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream));
+  SEM_CUDA(cudaStreamSynchronize(h->stream));
+  return SEM_OK;
+}
+
+int sem_rhs_fourier(sem_handle h, uint64_t seed, uint64_t sample, double* b) {
+  if (!h || !b) {
+    set_error("sem_rhs_fourier: null argument");
+    return SEM_EINVAL;
+  }
+  StreamScope scope(*h);
+  int rc;
+  if (is_device_ptr(b)) return launch_rhs_fourier(*h, seed, sample, b);
+  if ((rc = ensure_stage(*h))) return rc;
+  if ((rc = launch_rhs_fourier(*h, seed, sample, (double*)h->stage_a))) return rc;
   SEM_CUDA(cudaMemcpyAsync(b, h->stage_a, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream));
   SEM_CUDA(cudaStreamSynchronize(h->stream));
   return SEM_OK;

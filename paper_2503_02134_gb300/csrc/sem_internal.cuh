@@ -42,6 +42,7 @@ struct Handle {
   int N = 0, n = 0;
   int64_t E = 0, L = 0, U = 0;
   int kx = 0, ky = 0, kz = 0;
+  bool gid_user = false;               // mesh numbered by the caller (no box structure)
   cudaStream_t stream = nullptr;       // internal work stream (never the legacy stream)
   cudaStream_t user_stream = nullptr;  // stream given to sem_setup
   bool own_stream = false;
@@ -136,6 +137,7 @@ int launch_geometry(Handle& h, const double* user_coords_dev, double amp, int de
 int launch_gs_map(Handle& h);
 int launch_jacobi(Handle& h);
 int launch_rhs(Handle& h, int kind, uint64_t seed, double* b);
+int launch_rhs_fourier(Handle& h, uint64_t seed, uint64_t sample, double* b);
 
 // ax_kernels.cu
 // w = mask * A_L u (element operator, masked); optional PCG prologue/epilogue.

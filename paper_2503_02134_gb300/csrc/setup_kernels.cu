@@ -598,6 +598,63 @@ __global__ void mask_inplace(double* v, const double* mask, int64_t L) {
     v[l] *= mask[l];
 }
 
+// Random Fourier series f = sum_{k in {1..K}^3} a_k sin(pi k1 x) sin(pi k2 y)
+// sin(pi k3 z), a_k = xi_k / |k|^2, xi_k uniform in [-1, 1) from SplitMix64
+// output number (sample K^3 + index(k)) + 1 of state `seed`,
+// index(k) = (k1-1) + K (k2-1) + K^2 (k3-1).
+constexpr int kFourierK = 8;
+
+__global__ void fourier_coeff_kernel(uint64_t seed, uint64_t sample, double* a) {
+  const int K = kFourierK;
+  for (int q = threadIdx.x; q < K * K * K; q += blockDim.x) {
+    const int k1 = q % K + 1, k2 = (q / K) % K + 1, k3 = q / (K * K) + 1;
+    const uint64_t z = splitmix64_at(seed, sample * (uint64_t)(K * K * K) + (uint64_t)q);
+    const double xi = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    a[q] = xi / (double)(k1 * k1 + k2 * k2 + k3 * k3);
+  }
+}
+
+__global__ void fourier_rhs_kernel(const double* coords, const double* B, const double* a,
+                                   int64_t L, double* b) {
+  const int K = kFourierK;
+  __shared__ double sa[kFourierK * kFourierK * kFourierK];
+  for (int q = threadIdx.x; q < K * K * K; q += blockDim.x) sa[q] = a[q];
+  __syncthreads();
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    double sx[kFourierK], sy[kFourierK], sz[kFourierK];
+    const double x = coords[l], y = coords[L + l], z = coords[2 * L + l];
+    for (int k = 0; k < K; ++k) {
+      sx[k] = sin(M_PI * (k + 1) * x);
+      sy[k] = sin(M_PI * (k + 1) * y);
+      sz[k] = sin(M_PI * (k + 1) * z);
+    }
+    double f = 0.0;
+    for (int k3 = 0; k3 < K; ++k3)
+      for (int k2 = 0; k2 < K; ++k2) {
+        double t = 0.0;
+        for (int k1 = 0; k1 < K; ++k1) t += sa[k1 + K * (k2 + K * k3)] * sx[k1];
+        f += t * sy[k2] * sz[k3];
+      }
+    b[l] = B[l] * f;
+  }
+}
+
+int launch_rhs_fourier(Handle& h, uint64_t seed, uint64_t sample, double* b) {
+  double* a = nullptr;
+  SEM_CUDA(cudaMallocAsync((void**)&a, sizeof(double) * kFourierK * kFourierK * kFourierK, h.stream));
+  fourier_coeff_kernel<<<1, 512, 0, h.stream>>>(seed, sample, a);
+  fourier_rhs_kernel<<<grid_for(h, h.L, 256), 256, 0, h.stream>>>(h.coords, h.B64, a, h.L, b);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  SEM_CUDA(cudaFreeAsync(a, h.stream));
+  int rc = launch_gs(h, SEM_FP64, b);
+  if (rc) return rc;
+  mask_inplace<<<grid_for(h, h.L, 256), 256, 0, h.stream>>>(b, h.mask64, h.L);
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
 int launch_rhs(Handle& h, int kind, uint64_t seed, double* b) {
   if (kind == 1) {
     rhs_uniform_kernel<<<grid_for(h, h.L, 256), 256, 0, h.stream>>>(h.gid, h.mask64, h.L, seed, b);

@@ -1,0 +1,118 @@
+"""Learned initial guess on the GPU against the FP64 oracle: the Fourier
+right-hand side, the element features, the network gradients (FP32 debug
+mode and BF16 mode), and what the trained guess gains over x0 = 0."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import learned_x0 as lx  # noqa: E402
+from oracle import sem_oracle as so  # noqa: E402
+from tests.gpu_util import rel_maxerr  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sem():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2503_02134_gb300 as m
+    return m
+
+
+def test_fourier_rhs_matches_oracle(sem):
+    P = so.Problem(3, 2, 2, 5, deform=True)
+    S = sem.Solver(3, 2, 2, 5, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    for sample in (0, 3):
+        sem.sem_rhs_fourier(S.h, 1, sample, b)
+        assert rel_maxerr(b.cpu(), lx.fourier_rhs(P, 1, sample)) < 1e-12
+    S.close()
+
+
+def test_features_match_oracle(sem):
+    P = so.Problem(4, 3, 2, 3, deform=True)
+    S = sem.Solver(4, 3, 2, 3, deform=True)
+    m = sem.sem_x0_create(S.h, 32, 0)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs_fourier(S.h, 2, 1, b)
+    X = np.zeros((S.E, 544), dtype=np.float32)
+    sc = np.zeros(S.E)
+    sem.sem_x0_features(m, b, X, sc)
+    Xo, so_ = lx.features(P, b.cpu().numpy())
+    np.testing.assert_allclose(sc, so_, rtol=1e-12)
+    assert rel_maxerr(X[:, :530], Xo) < 1e-6
+    assert np.all(X[:, 530:] == 0)
+    sem.sem_x0_destroy(m)
+    S.close()
+
+
+def _flat_params(net, offsets, total):
+    flat = np.zeros(total, dtype=np.float32)
+    for q, p in enumerate(net.params):
+        flat[offsets[q]:offsets[q] + p.size] = p.reshape(-1)
+    return flat
+
+
+def test_gradients_match_oracle(sem):
+    S = sem.Solver(2, 2, 2, 3)
+    H = 32
+    m = sem.sem_x0_create(S.h, H, 0)
+    sizes, offs = sem.sem_x0_param_count(m)
+    total = offs[5] + ((sizes[5] + 31) // 32) * 32
+    n3 = 64
+    net = lx.MLP([544, H, H, n3], seed=3)
+    for q in range(1, 6, 2):   # non-zero biases exercise the bias gradients
+        net.params[q] = np.random.default_rng(q).standard_normal(net.params[q].shape) * 0.1
+    sem.sem_x0_params(m, _flat_params(net, offs, total), set_=True)
+    g = np.random.default_rng(11)
+    rows = 40
+    X = g.standard_normal((rows, 544)).astype(np.float32)
+    T = g.standard_normal((rows, n3)).astype(np.float32)
+    ref = net.gradients(X.astype(np.float64), T.astype(np.float64))
+    ref_loss = net.loss(X.astype(np.float64), T.astype(np.float64))
+    for mode, tol in ((0, 1e-5), (1, 2e-2)):
+        grads = np.zeros(total, dtype=np.float32)
+        loss = sem.sem_x0_gradients(m, X, T, rows, mode, grads)
+        assert abs(loss - ref_loss) <= tol * ref_loss * 10
+        for q, r in enumerate(ref):
+            got = grads[offs[q]:offs[q] + r.size].reshape(r.shape).astype(np.float64)
+            err = np.linalg.norm(got - r) / max(np.linalg.norm(r), 1e-30)
+            assert err <= tol, (mode, q, err)
+    sem.sem_x0_destroy(m)
+    S.close()
+
+
+def test_training_reduces_loss_and_guess_is_safe(sem):
+    """Train on solver-made pairs; the energy-scaled guess is continuous and
+    masked, never needs more than a handful of extra iterations, and the
+    iterations it saves are reported."""
+    S = sem.Solver(6, 6, 6, 5, deform=True)
+    m = sem.sem_x0_create(S.h, 64, 1)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    for sample in range(24):
+        sem.sem_rhs_fourier(S.h, 1, sample, b)
+        x, info = S.solve(b, tol=1e-9, maxit=4000, precision=sem.SEM_MIXED_FP32)
+        assert info["rc"] == 0
+        sem.sem_x0_add_pair(m, b, x)
+    first = sem.sem_x0_train(m, 1, 256, 1e-3, seed=0)
+    last = sem.sem_x0_train(m, 30, 256, 1e-3, seed=1)
+    assert last < first
+    P = so.Problem(6, 6, 6, 5, deform=True)
+    x0 = torch.empty_like(b)
+    saved = []
+    for sample in (100, 101):
+        sem.sem_rhs_fourier(S.h, 1, sample, b)
+        sem.sem_x0_predict(m, b, x0, True)
+        xh = x0.cpu().numpy()
+        np.testing.assert_allclose(P.dssum(xh) / P.mult, xh, rtol=1e-12, atol=1e-14)
+        assert np.all(xh[P.mask == 0] == 0)
+        _, i0 = S.solve(b, tol=1e-8, maxit=4000, precision=sem.SEM_FP64)
+        _, i1 = S.solve(b, x0=x0, tol=1e-8, maxit=4000, precision=sem.SEM_FP64)
+        assert i1["rc"] == 0 and i1["relres"] <= 1e-8
+        assert i1["iters"] <= i0["iters"] + 10
+        saved.append(i0["iters"] - i1["iters"])
+    print("iterations saved by the learned guess:", saved)
+    sem.sem_x0_destroy(m)
+    S.close()
