@@ -463,6 +463,10 @@ extern "C" int sem_x0_create(sem_handle h, int hidden, uint64_t seed, sem_x0_mod
     set_error("sem_x0_create: the learned guess needs a box mesh (face neighbours)");
     return SEM_EINVAL;
   }
+  if (h->n * h->n * h->n + 18 > kFeatPad) {
+    set_error("sem_x0_create: the network's 544 inputs hold n^3 + 18 features (N <= 7)");
+    return SEM_EINVAL;
+  }
   *out = nullptr;
   sem_x0_model_s* M = new sem_x0_model_s();
   M->h = h;

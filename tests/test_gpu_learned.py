@@ -41,11 +41,19 @@ def test_features_match_oracle(sem):
     sc = np.zeros(S.E)
     sem.sem_x0_features(m, b, X, sc)
     Xo, so_ = lx.features(P, b.cpu().numpy())
+    nf = P.n ** 3 + 18
     np.testing.assert_allclose(sc, so_, rtol=1e-12)
-    assert rel_maxerr(X[:, :530], Xo) < 1e-6
-    assert np.all(X[:, 530:] == 0)
+    assert rel_maxerr(X[:, :nf], Xo) < 1e-6
+    assert np.all(X[:, nf:] == 0)
     sem.sem_x0_destroy(m)
     S.close()
+
+
+def _bf16(a):
+    """Round float32 values to bfloat16 (round to nearest even), kept as float64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def _flat_params(net, offsets, total):
@@ -70,12 +78,18 @@ def test_gradients_match_oracle(sem):
     rows = 40
     X = g.standard_normal((rows, 544)).astype(np.float32)
     T = g.standard_normal((rows, n3)).astype(np.float32)
-    ref = net.gradients(X.astype(np.float64), T.astype(np.float64))
-    ref_loss = net.loss(X.astype(np.float64), T.astype(np.float64))
-    for mode, tol in ((0, 1e-5), (1, 2e-2)):
+    # FP32 mode against the plain FP64 network; BF16 mode against the FP64
+    # network evaluated on BF16-rounded inputs, targets and weights (what the
+    # BF16 products consume), leaving the rounding of activations and sums
+    net16 = lx.MLP([544, H, H, n3], params=[_bf16(p) if q % 2 == 0 else p.astype(np.float32)
+                                             for q, p in enumerate(net.params)])
+    cases = ((0, 1e-5, net, X, T), (1, 1e-2, net16, _bf16(X), _bf16(T)))
+    for mode, tol, ref_net, Xr, Tr in cases:
+        ref = ref_net.gradients(np.asarray(Xr, np.float64), np.asarray(Tr, np.float64))
+        ref_loss = ref_net.loss(np.asarray(Xr, np.float64), np.asarray(Tr, np.float64))
         grads = np.zeros(total, dtype=np.float32)
         loss = sem.sem_x0_gradients(m, X, T, rows, mode, grads)
-        assert abs(loss - ref_loss) <= tol * ref_loss * 10
+        assert abs(loss - ref_loss) <= tol * ref_loss
         for q, r in enumerate(ref):
             got = grads[offs[q]:offs[q] + r.size].reshape(r.shape).astype(np.float64)
             err = np.linalg.norm(got - r) / max(np.linalg.norm(r), 1e-30)
