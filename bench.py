@@ -172,6 +172,47 @@ def batched_leg(sem, torch):
     return out
 
 
+def learned_leg(sem, torch, train_pairs=128, epochs=20):
+    """Deformed 16^3 elements, N = 7, random Fourier right-hand sides: train
+    the element network on pairs solved by the mixed solver, then compare
+    iterations and time to 1e-8 from x0 = 0 and from the learned guess
+    (inference and energy scaling included in the learned time), FP64 and
+    mixed, on held-out right-hand sides."""
+    S = sem.Solver(16, 16, 16, 7, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    m = sem.sem_x0_create(S.h, 256, 7)
+    t0 = time.perf_counter()
+    for sample in range(train_pairs):
+        sem.sem_rhs_fourier(S.h, 5, sample, b)
+        x, info = S.solve(b, tol=1e-8, maxit=5000, precision=sem.SEM_MIXED_FP32)
+        sem.sem_x0_add_pair(m, b, x)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = sem.sem_x0_train(m, epochs, 4096, 1e-3, seed=0)
+    train_s = time.perf_counter() - t0
+    x0 = torch.empty_like(b)
+    res = {"train_pairs": train_pairs, "rows": train_pairs * S.E, "epochs": epochs,
+           "final_loss": loss, "data_s": gen_s, "train_s": train_s, "tests": []}
+    for sample in (10001, 10002, 10003):
+        sem.sem_rhs_fourier(S.h, 5, sample, b)
+        row = {}
+        for name, prec in (("fp64", sem.SEM_FP64), ("mixed", sem.SEM_MIXED_FP32)):
+            _, iz = S.solve(b, tol=1e-8, maxit=5000, precision=prec)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            sem.sem_x0_predict(m, b, x0, True)
+            _, il = S.solve(b, x0=x0, tol=1e-8, maxit=5000, precision=prec)
+            torch.cuda.synchronize()
+            row[name] = {"zero_iters": iz["iters"], "zero_ms": iz["solve_ms"],
+                         "learned_iters": il["iters"], "learned_ms": (time.perf_counter() - t1) * 1e3,
+                         "learned_converged": il["rc"] == 0}
+        res["tests"].append(row)
+    sem.sem_x0_destroy(m)
+    S.close()
+    return res
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -201,6 +242,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess leg")
     ap.add_argument("--profile", action="store_true",
                     help="small run for ncu captures: 3 fixed mixed iterations + 2 FP32 operator calls")
     ap.add_argument("--profile-batched", action="store_true",
@@ -388,6 +430,8 @@ def main():
         }
         if not args.no_batched:
             line["batched"] = batched_leg(sem, torch)
+        if not args.no_learned:
+            line["learned_x0"] = learned_leg(sem, torch)
         if not args.no_cpu and world >= 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
