@@ -200,8 +200,9 @@ int sem_pcg_solve_ex(sem_handle h, const double* f, const double* x0, double* x,
  * An element-local network (inputs: the element's b_L / s_e, the element
  * mean and standard deviation of G1..G6, the mean of b_L over each face
  * neighbour / s_e; s_e the RMS of b_L on the element; 530 inputs padded to
- * 544 -> hidden -> hidden -> n^3, ReLU) predicts u_L / s_e; the guess is
- * x0 = c * QQ^T(s_e * y) (continuity projection, c = mask / multiplicity),
+ * 544 -> hidden -> hidden -> n^3, ReLU) predicts u_L / (s_e t), t the RMS
+ * of the training targets u_L / s_e; the guess is
+ * x0 = c * QQ^T(s_e t y) (continuity projection, c = mask / multiplicity),
  * optionally scaled by the energy-optimal alpha = <b,c,x0>/<x0,c,A x0>,
  * which never increases the A-norm error over x0 = 0.  Box meshes only.
  * Weights: FP32 master + BF16 copies; products in BF16 with FP32

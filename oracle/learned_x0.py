@@ -22,7 +22,8 @@ Definitions (all per element e of a box mesh, local node order i + n j + n^2 k):
     G1..G6 its element mean and standard deviation; for each face
     (r-, r+, s-, s+, t-, t+) the mean of b_L over the whole neighbouring
     element divided by s_e (0 where the face is on the domain boundary).
-  * targets: x_L / s_e (x the converged solution).
+  * targets: x_L / s_e (x the converged solution); the network is trained
+    on targets / t with t the RMS of all training targets (prediction s_e t y).
   * network: h1 = relu(X W1 + b1), h2 = relu(h1 W2 + b2), y = h2 W3 + b3,
     loss = mean over rows and outputs of (y - t)^2.
   * prediction: u_pred_e = s_e * y_e, x0 = c * QQ^T(u_pred).

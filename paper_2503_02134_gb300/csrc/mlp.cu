@@ -10,7 +10,8 @@
 // Features of element e: b_L / s_e (n^3 values), the element mean and
 // standard deviation of each geometric factor G1..G6, and the mean of b_L
 // over each face neighbour / s_e (0 on the domain boundary);
-// s_e = sqrt(mean_e b_L^2) + 1e-30.  Targets: x_L / s_e.
+// s_e = sqrt(mean_e b_L^2) + 1e-30.  Targets: x_L / s_e, learned divided by
+// their training-set RMS t (prediction s_e * t * y).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -183,12 +184,26 @@ __global__ void elem_targets(const double* __restrict__ x, int n3, int64_t E,
   }
 }
 
-// u_L = s_e * y (FP64 local vector)
+// u_L = s_e * t * y (FP64 local vector; t the training-set target scale)
 __global__ void scale_prediction(const float* __restrict__ Y, int n3, int64_t E,
-                                 const double* __restrict__ escale, double* __restrict__ u) {
+                                 const double* __restrict__ escale, double tscale,
+                                 double* __restrict__ u) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < E * n3;
        q += (int64_t)gridDim.x * blockDim.x)
-    u[q] = (double)Y[q] * escale[q / n3];
+    u[q] = (double)Y[q] * tscale * escale[q / n3];
+}
+
+// sum of squares of BF16 values (per-block partials)
+__global__ void sumsq_bf16(const bf16* __restrict__ T, int64_t count, double* __restrict__ part) {
+  __shared__ double sh[8];
+  double s = 0.0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)__bfloat162float(T[q]);
+    s += v * v;
+  }
+  const double t = block_sum<kDotFP64>(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 __global__ void mul_weight(double* __restrict__ v, const double* __restrict__ c, int64_t L,
@@ -202,12 +217,13 @@ __global__ void mul_weight(double* __restrict__ v, const double* __restrict__ c,
 // dY = 2 (Y - T) / count, and per-block partial sums of (Y - T)^2.
 template <typename TT>
 __global__ void loss_grad(const float* __restrict__ Y, const TT* __restrict__ T, int64_t count,
-                          float scale, float* __restrict__ dY, double* __restrict__ part) {
+                          float scale, float tinv, float* __restrict__ dY,
+                          double* __restrict__ part) {
   __shared__ double sh[8];
   double s = 0.0;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const float d = Y[q] - to_f(T[q]);
+    const float d = Y[q] - tinv * to_f(T[q]);
     dY[q] = scale * d;
     s += (double)d * d;
   }
@@ -275,6 +291,7 @@ struct sem_x0_model_s {
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   sem::bf16* w16 = nullptr;
   int adam_t = 0;
+  double tscale = 1.0;   // RMS of the training targets: the network learns targets / tscale
   // training set
   sem::bf16 *Xtr = nullptr, *Ttr = nullptr;
   int64_t rows = 0, cap = 0;
@@ -408,10 +425,11 @@ static int x0_backward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16*
 
 // loss (mean of squares) and dY for `rows` rows against targets T
 template <typename TT>
-static int x0_loss(sem_x0_model_s& M, cudaStream_t st, int rows, const TT* T, double* loss) {
+static int x0_loss(sem_x0_model_s& M, cudaStream_t st, int rows, const TT* T, double* loss,
+                   float tinv = 1.f) {
   const int64_t count = (int64_t)rows * M.out;
   const int grid = (int)std::min<int64_t>((count + 255) / 256, 4096);
-  loss_grad<TT><<<grid, 256, 0, st>>>(M.Y, T, count, 2.f / (float)count, M.dY, M.part);
+  loss_grad<TT><<<grid, 256, 0, st>>>(M.Y, T, count, 2.f / (float)count, tinv, M.dY, M.part);
   SEM_CUDA(cudaGetLastError());
   if (loss) {
     std::vector<double> h(grid);
@@ -648,6 +666,19 @@ extern "C" int sem_x0_train(sem_x0_model m, int epochs, int batch, float lr, uin
   int rc;
   const int bs = (int)std::min<int64_t>(batch, m->rows);
   if ((rc = x0_ensure_batch(*m, bs))) return rc;
+  // global target scale: the RMS of every stored target value
+  {
+    const int64_t count = m->rows * m->out;
+    const int grid = (int)std::min<int64_t>((count + 255) / 256, 4096);
+    sumsq_bf16<<<grid, 256, 0, st>>>(m->Ttr, count, m->part);
+    std::vector<double> hp(grid);
+    SEM_CUDA(cudaMemcpyAsync(hp.data(), m->part, sizeof(double) * grid, cudaMemcpyDeviceToHost, st));
+    SEM_CUDA(cudaStreamSynchronize(st));
+    double ss = 0.0;
+    for (double v : hp) ss += v;
+    m->tscale = ss > 0.0 ? sqrt(ss / (double)count) : 1.0;
+  }
+  const float tinv = (float)(1.0 / m->tscale);
   std::vector<int> perm((size_t)m->rows);
   for (int64_t q = 0; q < m->rows; ++q) perm[(size_t)q] = (int)q;
   std::mt19937_64 gen(seed);
@@ -665,7 +696,7 @@ extern "C" int sem_x0_train(sem_x0_model m, int epochs, int batch, float lr, uin
       rc = x0_forward(*m, st, bs, m->Xb, nullptr, false);
       const bool last = (ep == epochs - 1);
       double bl = 0.0;
-      if (!rc) rc = x0_loss<bf16>(*m, st, bs, m->Tb, last ? &bl : nullptr);
+      if (!rc) rc = x0_loss<bf16>(*m, st, bs, m->Tb, last ? &bl : nullptr, tinv);
       if (!rc) rc = x0_backward(*m, st, bs, m->Xb, nullptr, false);
       if (!rc) {
         m->adam_t += 1;
@@ -700,7 +731,7 @@ extern "C" int sem_x0_predict(sem_x0_model m, const double* b, double* x0, int e
   if ((rc = x0_features(*m, b, m->Xb, nullptr))) return rc;
   if ((rc = x0_forward(*m, st, rows, m->Xb, nullptr, false))) return rc;
   const int grid = (int)std::min<int64_t>((h.L + 255) / 256, (int64_t)h.num_sms * 8);
-  scale_prediction<<<grid, 256, 0, st>>>(m->Y, m->out, h.E, m->escale, x0);
+  scale_prediction<<<grid, 256, 0, st>>>(m->Y, m->out, h.E, m->escale, m->tscale, x0);
   SEM_CUDA(cudaGetLastError());
   // continuity projection x0 = c * QQ^T(u_pred)
   if ((rc = launch_gs(h, SEM_FP64, x0))) return rc;
