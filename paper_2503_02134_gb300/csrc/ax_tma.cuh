@@ -39,6 +39,35 @@ constexpr size_t tma_smem_bytes() {
   return S::NS * (size_t)(NV + 6) * S::VEC + 2 * (size_t)S::VEC + S::NS * sizeof(uint64_t);
 }
 
+// Dot product of a row of n contiguous shared-memory floats (16- or 8-byte
+// aligned) with n register coefficients, using the widest vector loads the
+// alignment allows.
+template <int n>
+__device__ __forceinline__ float row_dot(const float* __restrict__ row, const float* coef) {
+  float s = 0.f;
+  if constexpr (n % 4 == 0) {
+#pragma unroll
+    for (int l = 0; l < n; l += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(row + l);
+      s += coef[l] * v.x;
+      s += coef[l + 1] * v.y;
+      s += coef[l + 2] * v.z;
+      s += coef[l + 3] * v.w;
+    }
+  } else if constexpr (n % 2 == 0) {
+#pragma unroll
+    for (int l = 0; l < n; l += 2) {
+      const float2 v = *reinterpret_cast<const float2*>(row + l);
+      s += coef[l] * v.x;
+      s += coef[l + 1] * v.y;
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < n; ++l) s += coef[l] * row[l];
+  }
+  return s;
+}
+
 template <int n, bool PCG, int DM, int V>
 __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     ax_tma_kernel(const float* __restrict__ uin, float* __restrict__ wout,
@@ -150,10 +179,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     for (int k = 0; k < n; ++k) wreg[k] = 0.f;
 #pragma unroll
     for (int k = 0; k < n; ++k) {
-      float ur = 0.f, us = 0.f, ut = 0.f;
+      const float ur = row_dot<n>(su_e + k * n2 + jr * n, Di);
+      float us = 0.f, ut = 0.f;
 #pragma unroll
       for (int l = 0; l < n; ++l) {
-        ur += Di[l] * su_e[k * n2 + jr * n + l];
         us += Dj[l] * su_e[k * n2 + l * n + ir];
         ut += sD[k][l] * ureg[l];
       }
@@ -173,12 +202,9 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
 
 #pragma unroll
     for (int k = 0; k < n; ++k) {
-      float wv = wreg[k];
+      float wv = wreg[k] + row_dot<n>(sr_e + k * n2 + jr * n, DiT);
 #pragma unroll
-      for (int l = 0; l < n; ++l) {
-        wv += DiT[l] * sr_e[k * n2 + jr * n + l];
-        wv += DjT[l] * ss_e[k * n2 + l * n + ir];
-      }
+      for (int l = 0; l < n; ++l) wv += DjT[l] * ss_e[k * n2 + l * n + ir];
       if (on_dirichlet(f, i, j, k, n - 1)) wv = 0.f;
       if (act) {
         wout[e * n3 + k * n2 + ij] = wv;

@@ -179,10 +179,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       for (int k = 0; k < n; ++k) wreg[k] = 0.f;
 #pragma unroll
       for (int k = 0; k < n; ++k) {
-        float ur = 0.f, us = 0.f, ut = 0.f;
+        const float ur = row_dot<n>(su_e + k * n2 + jr * n, Di);
+        float us = 0.f, ut = 0.f;
 #pragma unroll
         for (int l = 0; l < n; ++l) {
-          ur += Di[l] * su_e[k * n2 + jr * n + l];
           us += Dj[l] * su_e[k * n2 + l * n + ir];
           ut += sD[k][l] * ureg[l];
         }
@@ -201,12 +201,9 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < n; ++k) {
-        float wv = wreg[k];
+        float wv = wreg[k] + row_dot<n>(sr_e + k * n2 + jr * n, DiT);
 #pragma unroll
-        for (int l = 0; l < n; ++l) {
-          wv += DiT[l] * sr_e[k * n2 + jr * n + l];
-          wv += DjT[l] * ss_e[k * n2 + l * n + ir];
-        }
+        for (int l = 0; l < n; ++l) wv += DjT[l] * ss_e[k * n2 + l * n + ir];
         if (on_dirichlet(f, i, j, k, n - 1)) wv = 0.f;
         if (act) {
           wg[e * n3 + k * n2 + ij] = wv;

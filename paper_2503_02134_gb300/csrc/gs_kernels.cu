@@ -59,7 +59,6 @@ struct GsSum<float, kGsTwoSum> {
 
 constexpr int kGsThreads = 256;
 constexpr int kGsRegCopies = 8;   // copies kept in registers; longer segments reload indices
-constexpr int kGsChunks = 1;      // chunks a warp works on at once (more costs occupancy)
 
 template <typename T, int ACC>
 __device__ __forceinline__ void gs_chunk_generic(T* __restrict__ v, const int* sl, int m) {
@@ -75,64 +74,62 @@ __device__ __forceinline__ void gs_chunk_generic(T* __restrict__ v, const int* s
   }
 }
 
-// A warp takes kGsChunks consecutive chunks (32 segments each, neighbours in
-// global-id order) and issues all their index loads, then all their value
-// gathers, before summing: up to 32 independent loads per lane in flight.
+// A warp walks its chunks (32 segments each) with a one-chunk software
+// pipeline: the descriptor and the index table of the next chunk are loaded
+// before the value gathers of the current one, so every chunk pays one
+// dependent round trip (indices -> values) instead of three.
 template <typename T, int ACC>
 __global__ void __launch_bounds__(kGsThreads)
     gs_bucket_kernel(T* __restrict__ v, const int2* __restrict__ chunks, int64_t nchunks,
                      const int* __restrict__ slots) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  for (int64_t c0 = warp * kGsChunks; c0 < nchunks; c0 += nwarps * kGsChunks) {
-    int m[kGsChunks];
-    const int* sl[kGsChunks];
-    bool small = true;
+  int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= nchunks) return;
+  int2 d = __ldg(chunks + c);
+  int id[kGsRegCopies];
 #pragma unroll
-    for (int u = 0; u < kGsChunks; ++u) {
-      if (c0 + u < nchunks) {
-        const int2 d = __ldg(chunks + c0 + u);
-        m[u] = d.x;
-        sl[u] = slots + d.y + lane;
-      } else {
-        m[u] = 0;
-        sl[u] = slots;
-      }
-      small = small && m[u] <= kGsRegCopies;
-    }
-    if (small) {
-      int id[kGsChunks][kGsRegCopies];
-      T val[kGsChunks][kGsRegCopies];
-#pragma unroll
-      for (int u = 0; u < kGsChunks; ++u)
-#pragma unroll
-        for (int q = 0; q < kGsRegCopies; ++q) id[u][q] = q < m[u] ? __ldg(sl[u] + 32 * q) : -1;
-#pragma unroll
-      for (int u = 0; u < kGsChunks; ++u)
-#pragma unroll
-        for (int q = 0; q < kGsRegCopies; ++q) val[u][q] = id[u][q] >= 0 ? v[id[u][q]] : T(0);
-#pragma unroll
-      for (int u = 0; u < kGsChunks; ++u) {
-        GsSum<T, ACC> acc;
-#pragma unroll
-        for (int q = 0; q < kGsRegCopies; ++q)
-          if (id[u][q] >= 0) acc.add(val[u][q]);
-        const T out = acc.result();
-#pragma unroll
-        for (int q = 0; q < kGsRegCopies; ++q)
-          if (id[u][q] >= 0) v[id[u][q]] = out;
-      }
+  for (int q = 0; q < kGsRegCopies; ++q)
+    id[q] = q < d.x ? __ldg(slots + d.y + lane + 32 * q) : -1;
+  while (true) {
+    const int64_t cn = c + nwarps;
+    const bool has_next = cn < nchunks;
+    const int2 dn = has_next ? __ldg(chunks + cn) : make_int2(0, 0);
+    if (d.x > kGsRegCopies) {
+      gs_chunk_generic<T, ACC>(v, slots + d.y + lane, d.x);
     } else {
-      for (int u = 0; u < kGsChunks; ++u)
-        if (m[u] > 0) gs_chunk_generic<T, ACC>(v, sl[u], m[u]);
+      T val[kGsRegCopies];
+#pragma unroll
+      for (int q = 0; q < kGsRegCopies; ++q) val[q] = id[q] >= 0 ? v[id[q]] : T(0);
+      int idn[kGsRegCopies];
+#pragma unroll
+      for (int q = 0; q < kGsRegCopies; ++q)
+        idn[q] = (has_next && q < dn.x) ? __ldg(slots + dn.y + lane + 32 * q) : -1;
+      GsSum<T, ACC> acc;
+#pragma unroll
+      for (int q = 0; q < kGsRegCopies; ++q)
+        if (id[q] >= 0) acc.add(val[q]);
+      const T out = acc.result();
+#pragma unroll
+      for (int q = 0; q < kGsRegCopies; ++q)
+        if (id[q] >= 0) v[id[q]] = out;
+#pragma unroll
+      for (int q = 0; q < kGsRegCopies; ++q) id[q] = idn[q];
     }
+    if (!has_next) break;
+    if (d.x > kGsRegCopies) {   // the generic path did not prefetch
+#pragma unroll
+      for (int q = 0; q < kGsRegCopies; ++q)
+        id[q] = q < dn.x ? __ldg(slots + dn.y + lane + 32 * q) : -1;
+    }
+    c = cn;
+    d = dn;
   }
 }
 
 int launch_gs_acc(Handle& h, sem_precision p, void* v, int acc) {
   if (h.n_chunks == 0) return 0;
-  const int64_t chunks_per_block = kGsThreads / 32 * kGsChunks;
+  const int64_t chunks_per_block = kGsThreads / 32;
   int64_t g = (h.n_chunks + chunks_per_block - 1) / chunks_per_block;
   int64_t cap = (int64_t)h.num_sms * 8;
   const int grid = (int)(g < cap ? g : cap);

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kVecThreads)
   DotAcc<float, DM> a_rr, a_rz;
   const int64_t n4 = L >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += stride) {
+  auto step = [&](int64_t q) {
     float4 xv = reinterpret_cast<float4*>(x)[q];
     float4 rv = reinterpret_cast<float4*>(r)[q];
     const float4 pv = __ldg(reinterpret_cast<const float4*>(p) + q);
@@ -80,7 +80,14 @@ __global__ void __launch_bounds__(kVecThreads)
     c = weight_of(cv.y) * rv.y; a_rr.add(c, rv.y); a_rz.add(c, mv.y * rv.y);
     c = weight_of(cv.z) * rv.z; a_rr.add(c, rv.z); a_rz.add(c, mv.z * rv.z);
     c = weight_of(cv.w) * rv.w; a_rr.add(c, rv.w); a_rz.add(c, mv.w * rv.w);
+  };
+  // two independent float4 groups per trip keep twice the loads in flight
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; q + stride < n4; q += 2 * stride) {
+    step(q);
+    step(q + stride);
   }
+  if (q < n4) step(q);
   for (int64_t l = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L; l += stride) {
     const float xv = x[l] + alpha * p[l];
     const float rv = r[l] - alpha * w[l];
