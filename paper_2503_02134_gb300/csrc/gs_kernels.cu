@@ -74,56 +74,36 @@ __device__ __forceinline__ void gs_chunk_generic(T* __restrict__ v, const int* s
   }
 }
 
-// A warp walks its chunks (32 segments each) with a one-chunk software
-// pipeline: the descriptor and the index table of the next chunk are loaded
-// before the value gathers of the current one, so every chunk pays one
-// dependent round trip (indices -> values) instead of three.
+// One warp per chunk of 32 segments: coalesced index loads, value gathers,
+// error-free sums, scatter of the sum to every copy.  (Working on several
+// chunks at once, or prefetching the next chunk's indices, measured slower:
+// the extra registers cost more occupancy than the added loads in flight.)
 template <typename T, int ACC>
 __global__ void __launch_bounds__(kGsThreads)
     gs_bucket_kernel(T* __restrict__ v, const int2* __restrict__ chunks, int64_t nchunks,
                      const int* __restrict__ slots) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (c >= nchunks) return;
-  int2 d = __ldg(chunks + c);
-  int id[kGsRegCopies];
-#pragma unroll
-  for (int q = 0; q < kGsRegCopies; ++q)
-    id[q] = q < d.x ? __ldg(slots + d.y + lane + 32 * q) : -1;
-  while (true) {
-    const int64_t cn = c + nwarps;
-    const bool has_next = cn < nchunks;
-    const int2 dn = has_next ? __ldg(chunks + cn) : make_int2(0, 0);
-    if (d.x > kGsRegCopies) {
-      gs_chunk_generic<T, ACC>(v, slots + d.y + lane, d.x);
-    } else {
-      T val[kGsRegCopies];
-#pragma unroll
-      for (int q = 0; q < kGsRegCopies; ++q) val[q] = id[q] >= 0 ? v[id[q]] : T(0);
-      int idn[kGsRegCopies];
-#pragma unroll
-      for (int q = 0; q < kGsRegCopies; ++q)
-        idn[q] = (has_next && q < dn.x) ? __ldg(slots + dn.y + lane + 32 * q) : -1;
-      GsSum<T, ACC> acc;
-#pragma unroll
-      for (int q = 0; q < kGsRegCopies; ++q)
-        if (id[q] >= 0) acc.add(val[q]);
-      const T out = acc.result();
-#pragma unroll
-      for (int q = 0; q < kGsRegCopies; ++q)
-        if (id[q] >= 0) v[id[q]] = out;
-#pragma unroll
-      for (int q = 0; q < kGsRegCopies; ++q) id[q] = idn[q];
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks;
+       c += nwarps) {
+    const int2 d = __ldg(chunks + c);
+    const int m = d.x;
+    const int* sl = slots + d.y + lane;
+    if (m > kGsRegCopies) {
+      gs_chunk_generic<T, ACC>(v, sl, m);
+      continue;
     }
-    if (!has_next) break;
-    if (d.x > kGsRegCopies) {   // the generic path did not prefetch
+    int id[kGsRegCopies];
 #pragma unroll
-      for (int q = 0; q < kGsRegCopies; ++q)
-        id[q] = q < dn.x ? __ldg(slots + dn.y + lane + 32 * q) : -1;
-    }
-    c = cn;
-    d = dn;
+    for (int q = 0; q < kGsRegCopies; ++q) id[q] = q < m ? __ldg(sl + 32 * q) : -1;
+    GsSum<T, ACC> acc;
+#pragma unroll
+    for (int q = 0; q < kGsRegCopies; ++q)
+      if (id[q] >= 0) acc.add(v[id[q]]);
+    const T out = acc.result();
+#pragma unroll
+    for (int q = 0; q < kGsRegCopies; ++q)
+      if (id[q] >= 0) v[id[q]] = out;
   }
 }
 
