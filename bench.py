@@ -172,6 +172,54 @@ def batched_leg(sem, torch):
     return out
 
 
+def order_sweep_leg(sem, torch, hbm_gbs):
+    """Deformed cubes of about 2^24 local DOFs at N = 5, 7, ..., 15: FP32 and
+    FP64 operator (sem_ax_local) throughput with CUDA events, fraction of
+    the HBM roofline (FP32: 32 B per DOF), FP64 flop rate (12 n^4 + 15 n^3
+    per element), and the FP32 result's max-norm error relative to the FP64
+    operator on the same input."""
+    import sem_inputs
+    out = []
+    for N in (5, 7, 9, 11, 13, 15):
+        c = sem_inputs.order_sweep_case(N)
+        stream = torch.cuda.Stream()
+        S = sem.Solver(c.kx, c.ky, c.kz, N, deform=True, stream=stream.cuda_stream)
+        L = S.L
+        with torch.cuda.stream(stream):
+            u64 = torch.rand(L, dtype=torch.float64, device="cuda") * 2 - 1
+            u32 = u64.float()
+            w64 = torch.empty_like(u64)
+            w32 = torch.empty_like(u32)
+        stream.synchronize()
+
+        def timed(fn, u, w, prec, reps):
+            for _ in range(2):
+                fn(S.h, u, w, prec)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn(S.h, u, w, prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        ms32 = timed(sem.sem_ax_local, u32, w32, sem.SEM_MIXED_FP32, 10)
+        ms64 = timed(sem.sem_ax_local, u64, w64, sem.SEM_FP64, 3)
+        err = float((w32.double() - w64).abs().max() / w64.abs().max())
+        n = N + 1
+        flops = S.E * (12 * n ** 4 + 15 * n ** 3)
+        out.append({"N": N, "elements": S.E, "local_dofs": L,
+                    "fp32_gdofs": L / ms32 / 1e6, "fp32_hbm_frac": L * 32 / (ms32 * 1e-3) / 1e9 / hbm_gbs,
+                    "fp32_tflops": flops / (ms32 * 1e-3) / 1e12,
+                    "fp64_gdofs": L / ms64 / 1e6, "fp64_tflops": flops / (ms64 * 1e-3) / 1e12,
+                    "fp32_rel_err_vs_fp64": err,
+                    "fp32_kernel": "bulk-copy staged" if n <= 10 else "register/shared (unstaged)"})
+        S.close()
+        del u64, u32, w64, w32
+    return out
+
+
 def learned_leg(sem, torch, train_pairs=128, epochs=20):
     """Deformed 16^3 elements, N = 7, random Fourier right-hand sides: train
     the element network on pairs solved by the mixed solver, then compare
@@ -243,6 +291,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the order sweep N = 5..15")
     ap.add_argument("--profile", action="store_true",
                     help="small run for ncu captures: 3 fixed mixed iterations + 2 FP32 operator calls")
     ap.add_argument("--profile-batched", action="store_true",
@@ -432,6 +481,8 @@ def main():
             line["batched"] = batched_leg(sem, torch)
         if not args.no_learned:
             line["learned_x0"] = learned_leg(sem, torch)
+        if not args.no_sweep:
+            line["order_sweep"] = order_sweep_leg(sem, torch, hbm)
         if not args.no_cpu and world >= 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))

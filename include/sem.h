@@ -279,6 +279,9 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *   "use_tma"     1 (default) staged FP32 operator where it applies, 0 off
  *   "gs_acc"      mixed-path gather-scatter accumulation: 2 error-free
  *                 FP32 TwoSum (default), 0 FP64, 1 plain FP32
+ *   "l2_persist"  1 (default): during a mixed solve keep the operator output resident
+ *                 in L2 (access-policy window on the handle's stream and a
+ *                 persisting carve-out of the context, released at the end)
  * sem_get_option also reads "ax_tune_ms_plain_<v>", "ax_tune_ms_pcg_<v>"
  * (autotuner timings, ms) and "launches" (kernels enqueued so far).
  * Unknown keys and out-of-range values return SEM_EINVAL. */

@@ -463,6 +463,8 @@ int sem_set_option(sem_handle h, const char* key, int64_t value) {
     h->use_tma = value != 0;
   } else if (k == "gs_acc" && value >= 0 && value <= 2) {
     h->gs_acc = (int)value;
+  } else if (k == "l2_persist" && (value == 0 || value == 1)) {
+    h->l2_persist = value != 0;
   } else {
     set_error("sem_set_option: unknown key or value out of range: " + k);
     return SEM_EINVAL;
@@ -481,6 +483,7 @@ int sem_get_option(sem_handle h, const char* key, double* value) {
   else if (k == "ax_variant_pcg") *value = h->ax_variant_pcg;
   else if (k == "use_tma") *value = h->use_tma ? 1 : 0;
   else if (k == "gs_acc") *value = h->gs_acc;
+  else if (k == "l2_persist") *value = h->l2_persist ? 1 : 0;
   else if (k == "launches") *value = (double)h->launches;
   else if (k.rfind("ax_tune_ms_plain_", 0) == 0 && k.size() == 18 && k[17] >= '0' && k[17] <= '2')
     *value = h->ax_tune_ms[0][k[17] - '0'];

@@ -80,6 +80,7 @@ struct Handle {
   int ax_variant = 0;          // launch variant of the staged FP32 operator (plain / PCG mode)
   int ax_variant_pcg = 0;
   float ax_tune_ms[2][4] = {};  // autotuner timings [plain, PCG][variant]
+  bool l2_persist = true;      // mixed solve: keep w resident in L2 (access-policy window)
   int gs_acc = 2;              // mixed-path accumulation: 2 TwoSum (default), 0 FP64, 1 FP32
 
   // Jacobi

@@ -159,6 +159,52 @@ int ensure_history(Handle& h, int maxit) {
 
 }  // namespace
 
+// Keep the FP32 operator output w resident in L2 between the three kernels
+// of an iteration (written by the operator, gathered and scattered by the
+// gather-scatter, read by the update): an access-policy window marks it
+// persisting for kernels on the handle's stream.  The context's persisting
+// carve-out is released when the solve ends.
+struct L2Window {
+  Handle& h;
+  bool on = false;
+  L2Window(Handle& hh, const void* base, size_t bytes) : h(hh) {
+    if (!h.l2_persist || !base) return;
+    int max_persist = 0, max_window = 0;
+    if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, h.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, h.device) != cudaSuccess ||
+        max_persist <= 0 || max_window <= 0) {
+      cudaGetLastError();
+      return;
+    }
+    const size_t want = std::min(bytes, (size_t)std::min(max_persist, max_window));
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaStreamAttrValue a{};
+    a.accessPolicyWindow.base_ptr = const_cast<void*>(base);
+    a.accessPolicyWindow.num_bytes = want;
+    a.accessPolicyWindow.hitRatio = 1.0f;
+    a.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    if (cudaStreamSetAttribute(h.stream, cudaStreamAttributeAccessPolicyWindow, &a) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    on = true;
+  }
+  ~L2Window() {
+    if (!on) return;
+    cudaStreamAttrValue a{};
+    a.accessPolicyWindow.num_bytes = 0;
+    cudaStreamSetAttribute(h.stream, cudaStreamAttributeAccessPolicyWindow, &a);
+    cudaStreamSynchronize(h.stream);
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0);
+    cudaGetLastError();
+  }
+};
+
 int pcg_solve(Handle& h, const double* f, const double* x0, double* x, const sem_solve_opts& o,
               sem_info* info) {
   const double tol = o.tol > 0 ? o.tol : 1e-8;
@@ -231,6 +277,7 @@ int pcg_solve(Handle& h, const double* f, const double* x0, double* x, const sem
     SEM_CUDA(cudaEventRecord(h.ev1, h.stream));
     if ((rc = fp64_residual(h, f, false, &res.relres_true))) { restore(); return rc; }
   } else if (prec != SEM_FP32_ALL && !o.no_refine && !fixed && o.refine_mode == 0) {
+    L2Window l2(h, h.w32, sizeof(float) * (size_t)h.L);
     // Mixed with reliable updates: one FP32 CG recursion for A x = f with
     // x = x64 + x32.  Each time its residual has fallen by `delta` the
     // correction is folded into x64, the FP64 true residual is recomputed and
