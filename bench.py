@@ -207,13 +207,19 @@ def order_sweep_leg(sem, torch, hbm_gbs):
         ms32 = timed(sem.sem_ax_local, u32, w32, sem.SEM_MIXED_FP32, 10)
         ms64 = timed(sem.sem_ax_local, u64, w64, sem.SEM_FP64, 3)
         err = float((w32.double() - w64).abs().max() / w64.abs().max())
+        tc = {}
+        for name, prec in (("tf32", sem.SEM_MIXED_TF32), ("bf16x3", sem.SEM_MIXED_BF16X3)):
+            ms = timed(sem.sem_ax_local, u32, w32, prec, 5)
+            tc[name] = {"gdofs": L / ms / 1e6,
+                        "hbm_frac": L * 32 / (ms * 1e-3) / 1e9 / hbm_gbs,
+                        "rel_err_vs_fp64": float((w32.double() - w64).abs().max() / w64.abs().max())}
         n = N + 1
         flops = S.E * (12 * n ** 4 + 15 * n ** 3)
         out.append({"N": N, "elements": S.E, "local_dofs": L,
                     "fp32_gdofs": L / ms32 / 1e6, "fp32_hbm_frac": L * 32 / (ms32 * 1e-3) / 1e9 / hbm_gbs,
                     "fp32_tflops": flops / (ms32 * 1e-3) / 1e12,
                     "fp64_gdofs": L / ms64 / 1e6, "fp64_tflops": flops / (ms64 * 1e-3) / 1e12,
-                    "fp32_rel_err_vs_fp64": err,
+                    "fp32_rel_err_vs_fp64": err, "tensor_cores": tc,
                     "fp32_kernel": "bulk-copy staged" if n <= 10 else "register/shared (unstaged)"})
         S.close()
         del u64, u32, w64, w32

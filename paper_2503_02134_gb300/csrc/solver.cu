@@ -26,8 +26,12 @@ namespace sem {
 int ax_dispatch_fp64(Handle& h, const double* u, double* w, const AxPrologue* pro);
 int ax_dispatch_fp32(Handle& h, const float* u, float* w, const AxPrologue* pro, int dm);
 
+int ax_dispatch_tc(Handle& h, const float* u, float* w, sem_precision p);
+
 int launch_ax_local(Handle& h, sem_precision p, const void* u, void* w, const AxPrologue* pro) {
   if (p == SEM_FP64) return ax_dispatch_fp64(h, (const double*)u, (double*)w, pro);
+  if ((p == SEM_MIXED_TF32 || p == SEM_MIXED_BF16X3) && !pro)
+    return ax_dispatch_tc(h, (const float*)u, (float*)w, p);
   const int dm = p == SEM_FP32_ALL ? kDotFP32 : kDotDot2;
   return ax_dispatch_fp32(h, (const float*)u, (float*)w, pro, dm);
 }

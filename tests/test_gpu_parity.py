@@ -406,3 +406,30 @@ def test_reliable_updates_and_restarts_both_converge(sem):
     h = res[0]["history"]
     assert h[0] == pytest.approx(1.0, rel=1e-6) and h[-1] <= 1e-8
     S.close()
+
+
+@pytest.mark.parametrize("kx,ky,kz,N", [(3, 2, 2, 3), (3, 2, 3, 4), (2, 3, 2, 7), (2, 2, 3, 9),
+                                        (2, 2, 1, 11), (2, 1, 2, 15)])
+def test_ax_tensor_cores(sem, kx, ky, kz, N):
+    """D-contractions on tensor cores: TF32 products and the three-product
+    BF16 split, FP32 accumulation.  Error relative to the FP64 oracle: TF32
+    keeps 10 mantissa bits (unit roundoff 2^-11), the BF16 split ~16."""
+    P = so.Problem(kx, ky, kz, N, deform=True)
+    S = sem.Solver(kx, ky, kz, N, deform=True)
+    u = sem_inputs.uniform_local(P.L, seed=61, dtype=np.float32)
+    ref = P.mask * P.ax_local(u.astype(np.float64))
+    w = torch.empty(P.L, dtype=torch.float32, device="cuda")
+    errs = {}
+    for name, prec, tol in (("tf32", sem.SEM_MIXED_TF32, 2.0 ** -11 * 8 * P.n),
+                            ("bf16x3", sem.SEM_MIXED_BF16X3, 2.0 ** -16 * 8 * P.n)):
+        sem.sem_ax_local(S.h, cu(u, torch.float32), w, prec)
+        errs[name] = rel_maxerr(w.cpu(), ref)
+        assert errs[name] < tol, (name, errs[name], tol)
+    sem.sem_ax_local(S.h, cu(u, torch.float32), w, sem.SEM_MIXED_FP32)
+    errs["fp32"] = rel_maxerr(w.cpu(), ref)
+    assert errs["bf16x3"] < errs["tf32"]
+    # assembled operator through the same path
+    sem.sem_ax(S.h, cu(u, torch.float32), w, sem.SEM_MIXED_TF32)
+    assert rel_maxerr(w.cpu(), P.ax(u.astype(np.float64))) < 2.0 ** -11 * 8 * P.n
+    print(N, errs)
+    S.close()
