@@ -35,6 +35,33 @@ WORKLOAD_NAME = "deformed 32x32x32 hex, N=7 (16.8M local DOFs), Jacobi PCG to 1e
 CPU_SAMPLE = dict(k=8, N=7, iters=12)
 
 
+class EnergyMeter:
+    """Total energy counter of one GPU through the driver's NVML library
+    (ctypes, read-only: nvmlDeviceGetTotalEnergyConsumption, millijoules
+    since driver load).  None when the library or the counter is missing."""
+
+    def __init__(self, index):
+        import ctypes
+        self.ok = False
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            self.dev = ctypes.c_void_p()
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.dev)) != 0:
+                return
+            self.ctypes = ctypes
+            self.ok = self.read() is not None
+        except OSError:
+            pass
+
+    def read(self):
+        v = self.ctypes.c_ulonglong()
+        if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.dev, self.ctypes.byref(v)) != 0:
+            return None
+        return v.value / 1e3   # joules
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -406,7 +433,21 @@ def main():
     launches = sum(i["launches"] for i in infos)
     ok = all(i["rc"] == 0 and i["relres_true"] <= W["tol"] * 1.0000001 for i in infos)
 
-    # FP64 time to solution on the same problem (untimed by the step loop)
+    # FP64 time to solution on the same problem (untimed by the step loop),
+    # and energy to solution of both (NVML counter around each solve)
+    meter = EnergyMeter(local)
+    energy = None
+    if meter.ok:
+        energy = {}
+        for name, prec in (("fp64", sem.SEM_FP64), ("mixed", sem.SEM_MIXED_FP32)):
+            torch.cuda.synchronize()
+            j0 = meter.read()
+            inf_e = step(prec)
+            torch.cuda.synchronize()
+            j1 = meter.read()
+            energy[name] = {"joules": j1 - j0, "solve_ms": inf_e["solve_ms"]}
+        energy["gain"] = energy["fp64"]["joules"] / max(energy["mixed"]["joules"], 1e-9)
+        energy["note"] = "whole-GPU counter, includes idle and host-poll time"
     info64 = step(sem.SEM_FP64)
     info_mixed = infos[-1]
 
@@ -473,6 +514,7 @@ def main():
             "fp64": {"time_to_solution_ms": info64["solve_ms"], "iterations": info64["iters"],
                      "relres_true": info64["relres_true"]},
             "speedup_vs_fp64": info64["solve_ms"] / ms,
+            "energy_to_solution": energy,
             "ax_gdofs_fp32": L / (ax32_ms * 1e-3) / 1e9,
             "ax_gdofs_fp32_with_gs": L / (ax32_full_ms * 1e-3) / 1e9,
             "ax_gdofs_fp64": L / (ax64_ms * 1e-3) / 1e9,
