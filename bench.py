@@ -33,6 +33,10 @@ WORKLOAD = dict(kx=32, ky=32, kz=32, N=7, deform=True, rhs="uniform[-1,1) per gl
 WORKLOAD_NAME = "deformed 32x32x32 hex, N=7 (16.8M local DOFs), Jacobi PCG to 1e-8, mixed FP32/FP64"
 # a bounded sample of the same work for the CPU oracle: 8x8x8 elements, N = 7, deformed
 CPU_SAMPLE = dict(k=8, N=7, iters=12)
+# DRAM bytes (read + write) per local DOF of one launch, from an ncu capture
+# of the current kernels (the profile summaries under profiles/ give the
+# commands); None until measured for the kernel as it stands.
+TRAFFIC = {"operator_pcg": None, "operator_plain": None}
 
 
 class EnergyMeter:
@@ -474,14 +478,41 @@ def main():
     ax32_full_ms = time_ax(sem.SEM_MIXED_FP32, local_only=False)
     ax64_ms = time_ax(sem.SEM_FP64, reps=5)
     hbm, peak_kind = peaks()
-    bytes_per_dof = 32.0   # FP32: read u + 6 G, write w
-    achieved = L * bytes_per_dof / (ax32_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
-                "kernel": "ax_kernel<8,float> (sem_ax_local, FP32 element operator)",
-                "algorithmic_bytes_per_launch": L * bytes_per_dof, "launch_ms": ax32_ms,
-                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
-                else "fallback 6.8 TB/s"}
+    peak_source = (f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                   else "fallback 6.8 TB/s")
+
+    # per-kernel device times inside a mixed solve: the library records CUDA
+    # events on its own stream around each launch of every iteration (graphs
+    # off for this one untimed solve)
+    sem.sem_set_option(S.h, "kernel_timing", 1)
+    info_kt = step()
+    kt = {k: sem.sem_get_option(S.h, k) for k in ("kt_iters", "kt_ms_ax", "kt_ms_gs", "kt_ms_update")}
+    sem.sem_set_option(S.h, "kernel_timing", 0)
+    it_step = info_mixed["iters"]
+    shares = {name: kt[key] * it_step / ms for name, key in
+              (("operator_pcg", "kt_ms_ax"), ("gather_scatter", "kt_ms_gs"), ("update", "kt_ms_update"))}
+
+    # dominant kernel of the step: the PCG-mode FP32 operator (Jacobi +
+    # p update prologue, Dot2 p.w epilogue)
+    bytes_pcg = 44.0   # read r, J^-1, p_old, 6 G; write p, w (FP32)
+    ax_pcg_ms = kt["kt_ms_ax"]
+    ach = L * bytes_pcg / (ax_pcg_ms * 1e-3) / 1e9 if ax_pcg_ms > 0 else 0.0
+    traffic = TRAFFIC.get("operator_pcg")
+    roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": traffic * L if traffic else None,
+                "kernel": f"ax_tma_kernel<{W['N'] + 1},true> (FP32 operator, PCG mode)",
+                "algorithmic_bytes_per_launch": L * bytes_pcg, "launch_ms": ax_pcg_ms,
+                "timing": "CUDA events on the library stream around every launch of one mixed solve",
+                "iterations_timed": kt["kt_iters"], "peak_source": peak_source}
+    bytes_plain = 32.0   # FP32: read u + 6 G, write w
+    ach_plain = L * bytes_plain / (ax32_ms * 1e-3) / 1e9
+    traffic_plain = TRAFFIC.get("operator_plain")
+    roofline_plain = {"bound": "hbm", "achieved": ach_plain, "peak": hbm, "unit": "GB/s",
+                      "frac": ach_plain / hbm,
+                      "traffic": traffic_plain * L if traffic_plain else None,
+                      "kernel": f"ax_tma_kernel<{W['N'] + 1},false> (sem_ax_local, FP32 operator)",
+                      "algorithmic_bytes_per_launch": L * bytes_plain, "launch_ms": ax32_ms,
+                      "peak_source": peak_source}
 
     # end to end through the C-ABI with host (pinned) buffers
     fh = torch.empty(L, dtype=torch.float64, pin_memory=True)
@@ -518,7 +549,11 @@ def main():
             "ax_gdofs_fp32": L / (ax32_ms * 1e-3) / 1e9,
             "ax_gdofs_fp32_with_gs": L / (ax32_full_ms * 1e-3) / 1e9,
             "ax_gdofs_fp64": L / (ax64_ms * 1e-3) / 1e9,
-            "roofline": roofline, "clocks": clocks.summary(), "e2e": e2e,
+            "roofline": roofline, "roofline_operator_plain": roofline_plain,
+            "kernel_ms": {"operator_pcg": kt["kt_ms_ax"], "gather_scatter": kt["kt_ms_gs"],
+                          "update": kt["kt_ms_update"]},
+            "kernel_share_of_step": shares,
+            "clocks": clocks.summary(), "e2e": e2e,
             "autotune": {k: sem.sem_get_option(S.h, k) for k in
                          ("ax_variant", "ax_variant_pcg", "ax_tune_ms_plain_0", "ax_tune_ms_plain_1",
                           "ax_tune_ms_plain_2", "ax_tune_ms_pcg_0", "ax_tune_ms_pcg_1",

@@ -282,8 +282,15 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *   "l2_persist"  1 (default): during a mixed solve keep the operator output resident
  *                 in L2 (access-policy window on the handle's stream and a
  *                 persisting carve-out of the context, released at the end)
+ *   "kernel_timing" 1: PCG solves run without graphs and time each
+ *                 iteration's operator, gather-scatter and update launches
+ *                 with CUDA events on the handle's stream (the events add
+ *                 small gaps between launches); 0 (default) off.  Setting
+ *                 it, either way, clears the sums.
  * sem_get_option also reads "ax_tune_ms_plain_<v>", "ax_tune_ms_pcg_<v>"
- * (autotuner timings, ms) and "launches" (kernels enqueued so far).
+ * (autotuner timings, ms), "launches" (kernels enqueued so far),
+ * "kt_iters" (iterations timed) and "kt_ms_ax", "kt_ms_gs",
+ * "kt_ms_update" (average device time per launch, ms).
  * Unknown keys and out-of-range values return SEM_EINVAL. */
 int sem_set_option(sem_handle h, const char* key, int64_t value);
 int sem_get_option(sem_handle h, const char* key, double* value);

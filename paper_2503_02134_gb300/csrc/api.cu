@@ -60,6 +60,7 @@ static void free_handle(Handle* h) {
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  for (cudaEvent_t e : h->kt_events) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete static_cast<sem_handle_s*>(h);
 }
@@ -465,6 +466,11 @@ int sem_set_option(sem_handle h, const char* key, int64_t value) {
     h->gs_acc = (int)value;
   } else if (k == "l2_persist" && (value == 0 || value == 1)) {
     h->l2_persist = value != 0;
+  } else if (k == "kernel_timing" && (value == 0 || value == 1)) {
+    h->kernel_timing = value != 0;   // setting it (either way) clears the sums
+    h->kt_ms[0] = h->kt_ms[1] = h->kt_ms[2] = 0.0;
+    h->kt_iters = 0;
+    h->kt_recorded = 0;
   } else {
     set_error("sem_set_option: unknown key or value out of range: " + k);
     return SEM_EINVAL;
@@ -485,6 +491,12 @@ int sem_get_option(sem_handle h, const char* key, double* value) {
   else if (k == "gs_acc") *value = h->gs_acc;
   else if (k == "l2_persist") *value = h->l2_persist ? 1 : 0;
   else if (k == "launches") *value = (double)h->launches;
+  else if (k == "kernel_timing") *value = h->kernel_timing ? 1 : 0;
+  else if (k == "kt_iters") *value = (double)h->kt_iters;
+  else if (k == "kt_ms_ax" || k == "kt_ms_gs" || k == "kt_ms_update") {
+    const int q = k == "kt_ms_ax" ? 0 : k == "kt_ms_gs" ? 1 : 2;
+    *value = h->kt_iters ? h->kt_ms[q] / (double)h->kt_iters : 0.0;
+  }
   else if (k.rfind("ax_tune_ms_plain_", 0) == 0 && k.size() == 18 && k[17] >= '0' && k[17] <= '2')
     *value = h->ax_tune_ms[0][k[17] - '0'];
   else if (k.rfind("ax_tune_ms_pcg_", 0) == 0 && k.size() == 16 && k[15] >= '0' && k[15] <= '2')

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/sem.h"
 
@@ -116,6 +117,15 @@ struct Handle {
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+
+  // Per-kernel timing of PCG iterations (option "kernel_timing"): graphs
+  // off, an event before and after each of the operator, gather-scatter and
+  // update launches of every iteration of a chunk, read after the chunk.
+  bool kernel_timing = false;
+  std::vector<cudaEvent_t> kt_events;   // 4 per iteration of the current chunk
+  int kt_recorded = 0;                  // iterations recorded in the current chunk
+  double kt_ms[3] = {};                 // summed device time [operator, gs, update]
+  int64_t kt_iters = 0;                 // iterations summed
 };
 
 // ------------------------------------------------------------------ errors

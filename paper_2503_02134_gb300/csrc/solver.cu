@@ -75,18 +75,52 @@ constexpr int kStagWindow = 200;
 
 enum GraphKind { kG64 = 0, kGMixed = 1, kGFP32 = 2 };
 
+// Timing mode: record event q (0..3) of iteration `it` of the chunk on the
+// handle's stream (events are created once and kept).
+int kt_mark(Handle& h, int it, int q) {
+  const size_t idx = 4 * (size_t)it + q;
+  while (h.kt_events.size() <= idx) {
+    cudaEvent_t e = nullptr;
+    SEM_CUDA(cudaEventCreate(&e));
+    h.kt_events.push_back(e);
+  }
+  SEM_CUDA(cudaEventRecord(h.kt_events[idx], h.stream));
+  return 0;
+}
+
+// Timing mode: add the kernel times of the first `ran` recorded iterations
+// of the chunk (the stream has been synchronised by the caller); launches
+// after the solve finished return at once and are not counted.
+int kt_collect(Handle& h, int ran) {
+  const int m = std::max(0, std::min(h.kt_recorded, ran));
+  for (int it = 0; it < m; ++it) {
+    for (int q = 0; q < 3; ++q) {
+      float ms = 0.f;
+      SEM_CUDA(cudaEventElapsedTime(&ms, h.kt_events[4 * it + q], h.kt_events[4 * it + q + 1]));
+      h.kt_ms[q] += ms;
+    }
+  }
+  h.kt_iters += m;
+  h.kt_recorded = 0;
+  return 0;
+}
+
 // Enqueue `iters` PCG iterations (no host interaction).
 int enqueue_iterations(Handle& h, GraphKind kind, int iters) {
   AxPrologue pro;
   pro.scal = h.scal;
   pro.pap_partials = h.partials;
+  const bool kt = h.kernel_timing;
   for (int it = 0; it < iters; ++it) {
     int rc;
+    if (kt && (rc = kt_mark(h, it, 0))) return rc;
     if (kind == kG64) {
       pro.r = h.r64;
       pro.minv = h.minv64;
       if ((rc = ax_dispatch_fp64(h, h.p64, h.w64, &pro))) return rc;
+      if (kt && (rc = kt_mark(h, it, 1))) return rc;
       if ((rc = launch_gs(h, SEM_FP64, h.w64))) return rc;
+      if (kt && (rc = kt_mark(h, it, 2))) return rc;
       if ((rc = launch_cg_update64(h, h.x64, h.r64, h.p64, h.w64, h.scal, h.hist_dev))) return rc;
     } else {
       const int dm = kind == kGFP32 ? kDotFP32 : kDotDot2;
@@ -94,17 +128,22 @@ int enqueue_iterations(Handle& h, GraphKind kind, int iters) {
       pro.r = h.r32;
       pro.minv = h.minv32;
       if ((rc = ax_dispatch_fp32(h, h.p32, h.w32, &pro, dm))) return rc;
+      if (kt && (rc = kt_mark(h, it, 1))) return rc;
       if ((rc = launch_gs(h, gp, h.w32))) return rc;
+      if (kt && (rc = kt_mark(h, it, 2))) return rc;
       if ((rc = launch_cg_update32(h, dm, h.x32, h.r32, h.p32, h.w32, h.minv32, h.scal,
                                    h.hist_dev)))
         return rc;
     }
+    if (kt && (rc = kt_mark(h, it, 3))) return rc;
   }
+  if (kt) h.kt_recorded = iters;
   return 0;
 }
 
 int run_chunk(Handle& h, GraphKind kind, int chunk, bool use_graph) {
-  if (!use_graph) return enqueue_iterations(h, kind, chunk);
+  // per-kernel timing records events between launches: no graphs
+  if (!use_graph || h.kernel_timing) return enqueue_iterations(h, kind, chunk);
   if (!h.graph_exec[kind] || h.graph_chunk[kind] != chunk) {
     if (h.graph_exec[kind]) {
       cudaGraphExecDestroy(h.graph_exec[kind]);
@@ -132,12 +171,18 @@ int run_chunk(Handle& h, GraphKind kind, int chunk, bool use_graph) {
   return 0;
 }
 
-// Iterate until the device says done; returns 0 or an error.
+// Iterate until the device says done; returns 0 or an error.  On entry
+// *fin holds the scalars as they stand (read by the caller).
 int iterate(Handle& h, GraphKind kind, int chunk, bool use_graph, PcgScalars* fin) {
+  int base = fin->iter;
   for (;;) {
     int rc = run_chunk(h, kind, chunk, use_graph);
     if (rc) return rc;
     if ((rc = read_scalars(h, h.scal, fin))) return rc;
+    if (h.kernel_timing) {
+      if ((rc = kt_collect(h, fin->iter - base))) return rc;
+      base = fin->iter;
+    }
     if (fin->err) {
       set_error("pcg: a bounded device wait gave up (bulk copy did not complete)");
       return SEM_ETIMEOUT;

@@ -325,6 +325,27 @@ def test_graph_and_plain_launch_agree(sem):
     S.close()
 
 
+def test_kernel_timing_mode(sem):
+    """Per-kernel event timing changes nothing in the result (same kernels,
+    events between them), counts every iteration and reports positive
+    per-launch device times; turning it off clears the sums."""
+    S = sem.Solver(4, 4, 4, 7, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 4, b)
+    for prec in (sem.SEM_FP64, sem.SEM_MIXED_FP32):
+        x1, i1 = S.solve(b, tol=1e-9, maxit=2000, precision=prec)
+        sem.sem_set_option(S.h, "kernel_timing", 1)
+        x2, i2 = S.solve(b, tol=1e-9, maxit=2000, precision=prec)
+        assert sem.sem_get_option(S.h, "kt_iters") == i2["iters"]
+        for k in ("kt_ms_ax", "kt_ms_gs", "kt_ms_update"):
+            assert 0 < sem.sem_get_option(S.h, k) < i2["solve_ms"]
+        sem.sem_set_option(S.h, "kernel_timing", 0)
+        assert sem.sem_get_option(S.h, "kt_iters") == 0
+        assert i1["iters"] == i2["iters"]
+        assert torch.equal(x1, x2)
+    S.close()
+
+
 def test_launch_variants_agree(sem):
     """Every staged-operator launch variant and the unstaged kernel give the
     same FP32 result (identical arithmetic per element); the set-up
