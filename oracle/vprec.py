@@ -30,6 +30,17 @@ def round_t(x, t: int):
     return np.ldexp(np.rint(scaled), e - (t + 1))
 
 
+def random_rounding(x, t, rng):
+    """Monte Carlo arithmetic's random rounding (the paper's Sec. 2 MCA mode):
+    inexact(x) = x + 2^(e_x - t) xi, xi uniform in [-1/2, 1/2), with e_x the
+    exponent of x (x = m 2^e_x, 1 <= |m| < 2); zero stays zero.  The draws
+    xi come from the caller's numpy Generator."""
+    x = np.asarray(x, dtype=np.float64)
+    _, e = np.frexp(x)                       # x = m 2^e, 0.5 <= |m| < 1 -> e_x = e - 1
+    xi = rng.random(x.shape) - 0.5
+    return np.where(x == 0.0, 0.0, x + np.ldexp(xi, e - 1 - t))
+
+
 def _contract(D, U, axis, t):
     """sum_l D[o, l] U[..., l along `axis`] with every product and partial sum rounded."""
     n = D.shape[0]

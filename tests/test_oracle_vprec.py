@@ -43,3 +43,21 @@ def test_attainable_residual_improves_with_mantissa_bits():
     assert floors[7] > floors[10] > floors[16] > floors[23] > floors[52]
     assert floors[23] > 1e-9          # FP32 cannot reach the paper's 1e-10 on its own
     assert floors[52] < 1e-10
+
+
+def test_random_rounding_noise_is_unbiased_and_bounded():
+    """MCA random rounding: |inexact(x) - x| <= 2^(e_x - t - 1) with e_x the
+    exponent of x, mean noise ~ 0, zero unchanged; the noise relative to x
+    spans the t-bit spacing (x = 1: 2^-t wide)."""
+    g = np.random.default_rng(1)
+    t = 10
+    x = g.standard_normal(200000) * 10.0 ** g.uniform(-5, 5, 200000)
+    x[:10] = 0.0
+    y = vprec.random_rounding(x, t, np.random.default_rng(2))
+    assert np.all(y[:10] == 0.0)
+    ex = np.floor(np.log2(np.abs(x[10:])))
+    d = (y[10:] - x[10:]) / np.exp2(ex - t)
+    assert np.all(np.abs(d) <= 0.5 + 1e-9)
+    assert abs(d.mean()) < 0.01 and abs(d.std() * np.sqrt(12) - 1.0) < 0.01   # U[-1/2, 1/2)
+    ones = vprec.random_rounding(np.ones(100000), t, np.random.default_rng(3))
+    assert np.ptp(ones) > 0.99 * 2.0 ** -t and np.ptp(ones) <= 2.0 ** -t
