@@ -282,6 +282,12 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *   "l2_persist"  1 (default): during a mixed solve keep the operator output resident
  *                 in L2 (access-policy window on the handle's stream and a
  *                 persisting carve-out of the context, released at the end)
+ *   "fuse_gs"     1 (default): in FP32 and mixed PCG iterations on a box mesh
+ *                 (sem_setup without gid) the direct-stiffness summation is
+ *                 folded into the vector update -- each copy of a shared node
+ *                 gathers the others, found from its position, in ascending
+ *                 local index with the accumulation "gs_acc" selects, which
+ *                 gives the separate pass's bits; 0: separate pass
  *   "kernel_timing" 1: PCG solves run without graphs and time each
  *                 iteration's operator, gather-scatter and update launches
  *                 with CUDA events on the handle's stream (the events add

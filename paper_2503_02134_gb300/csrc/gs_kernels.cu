@@ -21,41 +21,10 @@
 //   all-FP32 variant     -> plain FP32 sums.
 #include <algorithm>
 
+#include "gs_sum.cuh"
 #include "sem_internal.cuh"
 
 namespace sem {
-
-enum GsAcc { kGsFP64 = 0, kGsFP32 = 1, kGsTwoSum = 2 };
-
-template <typename T, int ACC>
-struct GsSum;
-
-template <typename T>
-struct GsSum<T, kGsFP64> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(T x) { s += (double)x; }
-  __device__ __forceinline__ T result() const { return (T)s; }
-};
-
-template <>
-struct GsSum<float, kGsFP32> {
-  float s = 0.f;
-  __device__ __forceinline__ void add(float x) { s = __fadd_rn(s, x); }
-  __device__ __forceinline__ float result() const { return s; }
-};
-
-template <>
-struct GsSum<float, kGsTwoSum> {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = __fadd_rn(s, x);
-    const float z = __fsub_rn(t, s);
-    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
-    s = t;
-    c = __fadd_rn(c, e);
-  }
-  __device__ __forceinline__ float result() const { return __fadd_rn(s, c); }
-};
 
 constexpr int kGsThreads = 256;
 constexpr int kGsRegCopies = 8;   // copies kept in registers; longer segments reload indices

@@ -42,6 +42,9 @@ int launch_cg_update64(Handle& h, double* x, double* r, const double* p, const d
                        PcgScalars* s, double* hist);
 int launch_cg_update32(Handle& h, int dm, float* x, float* r, const float* p, const float* w,
                        const float* minv, PcgScalars* s, double* hist);
+bool gs_fusable(const Handle& h);
+int launch_cg_update32_gs(Handle& h, int dm, int acc, float* x, float* r, const float* p,
+                          const float* w, const float* minv, PcgScalars* s, double* hist);
 int launch_cg_init64(Handle& h, double* r, const double* b, const double* ax, const double* minv,
                      PcgScalars* s, double* hist);
 int launch_cg_init32(Handle& h, int dm, float* r, const float* b, const float* ax,

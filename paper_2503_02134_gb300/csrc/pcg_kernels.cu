@@ -4,6 +4,7 @@
 // convergence test, and the scalar recurrences beta = rtz / rtz_old.
 // Also: the initial residual, the weighted dot (glsc3) and the FP64
 // refinement helpers of the mixed path.
+#include "gs_sum.cuh"
 #include "pcg.cuh"
 
 namespace sem {
@@ -97,6 +98,135 @@ __global__ void __launch_bounds__(kVecThreads)
     a_rr.add(c, rv);
     a_rz.add(c, minv[l] * rv);
   }
+  const double v0 = block_sum<DM>(a_rr.value(), sh);
+  const double v1 = block_sum<DM>(a_rz.value(), sh);
+  const double vals[2] = {v0, v1};
+  if (publish_and_elect(vals, 2, partials, &s->counter[1])) {
+    const double rtr = reduce_partials<DM>(partials, 0, sh);
+    const double rtz = reduce_partials<DM>(partials, 1, sh);
+    if (threadIdx.x == 0) {
+      finish_iteration(s, rtr, rtz, hist);
+      s->counter[1] = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Update with the direct-stiffness summation folded in (box meshes).
+//
+// In the CG loop w = QQ^T A_L p is consumed only by r -= alpha w (the p.w
+// dot is taken on the unsummed w with the mask as weight, which is the same
+// number because p is continuous).  So instead of a separate pass that sums
+// the copies of every shared node and writes the sum back to each copy, each
+// local entry here gathers the copies of its own node and sums them itself.
+// On a box mesh the copies are found from the entry's position: a node on
+// face i = 0 of element e is also node i = n-1 of element e-1 (when the face
+// is not on the domain boundary), and likewise in j (element e -+ kx) and k
+// (element e -+ kx ky); edges and corners take the products of these.  The
+// copies are visited in ascending element order -- ascending local index,
+// the order of the separate gather-scatter -- with the same accumulator, so
+// every copy computes the same bits and the result equals the unfused path
+// bit for bit.  Nodes with one copy keep w unchanged, as there.
+
+// Any n: the float4 traversal of cg_update32_v4_kernel (same groups, same
+// dot order), each component gathered on its own.
+template <int DM, int ACC>
+__global__ void __launch_bounds__(kVecThreads)
+    cg_update32_gs_kernel(float* __restrict__ x, float* __restrict__ r,
+                          const float* __restrict__ p, const float* __restrict__ w,
+                          const uint8_t* __restrict__ cw, const float* __restrict__ minv,
+                          const uint8_t* __restrict__ faces, BoxNbr b, int64_t L,
+                          PcgScalars* __restrict__ s, double* __restrict__ partials,
+                          double* __restrict__ hist) {
+  __shared__ double sh[kVecThreads / 32];
+  if (s->done) return;
+  const float alpha = (float)s->alpha;
+  DotAcc<float, DM> a_rr, a_rz;
+  auto node = [&](int64_t l) -> float {
+    const int64_t e = l / b.n3;
+    const int rem = (int)(l - e * b.n3);
+    return gs_gather_node<ACC>(w, l, rem % b.n, (rem / b.n) % b.n, rem / (b.n * b.n),
+                               __ldg(faces + e), b);
+  };
+  const int64_t n4 = L >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  auto step = [&](int64_t q) {
+    float4 xv = reinterpret_cast<float4*>(x)[q];
+    float4 rv = reinterpret_cast<float4*>(r)[q];
+    const float4 pv = __ldg(reinterpret_cast<const float4*>(p) + q);
+    const float4 mv = __ldg(reinterpret_cast<const float4*>(minv) + q);
+    const uchar4 cv = __ldg(reinterpret_cast<const uchar4*>(cw) + q);
+    float4 wv;
+    wv.x = node(4 * q);
+    wv.y = node(4 * q + 1);
+    wv.z = node(4 * q + 2);
+    wv.w = node(4 * q + 3);
+    xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
+    rv.x -= alpha * wv.x; rv.y -= alpha * wv.y; rv.z -= alpha * wv.z; rv.w -= alpha * wv.w;
+    reinterpret_cast<float4*>(x)[q] = xv;
+    reinterpret_cast<float4*>(r)[q] = rv;
+    float c;
+    c = weight_of(cv.x) * rv.x; a_rr.add(c, rv.x); a_rz.add(c, mv.x * rv.x);
+    c = weight_of(cv.y) * rv.y; a_rr.add(c, rv.y); a_rz.add(c, mv.y * rv.y);
+    c = weight_of(cv.z) * rv.z; a_rr.add(c, rv.z); a_rz.add(c, mv.z * rv.z);
+    c = weight_of(cv.w) * rv.w; a_rr.add(c, rv.w); a_rz.add(c, mv.w * rv.w);
+  };
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += stride) step(q);
+  for (int64_t l = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L; l += stride) {
+    const float xv = x[l] + alpha * p[l];
+    const float rv = r[l] - alpha * node(l);
+    x[l] = xv;
+    r[l] = rv;
+    const float c = weight_of(cw[l]) * rv;
+    a_rr.add(c, rv);
+    a_rz.add(c, minv[l] * rv);
+  }
+  const double v0 = block_sum<DM>(a_rr.value(), sh);
+  const double v1 = block_sum<DM>(a_rz.value(), sh);
+  const double vals[2] = {v0, v1};
+  if (publish_and_elect(vals, 2, partials, &s->counter[1])) {
+    const double rtr = reduce_partials<DM>(partials, 0, sh);
+    const double rtz = reduce_partials<DM>(partials, 1, sh);
+    if (threadIdx.x == 0) {
+      finish_iteration(s, rtr, rtz, hist);
+      s->counter[1] = 0u;
+    }
+  }
+}
+
+template <int n, int DM, int ACC>
+__global__ void __launch_bounds__(kVecThreads)
+    cg_update32_gs_row4_kernel(float* __restrict__ x, float* __restrict__ r,
+                               const float* __restrict__ p, const float* __restrict__ w,
+                               const uint8_t* __restrict__ cw, const float* __restrict__ minv,
+                               const uint8_t* __restrict__ faces, int64_t kx, int64_t kxky,
+                               int64_t L, PcgScalars* __restrict__ s,
+                               double* __restrict__ partials, double* __restrict__ hist) {
+  __shared__ double sh[kVecThreads / 32];
+  if (s->done) return;
+  const float alpha = (float)s->alpha;
+  DotAcc<float, DM> a_rr, a_rz;
+  const int64_t n4 = L >> 2;   // L = E n^3 is a multiple of 4 here
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  auto step = [&](int64_t q) {
+    float4 xv = reinterpret_cast<float4*>(x)[q];
+    float4 rv = reinterpret_cast<float4*>(r)[q];
+    const float4 pv = __ldg(reinterpret_cast<const float4*>(p) + q);
+    const float4 wv = gs_gather_row4<n, ACC>(w, q, faces, kx, kxky);
+    const float4 mv = __ldg(reinterpret_cast<const float4*>(minv) + q);
+    const uchar4 cv = __ldg(reinterpret_cast<const uchar4*>(cw) + q);
+    xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
+    rv.x -= alpha * wv.x; rv.y -= alpha * wv.y; rv.z -= alpha * wv.z; rv.w -= alpha * wv.w;
+    reinterpret_cast<float4*>(x)[q] = xv;
+    reinterpret_cast<float4*>(r)[q] = rv;
+    float c;
+    c = weight_of(cv.x) * rv.x; a_rr.add(c, rv.x); a_rz.add(c, mv.x * rv.x);
+    c = weight_of(cv.y) * rv.y; a_rr.add(c, rv.y); a_rz.add(c, mv.y * rv.y);
+    c = weight_of(cv.z) * rv.z; a_rr.add(c, rv.z); a_rz.add(c, mv.z * rv.z);
+    c = weight_of(cv.w) * rv.w; a_rr.add(c, rv.w); a_rz.add(c, mv.w * rv.w);
+  };
+  // one group per trip: the gathers already keep several loads in flight
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += stride) step(q);
   const double v0 = block_sum<DM>(a_rr.value(), sh);
   const double v1 = block_sum<DM>(a_rz.value(), sh);
   const double vals[2] = {v0, v1};
@@ -328,6 +458,78 @@ int launch_cg_update64(Handle& h, double* x, double* r, const double* p, const d
 int launch_cg_update32(Handle& h, int dm, float* x, float* r, const float* p, const float* w,
                        const float* minv, PcgScalars* s, double* hist) {
   return update_t<float>(h, dm, x, r, p, w, h.c32, minv, s, hist);
+}
+
+bool gs_fusable(const Handle& h) { return !h.gid_user && h.fuse_gs && h.n >= 2; }
+
+// Grid of a fused update kernel: the v4 update's grid (one thread per DOF,
+// capped) with the cap set by the kernel's own occupancy.  Where the cap
+// does not bind -- small problems -- the two kernels traverse the vectors
+// identically, so their dot products agree bit for bit.
+template <typename K>
+static int fused_grid(Handle& h, K kernel, int slot) {
+  if (h.upd_gs_occ[slot] == 0) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kVecThreads, 0) != cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    h.upd_gs_occ[slot] = occ;
+  }
+  int64_t g = (h.L + kVecThreads - 1) / kVecThreads;
+  int64_t cap = (int64_t)h.num_sms * h.upd_gs_occ[slot];
+  if (cap > h.max_blocks) cap = h.max_blocks;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <int DM, int ACC>
+static void update_gs_dispatch(Handle& h, float* x, float* r, const float* p, const float* w,
+                               const float* minv, PcgScalars* s, double* hist, int slot) {
+  const int64_t kx = h.kx, kxky = (int64_t)h.kx * h.ky;
+#define SEM_UPD_ROW4(NN)                                                                  \
+  case NN: {                                                                              \
+    auto kern = cg_update32_gs_row4_kernel<NN, DM, ACC>;                                  \
+    const int grid = fused_grid(h, kern, slot);                                           \
+    kern<<<grid, kVecThreads, 0, h.stream>>>(x, r, p, w, h.cw8, minv, h.bfaces, kx, kxky, \
+                                             h.L, s, h.partials, hist);                   \
+    return;                                                                               \
+  }
+  switch (h.n) {
+    SEM_UPD_ROW4(4)
+    SEM_UPD_ROW4(8)
+    SEM_UPD_ROW4(12)
+    SEM_UPD_ROW4(16)
+    default: break;
+  }
+#undef SEM_UPD_ROW4
+  BoxNbr b{h.n, h.n * h.n * h.n, kx, kxky};
+  auto kern = cg_update32_gs_kernel<DM, ACC>;
+  const int grid = fused_grid(h, kern, slot);
+  kern<<<grid, kVecThreads, 0, h.stream>>>(x, r, p, w, h.cw8, minv, h.bfaces, b, h.L, s,
+                                           h.partials, hist);
+}
+
+// x += alpha p, r -= alpha QQ^T w with the summation folded in (box meshes,
+// FP32 data; `acc` as for the separate gather-scatter).
+int launch_cg_update32_gs(Handle& h, int dm, int acc, float* x, float* r, const float* p,
+                          const float* w, const float* minv, PcgScalars* s, double* hist) {
+  if (((uintptr_t)x | (uintptr_t)r | (uintptr_t)p | (uintptr_t)w | (uintptr_t)minv) % 16 != 0) {
+    set_error("update: vectors must be 16-byte aligned");
+    return SEM_EINVAL;
+  }
+  if (dm == kDotFP32)
+    update_gs_dispatch<kDotFP32, kGsFP32>(h, x, r, p, w, minv, s, hist, 0);
+  else if (acc == kGsFP64)
+    update_gs_dispatch<kDotDot2, kGsFP64>(h, x, r, p, w, minv, s, hist, 1);
+  else if (acc == kGsFP32)
+    update_gs_dispatch<kDotDot2, kGsFP32>(h, x, r, p, w, minv, s, hist, 2);
+  else
+    update_gs_dispatch<kDotDot2, kGsTwoSum>(h, x, r, p, w, minv, s, hist, 3);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
 }
 
 int launch_cg_init64(Handle& h, double* r, const double* b, const double* ax, const double* minv,

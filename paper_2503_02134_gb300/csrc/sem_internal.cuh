@@ -83,6 +83,8 @@ struct Handle {
   float ax_tune_ms[2][4] = {};  // autotuner timings [plain, PCG][variant]
   bool l2_persist = true;      // mixed solve: keep w resident in L2 (access-policy window)
   int gs_acc = 2;              // mixed-path accumulation: 2 TwoSum (default), 0 FP64, 1 FP32
+  bool fuse_gs = true;         // FP32 PCG on box meshes: summation folded into the update
+  int upd_gs_occ[4] = {};      // resident blocks per SM of the fused update kernels (0: not yet read)
 
   // Jacobi
   double* minv64 = nullptr;

@@ -129,11 +129,20 @@ int enqueue_iterations(Handle& h, GraphKind kind, int iters) {
       pro.minv = h.minv32;
       if ((rc = ax_dispatch_fp32(h, h.p32, h.w32, &pro, dm))) return rc;
       if (kt && (rc = kt_mark(h, it, 1))) return rc;
-      if ((rc = launch_gs(h, gp, h.w32))) return rc;
-      if (kt && (rc = kt_mark(h, it, 2))) return rc;
-      if ((rc = launch_cg_update32(h, dm, h.x32, h.r32, h.p32, h.w32, h.minv32, h.scal,
-                                   h.hist_dev)))
-        return rc;
+      if (gs_fusable(h)) {
+        // box mesh: QQ^T folded into the update (no separate pass)
+        if (kt && (rc = kt_mark(h, it, 2))) return rc;
+        const int acc = kind == kGFP32 ? 1 : h.gs_acc;
+        if ((rc = launch_cg_update32_gs(h, dm, acc, h.x32, h.r32, h.p32, h.w32, h.minv32,
+                                        h.scal, h.hist_dev)))
+          return rc;
+      } else {
+        if ((rc = launch_gs(h, gp, h.w32))) return rc;
+        if (kt && (rc = kt_mark(h, it, 2))) return rc;
+        if ((rc = launch_cg_update32(h, dm, h.x32, h.r32, h.p32, h.w32, h.minv32, h.scal,
+                                     h.hist_dev)))
+          return rc;
+      }
     }
     if (kt && (rc = kt_mark(h, it, 3))) return rc;
   }

@@ -325,6 +325,53 @@ def test_graph_and_plain_launch_agree(sem):
     S.close()
 
 
+@pytest.mark.parametrize("dims,N", [((3, 2, 2), 1), ((2, 3, 1), 2), ((3, 3, 2), 3),
+                                    ((1, 2, 3), 5), ((4, 3, 3), 7), ((2, 2, 1), 11)])
+def test_fused_gather_scatter_is_bitwise(sem, dims, N):
+    """The update with the direct-stiffness summation folded in (box meshes)
+    gives the separate pass's bits: same iterations, identical solution, for
+    every accumulation mode and the all-FP32 variant (small meshes, where the
+    two update kernels run the same grid)."""
+    S = sem.Solver(*dims, N, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 5, b)
+    assert sem.sem_get_option(S.h, "fuse_gs") == 1
+    cases = [(sem.SEM_MIXED_FP32, acc, {}) for acc in (2, 0, 1)]
+    cases.append((sem.SEM_FP32_ALL, 2, {"fixed_iters": 40}))
+    for prec, acc, kw in cases:
+        sem.sem_set_option(S.h, "gs_acc", acc)
+        out = []
+        for fuse in (1, 0):
+            sem.sem_set_option(S.h, "fuse_gs", fuse)
+            if kw:
+                x, info = S.solve(b, precision=prec, **kw)
+            else:
+                x, info = S.solve(b, tol=1e-9, maxit=3000, precision=prec)
+            out.append((x, info))
+        (x1, i1), (x0, i0) = out
+        assert i1["iters"] == i0["iters"], (prec, acc)
+        assert torch.equal(x1, x0), (prec, acc)
+        sem.sem_set_option(S.h, "fuse_gs", 1)
+    S.close()
+
+
+def test_fused_gather_scatter_large_mesh(sem):
+    """Where the fused update runs its own (occupancy-sized) grid, the dot
+    products are summed in another order: the solves agree to rounding."""
+    P = so.Problem(12, 10, 9, 7, deform=True)
+    S = sem.Solver(12, 10, 9, 7, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 6, b)
+    x1, i1 = S.solve(b, tol=1e-9, maxit=5000, precision=sem.SEM_MIXED_FP32)
+    sem.sem_set_option(S.h, "fuse_gs", 0)
+    x0, i0 = S.solve(b, tol=1e-9, maxit=5000, precision=sem.SEM_MIXED_FP32)
+    assert i1["rc"] == 0 and i1["relres_true"] <= 1e-9
+    assert abs(i1["iters"] - i0["iters"]) <= max(3, i0["iters"] // 50)
+    assert rel_maxerr(x1.cpu(), x0.cpu()) < 1e-7
+    assert P.true_relres(b.cpu().numpy(), x1.cpu().numpy()) <= 1.0000001e-9
+    S.close()
+
+
 def test_kernel_timing_mode(sem):
     """Per-kernel event timing changes nothing in the result (same kernels,
     events between them), counts every iteration and reports positive
