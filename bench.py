@@ -331,6 +331,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the order sweep N = 5..15")
     ap.add_argument("--profile", action="store_true",
                     help="small run for ncu captures: 3 fixed mixed iterations + 2 FP32 operator calls")
+    ap.add_argument("--profile-k", type=int, default=0,
+                    help="with --profile: a k^3-element mesh instead of the benchmark's (smaller ncu captures)")
     ap.add_argument("--profile-batched", action="store_true",
                     help="ncu run of the 64-problem batch: one solve inside an NVTX range")
     ap.add_argument("--profile-batched-small", action="store_true",
@@ -377,7 +379,9 @@ def main():
         return 0
 
     stream = torch.cuda.Stream()
-    W = WORKLOAD
+    W = dict(WORKLOAD)
+    if args.profile and args.profile_k > 0:
+        W.update(kx=args.profile_k, ky=args.profile_k, kz=args.profile_k)
     S = sem.Solver(W["kx"], W["ky"], W["kz"], W["N"], deform=W["deform"], stream=stream.cuda_stream)
     L = S.L
     with torch.cuda.stream(stream):

@@ -233,7 +233,9 @@ void sem_x0_destroy(sem_x0_model m);
  * sem_batch_setup builds one sub-handle per problem (meshes[i], Ns[i]; odd
  * N in 1..9), all on one stream, and the work lists of the batched kernels:
  * each phase of a PCG iteration (operator, gather-scatter, update + dots) is
- * ONE persistent launch over every problem's work items, and chunks of
+ * ONE persistent launch over every problem's work items (for box-mesh
+ * problems the gather-scatter is folded into the update, as with the
+ * handle option "fuse_gs"), and chunks of
  * iterations are replayed as a CUDA graph.  A project autotuner picks the
  * operator's pipeline depth and grid at set-up.  The solve is the mixed
  * path with reliable updates (as sem_pcg_solve_ex, refine_mode 0), per
@@ -247,7 +249,8 @@ int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count, void* stre
 int sem_batch_problem(sem_batch b, int i, sem_handle* out);
 int sem_batch_pcg_solve(sem_batch b, const double* const* f, double* const* x,
                         const sem_solve_opts* opts, sem_info* infos);
-/* keys: "work_items", "launches", and per GLL points per direction n (2..10,
+/* keys: "work_items", "launches", "fused_problems" (problems whose
+ * gather-scatter is folded into the update), and per GLL points per direction n (2..10,
  * even): "variant_n<n>", "grid_n<n>" (autotuned launch), "tune_ms_n<n>_v<0..2>" */
 int sem_batch_get_option(sem_batch b, const char* key, double* value);
 void sem_batch_destroy(sem_batch b);

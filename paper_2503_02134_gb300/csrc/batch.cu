@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "ax_tma.cuh"
+#include "gs_sum.cuh"
 #include "pcg.cuh"
 
 namespace sem {
@@ -38,7 +39,9 @@ struct BatchProb {
   double* ax_part;   // one partial per element group
   double* up_part;   // two partials per update item
   int64_t E, L;
+  int64_t kx, kxky;   // box strides of the element index (fused summation)
   int n, epb, ngroups, nupd;
+  int fuse;           // 1: QQ^T folded into the update (box mesh), 0: separate pass
 };
 
 constexpr int kUpdItem4 = 1024;           // float4 per update work item (4096 values)
@@ -344,7 +347,26 @@ __global__ void __launch_bounds__(256)
 
 __device__ __forceinline__ float batch_weight(uint8_t m) { return m ? __frcp_rn((float)m) : 0.f; }
 
-// add2s2 x 2 + glsc3(r,c,r) + glsc3(r,c,z) for one range of every problem.
+// QQ^T w at float4 group q of a box-mesh problem, gathered from the copies'
+// positions (the separate pass's order and TwoSum accumulation).
+__device__ __forceinline__ float4 batch_gather(const BatchProb& P, int64_t q) {
+  if (P.n == 8) return gs_gather_row4<8, kGsTwoSum>(P.w, q, P.faces, P.kx, P.kxky);
+  if (P.n == 4) return gs_gather_row4<4, kGsTwoSum>(P.w, q, P.faces, P.kx, P.kxky);
+  const BoxNbr nb{P.n, P.n * P.n * P.n, P.kx, P.kxky};
+  float v[4];
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    const int64_t l = 4 * q + c;
+    const int64_t e = l / nb.n3;
+    const int rem = (int)(l - e * nb.n3);
+    v[c] = gs_gather_node<kGsTwoSum>(P.w, l, rem % P.n, (rem / P.n) % P.n, rem / (P.n * P.n),
+                                     __ldg(P.faces + e), nb);
+  }
+  return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// add2s2 x 2 + glsc3(r,c,r) + glsc3(r,c,z) for one range of every problem
+// (for box-mesh problems with the summation QQ^T folded in).
 __global__ void __launch_bounds__(256)
     batch_update_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ uitems,
                         const int* __restrict__ nuitems_dev) {
@@ -363,7 +385,7 @@ __global__ void __launch_bounds__(256)
       float4 xv = reinterpret_cast<float4*>(P.x)[q];
       float4 rv = reinterpret_cast<float4*>(P.r)[q];
       const float4 pv = reinterpret_cast<const float4*>(P.p)[q];
-      const float4 wv = reinterpret_cast<const float4*>(P.w)[q];
+      const float4 wv = P.fuse ? batch_gather(P, q) : reinterpret_cast<const float4*>(P.w)[q];
       const float4 mv = __ldg(reinterpret_cast<const float4*>(P.minv) + q);
       const uchar4 cv = __ldg(reinterpret_cast<const uchar4*>(P.cw) + q);
       xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
@@ -454,6 +476,7 @@ struct sem_batch_s {
   int* d_chunk_prob = nullptr;
   int2* d_chunk_desc = nullptr;
   int64_t nchunks = 0;
+  int fused = 0;             // problems whose summation is folded into the update
   int2* d_uitems = nullptr;
   int nuitems = 0;
   double* d_part = nullptr;
@@ -775,12 +798,16 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
     P.epb = 1;
     P.ngroups = (int)h.E;   // the most groups any variant makes
     P.nupd = (int)(((h.L >> 2) + kUpdItem4 - 1) / kUpdItem4);
+    P.kx = h.kx;
+    P.kxky = (int64_t)h.kx * h.ky;
+    P.fuse = gs_fusable(h) ? 1 : 0;
     b->present[order_slot(h.n)] = true;
     ax_off[p] = part_total;
     part_total += h.E;
     up_off[p] = part_total;
     part_total += 2 * (int64_t)P.nupd;
-    b->nchunks += h.n_chunks;
+    if (!P.fuse) b->nchunks += h.n_chunks;
+    b->fused += P.fuse;
   }
   // per-problem work lists (kept on the host; the active ones are uploaded
   // interleaved, so every launch spreads over all unfinished problems)
@@ -791,11 +818,13 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
     Handle& h = *b->subs[p];
     for (int g = 0; g < probs[p].ngroups; ++g) b->items_of[p].push_back(make_int2(p, g));
     for (int q = 0; q < probs[p].nupd; ++q) b->uitems_of[p].push_back(make_int2(p, q));
-    b->chunks_of[p].resize((size_t)h.n_chunks);
-    if (h.n_chunks > 0 &&
-        (ce = cudaMemcpy(b->chunks_of[p].data(), h.gs_chunks, sizeof(int2) * h.n_chunks,
-                         cudaMemcpyDeviceToHost)) != cudaSuccess)
-      return fail(cuda_fail(ce, "cudaMemcpy"));
+    if (!probs[p].fuse) {   // fused problems have no separate summation pass
+      b->chunks_of[p].resize((size_t)h.n_chunks);
+      if (h.n_chunks > 0 &&
+          (ce = cudaMemcpy(b->chunks_of[p].data(), h.gs_chunks, sizeof(int2) * h.n_chunks,
+                           cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(cuda_fail(ce, "cudaMemcpy"));
+    }
     b->nitems += probs[p].ngroups;
     b->nuitems += probs[p].nupd;
   }
@@ -860,6 +889,7 @@ extern "C" int sem_batch_get_option(sem_batch b, const char* key, double* value)
   };
   int q = 0;
   if (k == "work_items") *value = b->nitems;
+  else if (k == "fused_problems") *value = b->fused;
   else if (k == "launches") *value = (double)b->launches;
   else if (order_of("variant_n", &q)) *value = b->present[q] ? b->variant[q] : -1;
   else if (order_of("grid_n", &q)) *value = b->present[q] ? b->grid[q] : 0;
