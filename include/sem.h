@@ -285,6 +285,11 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *   "l2_persist"  1 (default): during a mixed solve keep the operator output resident
  *                 in L2 (access-policy window on the handle's stream and a
  *                 persisting carve-out of the context, released at the end)
+ *   "l2_hints"    1: in FP32 PCG iterations the streamed vectors and G pass
+ *                 through L2 with evict-first priority and the operator
+ *                 output w is written evict-last (per-access cache hints),
+ *                 instead of the access-policy window of "l2_persist";
+ *                 0 (default) off
  *   "fuse_gs"     1 (default): in FP32 and mixed PCG iterations on a box mesh
  *                 (sem_setup without gid) the direct-stiffness summation is
  *                 folded into the vector update -- each copy of a shared node
@@ -298,6 +303,8 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *                 it, either way, clears the sums.
  * sem_get_option also reads "ax_tune_ms_plain_<v>", "ax_tune_ms_pcg_<v>"
  * (autotuner timings, ms), "launches" (kernels enqueued so far),
+ * "l2_window_bytes", "l2_max_persist", "l2_max_window" (the L2 window of
+ * the last mixed solve and the device limits it was cut to),
  * "kt_iters" (iterations timed) and "kt_ms_ax", "kt_ms_gs",
  * "kt_ms_update" (average device time per launch, ms).
  * Unknown keys and out-of-range values return SEM_EINVAL. */

@@ -466,6 +466,8 @@ int sem_set_option(sem_handle h, const char* key, int64_t value) {
     h->gs_acc = (int)value;
   } else if (k == "l2_persist" && (value == 0 || value == 1)) {
     h->l2_persist = value != 0;
+  } else if (k == "l2_hints" && (value == 0 || value == 1)) {
+    h->l2_hints = value != 0;
   } else if (k == "fuse_gs" && (value == 0 || value == 1)) {
     h->fuse_gs = value != 0;
   } else if (k == "kernel_timing" && (value == 0 || value == 1)) {
@@ -493,6 +495,10 @@ int sem_get_option(sem_handle h, const char* key, double* value) {
   else if (k == "gs_acc") *value = h->gs_acc;
   else if (k == "l2_persist") *value = h->l2_persist ? 1 : 0;
   else if (k == "fuse_gs") *value = h->fuse_gs ? 1 : 0;
+  else if (k == "l2_hints") *value = h->l2_hints ? 1 : 0;
+  else if (k == "l2_window_bytes") *value = (double)h->l2_window_bytes;
+  else if (k == "l2_max_persist") *value = (double)h->l2_max_persist;
+  else if (k == "l2_max_window") *value = (double)h->l2_max_window;
   else if (k == "launches") *value = (double)h->launches;
   else if (k == "kernel_timing") *value = h->kernel_timing ? 1 : 0;
   else if (k == "kt_iters") *value = (double)h->kt_iters;

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
                   const float* __restrict__ G, const float* __restrict__ Dg,
                   const uint8_t* __restrict__ faces, int64_t E, const float* __restrict__ rr,
                   const float* __restrict__ minv, float* pp, PcgScalars* __restrict__ scal,
-                  double* __restrict__ partials, int* __restrict__ err) {
+                  double* __restrict__ partials, int* __restrict__ err, int l2h) {
   using S = TmaShape<n, V>;
   constexpr int n2 = S::n2, n3 = S::n3, EPB = S::EPB, NS = S::NS;
   constexpr int NV = PCG ? 3 : 1;
@@ -98,6 +98,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   const bool lane_ok = le < EPB;
   const int ir = lane_ok ? i : 0, jr = lane_ok ? j : 0, ler = lane_ok ? le : 0;
   const int64_t ngroups = (E + EPB - 1) / EPB;
+  // with l2h: everything streams through L2 evict-first except the output
+  // w, which the next kernel reads (and gathers) again
+  const uint64_t pol_first = l2h ? l2_policy_evict_first() : 0ull;
+  const uint64_t pol_last = l2h ? l2_policy_evict_last() : 0ull;
 
   auto issue = [&](int st, int64_t g) {
     const int64_t e0 = g * EPB;
@@ -105,6 +109,17 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     const uint32_t vb = (uint32_t)(cnt * n3 * 4);
     float* dst = stage0 + st * STAGE;
     mbar_arrive_expect_tx(&bar[st], (NV + 6) * vb);
+    if (l2h) {
+      if (PCG) {
+        bulk_load_hint(dst, rr + e0 * n3, vb, &bar[st], pol_first);
+        bulk_load_hint(dst + SV, minv + e0 * n3, vb, &bar[st], pol_first);
+        bulk_load_hint(dst + 2 * SV, pp + e0 * n3, vb, &bar[st], pol_first);
+      } else {
+        bulk_load_hint(dst, uin + e0 * n3, vb, &bar[st], pol_first);
+      }
+      bulk_load_hint(dst + NV * SV, G + e0 * 6 * n3, 6 * vb, &bar[st], pol_first);
+      return;
+    }
     if (PCG) {
       bulk_load(dst, rr + e0 * n3, vb, &bar[st]);
       bulk_load(dst + SV, minv + e0 * n3, vb, &bar[st]);
@@ -166,7 +181,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       if (PCG) {
         v = sb[SV + ler * n3 + si] * sb[ler * n3 + si] + beta * su_e[si];
         if (lane_ok) su_e[si] = v;
-        if (act) pp[e * n3 + si] = v;
+        if (act) {
+          if (l2h) st_hint(pp + e * n3 + si, v, pol_first);
+          else pp[e * n3 + si] = v;
+        }
       } else {
         v = su_e[si];
       }
@@ -207,7 +225,8 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       for (int l = 0; l < n; ++l) wv += DjT[l] * ss_e[k * n2 + l * n + ir];
       if (on_dirichlet(f, i, j, k, n - 1)) wv = 0.f;
       if (act) {
-        wout[e * n3 + k * n2 + ij] = wv;
+        if (l2h) st_hint(wout + e * n3 + k * n2 + ij, wv, pol_last);
+        else wout[e * n3 + k * n2 + ij] = wv;
         if (PCG) acc.add(ureg[k], wv);
       }
     }
@@ -276,8 +295,9 @@ int ax_tma_launch(Handle& h, const float* u, float* w, const AxPrologue* pro) {
   PcgScalars* scal = PCG ? const_cast<PcgScalars*>(pro->scal) : nullptr;
   double* partials = PCG ? pro->pap_partials : nullptr;
   float* pp = PCG ? const_cast<float*>(u) : nullptr;
+  const int l2h = PCG && h.l2_hints ? 1 : 0;
   kern<<<grid, S::NT, smem, h.stream>>>(u, w, h.G32, h.D32, h.bfaces, h.E, r, minv, pp, scal,
-                                        partials, h.dev_err);
+                                        partials, h.dev_err, l2h);
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
   return 0;

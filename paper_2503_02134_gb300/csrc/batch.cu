@@ -347,26 +347,17 @@ __global__ void __launch_bounds__(256)
 
 __device__ __forceinline__ float batch_weight(uint8_t m) { return m ? __frcp_rn((float)m) : 0.f; }
 
-// QQ^T w at float4 group q of a box-mesh problem, gathered from the copies'
-// positions (the separate pass's order and TwoSum accumulation).
+// QQ^T w at float4 group q of a box-mesh problem with n = 4 or 8, gathered
+// from the copies' positions (the separate pass's order and TwoSum
+// accumulation).
 __device__ __forceinline__ float4 batch_gather(const BatchProb& P, int64_t q) {
   if (P.n == 8) return gs_gather_row4<8, kGsTwoSum>(P.w, q, P.faces, P.kx, P.kxky);
-  if (P.n == 4) return gs_gather_row4<4, kGsTwoSum>(P.w, q, P.faces, P.kx, P.kxky);
-  const BoxNbr nb{P.n, P.n * P.n * P.n, P.kx, P.kxky};
-  float v[4];
-#pragma unroll 1
-  for (int c = 0; c < 4; ++c) {
-    const int64_t l = 4 * q + c;
-    const int64_t e = l / nb.n3;
-    const int rem = (int)(l - e * nb.n3);
-    v[c] = gs_gather_node<kGsTwoSum>(P.w, l, rem % P.n, (rem / P.n) % P.n, rem / (P.n * P.n),
-                                     __ldg(P.faces + e), nb);
-  }
-  return make_float4(v[0], v[1], v[2], v[3]);
+  return gs_gather_row4<4, kGsTwoSum>(P.w, q, P.faces, P.kx, P.kxky);
 }
 
 // add2s2 x 2 + glsc3(r,c,r) + glsc3(r,c,z) for one range of every problem
 // (for box-mesh problems with the summation QQ^T folded in).
+template <bool FUSED>
 __global__ void __launch_bounds__(256)
     batch_update_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ uitems,
                         const int* __restrict__ nuitems_dev) {
@@ -375,7 +366,9 @@ __global__ void __launch_bounds__(256)
   for (int ui = blockIdx.x; ui < nuitems; ui += gridDim.x) {
     const int2 itm = uitems[ui];
     const BatchProb& P = probs[itm.x];
-    if (P.scal->done) continue;   // uniform for the block
+    // uniform for the block: finished problems, and problems the other
+    // instantiation handles (the fused gather needs twice the registers)
+    if (P.scal->done || (P.fuse != 0) != FUSED) continue;
     const float alpha = (float)P.scal->alpha;
     const int64_t n4 = P.L >> 2;
     const int64_t q0 = (int64_t)itm.y * kUpdItem4;
@@ -385,7 +378,7 @@ __global__ void __launch_bounds__(256)
       float4 xv = reinterpret_cast<float4*>(P.x)[q];
       float4 rv = reinterpret_cast<float4*>(P.r)[q];
       const float4 pv = reinterpret_cast<const float4*>(P.p)[q];
-      const float4 wv = P.fuse ? batch_gather(P, q) : reinterpret_cast<const float4*>(P.w)[q];
+      const float4 wv = FUSED ? batch_gather(P, q) : reinterpret_cast<const float4*>(P.w)[q];
       const float4 mv = __ldg(reinterpret_cast<const float4*>(P.minv) + q);
       const uchar4 cv = __ldg(reinterpret_cast<const uchar4*>(P.cw) + q);
       xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
@@ -531,10 +524,18 @@ static int batch_enqueue_iteration(sem_batch_s& b) {
     SEM_CUDA(cudaGetLastError());
   }
   const int up_blocks = std::min(b.nuitems, num_sms * 8);
-  batch_update_kernel<<<std::max(up_blocks, 1), 256, 0, b.stream>>>(b.d_probs, b.d_uitems,
-                                                                     b.d_counts + 2 * kBatchOrders + 1);
-  ++b.launches;
-  SEM_CUDA(cudaGetLastError());
+  if (b.fused < b.count) {
+    batch_update_kernel<false><<<std::max(up_blocks, 1), 256, 0, b.stream>>>(
+        b.d_probs, b.d_uitems, b.d_counts + 2 * kBatchOrders + 1);
+    ++b.launches;
+    SEM_CUDA(cudaGetLastError());
+  }
+  if (b.fused > 0) {
+    batch_update_kernel<true><<<std::max(up_blocks, 1), 256, 0, b.stream>>>(
+        b.d_probs, b.d_uitems, b.d_counts + 2 * kBatchOrders + 1);
+    ++b.launches;
+    SEM_CUDA(cudaGetLastError());
+  }
   batch_finalize_update<<<b.count, 256, 0, b.stream>>>(b.d_probs, b.count);
   ++b.launches;
   SEM_CUDA(cudaGetLastError());
@@ -800,7 +801,9 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
     P.nupd = (int)(((h.L >> 2) + kUpdItem4 - 1) / kUpdItem4);
     P.kx = h.kx;
     P.kxky = (int64_t)h.kx * h.ky;
-    P.fuse = gs_fusable(h) ? 1 : 0;
+    // folded summation for n a multiple of 4 (whole float4 rows); the
+    // per-node gather of other orders measured slower than the separate pass
+    P.fuse = gs_fusable(h) && (h.n == 4 || h.n == 8) ? 1 : 0;
     b->present[order_slot(h.n)] = true;
     ax_off[p] = part_total;
     part_total += h.E;

@@ -91,10 +91,52 @@ __device__ __forceinline__ float gs_gather_node(const float* __restrict__ w, int
   return acc.result();
 }
 
+// Sum of two copies a, b in that order with the accumulator's arithmetic:
+// the value GsSum<float, ACC> gives after add(a), add(b).  (For TwoSum the
+// error term of a two-term sum is the exact rounding error of fl(a' + b),
+// a' = fl(0 + a), so the final rounding returns fl(a' + b) itself.)
+template <int ACC>
+__device__ __forceinline__ float gs_sum2(float a, float b) {
+  if constexpr (ACC == kGsFP64) return (float)((0.0 + (double)a) + (double)b);
+  return __fadd_rn(__fadd_rn(0.f, a), b);
+}
+
+// Copies of a float4 group lying on NC = 2 (one j or k face) or 4 (a j-k
+// edge) rows: rows at float4 offsets ro[0] < ... < ro[NC-1] (one of them 0,
+// the group itself), plus, where the group's first (last) value lies on an
+// i face, the single values across it in each of those rows.
+template <int NC, int n, int ACC>
+__device__ __forceinline__ float4 gs_gather_rows(const float* __restrict__ w, int64_t q,
+                                                 const int64_t* ro, float4 own, bool xm,
+                                                 bool xp) {
+  constexpr int n3 = n * n * n;
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  float4 R[NC];
+  float XM[NC], XP[NC];
+#pragma unroll
+  for (int t = 0; t < NC; ++t) {
+    R[t] = ro[t] == 0 ? own : __ldg(w4 + q + ro[t]);
+    const int64_t l0 = 4 * (q + ro[t]);
+    XM[t] = xm ? __ldg(w + l0 - n3 + (n - 1)) : 0.f;
+    XP[t] = xp ? __ldg(w + l0 + 3 + n3 - (n - 1)) : 0.f;
+  }
+  GsSum<float, ACC> s0, s1, s2, s3;
+#pragma unroll
+  for (int t = 0; t < NC; ++t) {
+    if (xm) s0.add(XM[t]);
+    s0.add(R[t].x);
+    s1.add(R[t].y);
+    s2.add(R[t].z);
+    s3.add(R[t].w);
+    if (xp) s3.add(XP[t]);
+  }
+  return make_float4(s0.result(), s1.result(), s2.result(), s3.result());
+}
+
 // n a multiple of 4: a float4 group lies inside one row of one element, so
 // the copies across j and k faces are whole float4 rows of the neighbouring
 // elements; only the copies across i faces (components 0 and 3) are single
-// values.
+// values.  Interior rows (no j or k face) take a short path.
 template <int n, int ACC>
 __device__ __forceinline__ float4 gs_gather_row4(const float* __restrict__ w, int64_t q,
                                                  const uint8_t* __restrict__ faces,
@@ -112,54 +154,24 @@ __device__ __forceinline__ float4 gs_gather_row4(const float* __restrict__ w, in
   const bool xm = i0 == 0 && !(f & 1);
   const bool xp = i0 + 3 == n - 1 && !(f & 2);
   const float4 own = __ldg(w4 + q);
-  if (!(dy | dz) && !xm && !xp) return own;
+  if (!(dy | dz)) {
+    float4 out = own;
+    if (xm) out.x = gs_sum2<ACC>(__ldg(w + 4 * q - n3 + (n - 1)), own.x);
+    if (xp) out.w = gs_sum2<ACC>(own.w, __ldg(w + 4 * q + 3 + n3 - (n - 1)));
+    return out;
+  }
   // row offsets (float4 units) of the copies across j / k faces
   const int64_t oy = (int64_t)dy * (kx * g4 - (int64_t)(n - 1) * row4);
   const int64_t oz = (int64_t)dz * (kxky * g4 - (int64_t)(n - 1) * n * row4);
-  const int64_t ys[2] = {dy < 0 ? oy : 0, dy > 0 ? oy : 0};
-  const int64_t zs[2] = {dz < 0 ? oz : 0, dz > 0 ? oz : 0};
-  const int ny = dy ? 2 : 1, nz = dz ? 2 : 1;
-  float4 R[4];
-  float XM[4], XP[4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int t = 2 * a + c;
-      if (a < nz && c < ny) {
-        const int64_t ro = zs[a] + ys[c];
-        R[t] = ro == 0 ? own : __ldg(w4 + q + ro);
-        const int64_t l0 = 4 * (q + ro);
-        XM[t] = xm ? __ldg(w + l0 - n3 + (n - 1)) : 0.f;
-        XP[t] = xp ? __ldg(w + l0 + 3 + n3 - (n - 1)) : 0.f;
-      }
-    }
-  GsSum<float, ACC> s0, s1, s2, s3;
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int t = 2 * a + c;
-      if (a < nz && c < ny) {
-        if (xm) s0.add(XM[t]);
-        s0.add(R[t].x);
-        s1.add(R[t].y);
-        s2.add(R[t].z);
-        s3.add(R[t].w);
-        if (xp) s3.add(XP[t]);
-      }
-    }
-  float4 out;
-  if (dy | dz) {
-    out.y = s1.result();
-    out.z = s2.result();
-  } else {
-    out.y = own.y;
-    out.z = own.z;
+  if (dy && dz) {
+    const int64_t ylo = dy < 0 ? oy : 0, yhi = dy > 0 ? oy : 0;
+    const int64_t zlo = dz < 0 ? oz : 0, zhi = dz > 0 ? oz : 0;
+    const int64_t ro[4] = {zlo + ylo, zlo + yhi, zhi + ylo, zhi + yhi};
+    return gs_gather_rows<4, n, ACC>(w, q, ro, own, xm, xp);
   }
-  out.x = (dy | dz) || xm ? s0.result() : own.x;
-  out.w = (dy | dz) || xp ? s3.result() : own.w;
-  return out;
+  const int64_t o = dy ? oy : oz;
+  const int64_t ro[2] = {o < 0 ? o : 0, o > 0 ? o : 0};
+  return gs_gather_rows<2, n, ACC>(w, q, ro, own, xm, xp);
 }
 
 }  // namespace sem

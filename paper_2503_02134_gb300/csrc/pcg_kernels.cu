@@ -6,6 +6,7 @@
 // refinement helpers of the mixed path.
 #include "gs_sum.cuh"
 #include "pcg.cuh"
+#include "tma.cuh"
 
 namespace sem {
 
@@ -201,24 +202,43 @@ __global__ void __launch_bounds__(kVecThreads)
                                const uint8_t* __restrict__ cw, const float* __restrict__ minv,
                                const uint8_t* __restrict__ faces, int64_t kx, int64_t kxky,
                                int64_t L, PcgScalars* __restrict__ s,
-                               double* __restrict__ partials, double* __restrict__ hist) {
+                               double* __restrict__ partials, double* __restrict__ hist,
+                               int l2h) {
   __shared__ double sh[kVecThreads / 32];
   if (s->done) return;
   const float alpha = (float)s->alpha;
   DotAcc<float, DM> a_rr, a_rz;
   const int64_t n4 = L >> 2;   // L = E n^3 is a multiple of 4 here
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // with l2h the streams go through L2 evict-first, leaving w (written by
+  // the operator evict-last) resident for the gathers
+  const uint64_t pol = l2h ? l2_policy_evict_first() : 0ull;
   auto step = [&](int64_t q) {
-    float4 xv = reinterpret_cast<float4*>(x)[q];
-    float4 rv = reinterpret_cast<float4*>(r)[q];
-    const float4 pv = __ldg(reinterpret_cast<const float4*>(p) + q);
+    float4 xv, rv, pv, mv;
+    uchar4 cv;
+    if (l2h) {
+      xv = ld_hint4_rw(reinterpret_cast<const float4*>(x) + q, pol);
+      rv = ld_hint4_rw(reinterpret_cast<const float4*>(r) + q, pol);
+      pv = ld_hint4(reinterpret_cast<const float4*>(p) + q, pol);
+      mv = ld_hint4(reinterpret_cast<const float4*>(minv) + q, pol);
+      cv = ld_hint_u8x4(reinterpret_cast<const uchar4*>(cw) + q, pol);
+    } else {
+      xv = reinterpret_cast<float4*>(x)[q];
+      rv = reinterpret_cast<float4*>(r)[q];
+      pv = __ldg(reinterpret_cast<const float4*>(p) + q);
+      mv = __ldg(reinterpret_cast<const float4*>(minv) + q);
+      cv = __ldg(reinterpret_cast<const uchar4*>(cw) + q);
+    }
     const float4 wv = gs_gather_row4<n, ACC>(w, q, faces, kx, kxky);
-    const float4 mv = __ldg(reinterpret_cast<const float4*>(minv) + q);
-    const uchar4 cv = __ldg(reinterpret_cast<const uchar4*>(cw) + q);
     xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
     rv.x -= alpha * wv.x; rv.y -= alpha * wv.y; rv.z -= alpha * wv.z; rv.w -= alpha * wv.w;
-    reinterpret_cast<float4*>(x)[q] = xv;
-    reinterpret_cast<float4*>(r)[q] = rv;
+    if (l2h) {
+      st_hint4(reinterpret_cast<float4*>(x) + q, xv, pol);
+      st_hint4(reinterpret_cast<float4*>(r) + q, rv, pol);
+    } else {
+      reinterpret_cast<float4*>(x)[q] = xv;
+      reinterpret_cast<float4*>(r)[q] = rv;
+    }
     float c;
     c = weight_of(cv.x) * rv.x; a_rr.add(c, rv.x); a_rz.add(c, mv.x * rv.x);
     c = weight_of(cv.y) * rv.y; a_rr.add(c, rv.y); a_rz.add(c, mv.y * rv.y);
@@ -493,7 +513,7 @@ static void update_gs_dispatch(Handle& h, float* x, float* r, const float* p, co
     auto kern = cg_update32_gs_row4_kernel<NN, DM, ACC>;                                  \
     const int grid = fused_grid(h, kern, slot);                                           \
     kern<<<grid, kVecThreads, 0, h.stream>>>(x, r, p, w, h.cw8, minv, h.bfaces, kx, kxky, \
-                                             h.L, s, h.partials, hist);                   \
+                                             h.L, s, h.partials, hist, h.l2_hints ? 1 : 0); \
     return;                                                                               \
   }
   switch (h.n) {

@@ -82,6 +82,9 @@ struct Handle {
   int ax_variant_pcg = 0;
   float ax_tune_ms[2][4] = {};  // autotuner timings [plain, PCG][variant]
   bool l2_persist = true;      // mixed solve: keep w resident in L2 (access-policy window)
+  bool l2_hints = false;       // PCG kernels: per-access L2 eviction priorities keep w resident
+  int64_t l2_window_bytes = 0;     // window of the last mixed solve (0: none set)
+  int64_t l2_max_persist = 0, l2_max_window = 0;   // device limits read then
   int gs_acc = 2;              // mixed-path accumulation: 2 TwoSum (default), 0 FP64, 1 FP32
   bool fuse_gs = true;         // FP32 PCG on box meshes: summation folded into the update
   int upd_gs_occ[4] = {};      // resident blocks per SM of the fused update kernels (0: not yet read)

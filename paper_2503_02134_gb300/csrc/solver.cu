@@ -226,7 +226,7 @@ struct L2Window {
   Handle& h;
   bool on = false;
   L2Window(Handle& hh, const void* base, size_t bytes) : h(hh) {
-    if (!h.l2_persist || !base) return;
+    if (!h.l2_persist || h.l2_hints || !base) return;
     int max_persist = 0, max_window = 0;
     if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, h.device) != cudaSuccess ||
         cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, h.device) != cudaSuccess ||
@@ -235,6 +235,9 @@ struct L2Window {
       return;
     }
     const size_t want = std::min(bytes, (size_t)std::min(max_persist, max_window));
+    h.l2_window_bytes = (int64_t)want;
+    h.l2_max_persist = max_persist;
+    h.l2_max_window = max_window;
     if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
       cudaGetLastError();
       return;

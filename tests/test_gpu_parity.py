@@ -372,6 +372,22 @@ def test_fused_gather_scatter_large_mesh(sem):
     S.close()
 
 
+def test_l2_options_change_no_bits(sem):
+    """L2 residency controls (access-policy window, per-access eviction
+    hints) change where data lives, not the arithmetic."""
+    S = sem.Solver(4, 4, 4, 7, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 8, b)
+    ref, iref = S.solve(b, tol=1e-9, maxit=3000, precision=sem.SEM_MIXED_FP32)
+    for persist, hints in ((0, 0), (0, 1), (1, 1)):
+        sem.sem_set_option(S.h, "l2_persist", persist)
+        sem.sem_set_option(S.h, "l2_hints", hints)
+        x, info = S.solve(b, tol=1e-9, maxit=3000, precision=sem.SEM_MIXED_FP32)
+        assert info["iters"] == iref["iters"]
+        assert torch.equal(x, ref), (persist, hints)
+    S.close()
+
+
 def test_kernel_timing_mode(sem):
     """Per-kernel event timing changes nothing in the result (same kernels,
     events between them), counts every iteration and reports positive
