@@ -126,7 +126,9 @@ typedef struct {
   int max_cycles;        /* mixed only: FP64 outer cycles cap (default 20) */
   int use_graph;         /* 0 (default) or 1: replay iteration chunks as CUDA graphs; -1: plain launches */
   int chunk;             /* iterations per convergence poll (default 32) */
-  int precond;           /* 1 Jacobi (default), -1 identity */
+  int precond;           /* 1 Jacobi (default), -1 identity, 2 multigrid (sem_mg_apply's
+                            V-cycle; FP64, or mixed with FP64 restarts of FP32 inner
+                            solves whose residual reduction is inner_tol, default 1e-4) */
   double* history;       /* optional host array of maxit+1 recursive residuals (or NULL) */
   int refine_mode;       /* mixed only: 0 reliable updates (default): the FP64 true residual
                             replaces the FP32 one each time it fell by replace_factor, CG
@@ -282,20 +284,24 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *   "use_tma"     1 (default) staged FP32 operator where it applies, 0 off
  *   "gs_acc"      mixed-path gather-scatter accumulation: 2 error-free
  *                 FP32 TwoSum (default), 0 FP64, 1 plain FP32
- *   "l2_persist"  1 (default): during a mixed solve keep the operator output resident
+ *   "l2_persist"  1: during a mixed solve keep the operator output resident
  *                 in L2 (access-policy window on the handle's stream and a
- *                 persisting carve-out of the context, released at the end)
+ *                 persisting carve-out of the context, released at the end);
+ *                 0 (default: measured no faster with the summation folded
+ *                 into the update, slower with the separate pass)
  *   "l2_hints"    1: in FP32 PCG iterations the streamed vectors and G pass
  *                 through L2 with evict-first priority and the operator
  *                 output w is written evict-last (per-access cache hints),
  *                 instead of the access-policy window of "l2_persist";
  *                 0 (default) off
  *   "fuse_gs"     1 (default): in FP32 and mixed PCG iterations on a box mesh
- *                 (sem_setup without gid) the direct-stiffness summation is
- *                 folded into the vector update -- each copy of a shared node
- *                 gathers the others, found from its position, in ascending
- *                 local index with the accumulation "gs_acc" selects, which
- *                 gives the separate pass's bits; 0: separate pass
+ *                 (sem_setup without gid) with n a multiple of 4 the
+ *                 direct-stiffness summation is folded into the vector update
+ *                 -- each copy of a shared node gathers the others, found from
+ *                 its position, in ascending local index with the
+ *                 accumulation "gs_acc" selects, which gives the separate
+ *                 pass's bits; 2: folded for every n (slower than the
+ *                 separate pass where n is not a multiple of 4); 0: separate pass
  *   "kernel_timing" 1: PCG solves run without graphs and time each
  *                 iteration's operator, gather-scatter and update launches
  *                 with CUDA events on the handle's stream (the events add
@@ -303,11 +309,27 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *                 it, either way, clears the sums.
  * sem_get_option also reads "ax_tune_ms_plain_<v>", "ax_tune_ms_pcg_<v>"
  * (autotuner timings, ms), "launches" (kernels enqueued so far),
+ * "mg_levels", "mg_omega_<l>" (multigrid levels and damping, 0 before first use),
  * "l2_window_bytes", "l2_max_persist", "l2_max_window" (the L2 window of
  * the last mixed solve and the device limits it was cut to),
  * "kt_iters" (iterations timed) and "kt_ms_ax", "kt_ms_gs",
  * "kt_ms_update" (average device time per launch, ms).
  * Unknown keys and out-of-range values return SEM_EINVAL. */
+/* Multigrid preconditioner z = M^{-1} r (box meshes only).  The paper runs
+ * Nekbone with its multigrid preconditioner (Sec. 3.1, profiling table;
+ * Sec. 4, the Schwarz weights' square roots kept in FP64) without giving
+ * its algorithm; this one is a symmetric p-multigrid V-cycle over orders
+ * N, floor(N/2), ..., 1 on the same mesh: tensor-product interpolation
+ * between orders (restriction its adjoint on unique nodes), additive
+ * overlapping Schwarz smoothing (each element extended by one node layer,
+ * separable local operator solved by fast diagonalisation, weights
+ * 1/sqrt(blocks holding the node) computed in FP64, damping 1/lambda_max
+ * from a power iteration), smoothing only on the N = 1 level.  r, z: L
+ * device values, FP64 for SEM_FP64 or FP32 for SEM_MIXED_FP32 (the FP32
+ * cycle sums shared nodes error-free); r continuous and masked.  Builds
+ * the levels on first use (handles of their own, kept with this one). */
+int sem_mg_apply(sem_handle h, const void* r, void* z, sem_precision p);
+
 int sem_set_option(sem_handle h, const char* key, int64_t value);
 int sem_get_option(sem_handle h, const char* key, double* value);
 

@@ -105,6 +105,7 @@ def _load():
         "sem_x0_predict": (i, [h, vp, vp, i]),
         "sem_x0_destroy": (None, [h]),
         "sem_get_option": (i, [h, ctypes.c_char_p, ctypes.POINTER(d)]),
+        "sem_mg_apply": (i, [h, vp, vp, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -120,7 +121,7 @@ EXPORTED = ("sem_setup", "sem_destroy", "sem_last_error", "sem_get_sizes", "sem_
             "sem_batch_setup", "sem_batch_problem", "sem_batch_pcg_solve", "sem_batch_get_option",
             "sem_batch_destroy", "sem_rhs_fourier", "sem_x0_create", "sem_x0_param_count",
             "sem_x0_params", "sem_x0_features", "sem_x0_gradients", "sem_x0_add_pair",
-            "sem_x0_train", "sem_x0_predict", "sem_x0_destroy")
+            "sem_x0_train", "sem_x0_predict", "sem_x0_destroy", "sem_mg_apply")
 
 
 class SemError(RuntimeError):
@@ -182,6 +183,10 @@ def sem_ax_local(h, u, w, precision):
 
 def sem_gs(h, v, precision):
     return _check(_lib.sem_gs(h, _ptr(v), precision), "sem_gs")
+
+
+def sem_mg_apply(h, r, z, precision):
+    return _check(_lib.sem_mg_apply(h, _ptr(r), _ptr(z), precision), "sem_mg_apply")
 
 
 def sem_glsc3(h, a, b, precision) -> float:
@@ -377,7 +382,7 @@ class Solver:
         o.use_graph = 1 if use_graph else -1
         o.chunk = chunk
         o.inner_tol = inner_tol
-        o.precond = 1 if precond else -1
+        o.precond = 2 if precond == "mg" else (1 if precond else -1)
         o.refine_mode = refine_mode
         o.replace_factor = replace_factor
         hist = None

@@ -41,6 +41,11 @@ int alloc(Handle& h, void** p, size_t bytes) {
   return 0;
 }
 
+void mg_free(Handle& h);
+int mg_apply(Handle& h, sem_precision p, const void* r, void* z);
+double mg_omega(Handle& h, int level);
+int mg_levels(Handle& h);
+
 static void free_handle(Handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -61,6 +66,7 @@ static void free_handle(Handle* h) {
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   for (cudaEvent_t e : h->kt_events) cudaEventDestroy(e);
+  mg_free(*h);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete static_cast<sem_handle_s*>(h);
 }
@@ -239,6 +245,12 @@ int sem_setup(const sem_mesh* mesh, int N, int geom_flags, void* stream, sem_han
       return fail(SEM_EINVAL);
     }
   }
+  for (int d = 0; d < 3; ++d) {
+    h->mesh_lo[d] = lo[d];
+    h->mesh_hi[d] = hi[d];
+  }
+  h->deform_amp = mesh->deform_amp;
+  h->deform_kind = mesh->deform_kind;
   rc = launch_geometry(*h, ucoords, mesh->deform_amp, mesh->deform_kind, lo, hi);
   if (ucoords) cudaFree(ucoords);
   if (rc) return fail(rc);
@@ -452,6 +464,23 @@ static void drop_graphs(Handle& h) {
   }
 }
 
+int sem_mg_apply(sem_handle h, const void* r, void* z, sem_precision p) {
+  if (!h || !r || !z) {
+    set_error("sem_mg_apply: null argument");
+    return SEM_EINVAL;
+  }
+  if (p != SEM_FP64 && p != SEM_MIXED_FP32) {
+    set_error("sem_mg_apply: precision must be SEM_FP64 or SEM_MIXED_FP32");
+    return SEM_EINVAL;
+  }
+  if (!is_device_ptr(r) || !is_device_ptr(z)) {
+    set_error("sem_mg_apply: r and z must be device pointers");
+    return SEM_EINVAL;
+  }
+  StreamScope scope(*h);
+  return mg_apply(*h, p, r, z);
+}
+
 int sem_set_option(sem_handle h, const char* key, int64_t value) {
   if (!h || !key) {
     set_error("sem_set_option: null argument");
@@ -468,8 +497,8 @@ int sem_set_option(sem_handle h, const char* key, int64_t value) {
     h->l2_persist = value != 0;
   } else if (k == "l2_hints" && (value == 0 || value == 1)) {
     h->l2_hints = value != 0;
-  } else if (k == "fuse_gs" && (value == 0 || value == 1)) {
-    h->fuse_gs = value != 0;
+  } else if (k == "fuse_gs" && value >= 0 && value <= 2) {
+    h->fuse_gs = (int)value;
   } else if (k == "kernel_timing" && (value == 0 || value == 1)) {
     h->kernel_timing = value != 0;   // setting it (either way) clears the sums
     h->kt_ms[0] = h->kt_ms[1] = h->kt_ms[2] = 0.0;
@@ -494,8 +523,11 @@ int sem_get_option(sem_handle h, const char* key, double* value) {
   else if (k == "use_tma") *value = h->use_tma ? 1 : 0;
   else if (k == "gs_acc") *value = h->gs_acc;
   else if (k == "l2_persist") *value = h->l2_persist ? 1 : 0;
-  else if (k == "fuse_gs") *value = h->fuse_gs ? 1 : 0;
+  else if (k == "fuse_gs") *value = h->fuse_gs;
   else if (k == "l2_hints") *value = h->l2_hints ? 1 : 0;
+  else if (k == "mg_levels") *value = mg_levels(*h);
+  else if (k.rfind("mg_omega_", 0) == 0 && k.size() == 10 && k[9] >= '0' && k[9] <= '9')
+    *value = mg_omega(*h, k[9] - '0');
   else if (k == "l2_window_bytes") *value = (double)h->l2_window_bytes;
   else if (k == "l2_max_persist") *value = (double)h->l2_max_persist;
   else if (k == "l2_max_window") *value = (double)h->l2_max_window;

@@ -480,7 +480,13 @@ int launch_cg_update32(Handle& h, int dm, float* x, float* r, const float* p, co
   return update_t<float>(h, dm, x, r, p, w, h.c32, minv, s, hist);
 }
 
-bool gs_fusable(const Handle& h) { return !h.gid_user && h.fuse_gs && h.n >= 2; }
+// Fold QQ^T into the update on box meshes; by default only where whole
+// float4 rows can be gathered (n a multiple of 4): the per-node gather of
+// other orders measured slower than the separate pass.
+bool gs_fusable(const Handle& h) {
+  if (h.gid_user || h.n < 2 || h.fuse_gs == 0) return false;
+  return h.fuse_gs == 2 || h.n % 4 == 0;
+}
 
 // Grid of a fused update kernel: the v4 update's grid (one thread per DOF,
 // capped) with the cap set by the kernel's own occupancy.  Where the cap

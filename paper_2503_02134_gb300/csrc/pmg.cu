@@ -1,0 +1,924 @@
+// p-multigrid preconditioner with overlapping Schwarz smoothing.
+//
+// The paper runs Nekbone with and without its multigrid preconditioner
+// (Sec. 3.1: `solveM` is 70 % of the time when enabled; Sec. 4: the square
+// roots of the Schwarz weights must stay FP64 in the mixed version) but
+// prints no algorithm.  Built here, for box meshes:
+//
+//  * levels: the same mesh at orders N, floor(N/2), ..., 1, each a handle of
+//    its own (operator, gather-scatter, mask);
+//  * transfer: prolongation = per-element tensor-product interpolation J
+//    (coarse GLL basis at fine GLL nodes); restriction = its adjoint on
+//    unique nodes, r_c = mask_c QQ^T_c (J^T x J^T x J^T)(r_f / mult_f);
+//  * smoother: additive Schwarz over the elements extended by one node
+//    layer (the (n+2)^3 block of the global node grid), each block solved by
+//    fast diagonalisation of the separable operator A x B x B + B x A x B +
+//    B x B x A built from 1-D GLL stiffness/mass on the extended 1-D grids
+//    (element and neighbour lengths; at N = 1 the overlap node is held at
+//    zero); block solutions summed with weights 1/sqrt(c), c = blocks
+//    holding the node (computed in FP64, also for the FP32 smoother), and
+//    damped by omega = 1/lambda_max(S A) from a power iteration;
+//  * cycle: symmetric V-cycle; the coarsest level applies the smoother.
+//
+// The block sum is a gather over the blocks that hold a node, found from its
+// grid position and summed in ascending element order, so every local copy
+// of a node gets the same bits (no scatter, no atomics).  The mixed variant
+// runs the cycle on FP32 data with the gather-scatter and block sums
+// accumulated error-free (TwoSum) and the CG dots in Dot2.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gs_sum.cuh"
+#include "pcg.cuh"
+
+namespace sem {
+
+int ax_dispatch_fp64(Handle& h, const double* u, double* w, const AxPrologue* pro);
+int ax_dispatch_fp32(Handle& h, const float* u, float* w, const AxPrologue* pro, int dm);
+int fp64_residual(Handle& h, const double* f, bool x_is_zero, double* relres, double* bnorm);
+
+constexpr int kMgMaxM = kMaxn + 2;   // extended points per direction (n + 2)
+
+struct MgLevel {
+  Handle* h = nullptr;     // level 0: the solver's handle (not owned)
+  bool owned = false;
+  int N = 0, n = 0, m = 0;
+  double* S64 = nullptr;   // [3][E][m*m], S_d(a, b) at a*m + b (column b = eigenvector b)
+  float* S32 = nullptr;
+  double* lam64 = nullptr;  // [3][E][m]
+  float* lam32 = nullptr;
+  uint8_t* act = nullptr;   // [3][E][m]: 1 where the extended index is an unknown
+  double* wsq64 = nullptr;  // [L] 1/sqrt(blocks holding the node)
+  float* wsq32 = nullptr;
+  double omega = 1.0;
+  double* J64 = nullptr;    // interpolation from the next coarser level: [n][nc]
+  float* J32 = nullptr;
+  // work vectors of this level (both precisions)
+  double *r64 = nullptr, *z64 = nullptr, *t64 = nullptr, *w64 = nullptr, *ext64 = nullptr;
+  float *r32 = nullptr, *z32 = nullptr, *t32 = nullptr, *w32 = nullptr, *ext32 = nullptr;
+};
+
+struct MgData {
+  std::vector<MgLevel> lv;
+  // outer-solve vectors
+  double *p64 = nullptr, *zz64 = nullptr, *w64 = nullptr, *r64 = nullptr, *x64 = nullptr;
+  float *p32 = nullptr, *zz32 = nullptr, *w32 = nullptr, *r32 = nullptr, *x32 = nullptr;
+  double* dot = nullptr;    // device scalar of the dots
+  double* dot_host = nullptr;
+};
+
+// ---------------------------------------------------------------- set-up
+
+// Element lengths along r, s, t: distance between the centroids of the two
+// opposite faces.  coords: x block, y block, z block of L values each.
+__global__ void mg_lengths_kernel(const double* __restrict__ X, int64_t L, int64_t E, int n,
+                                  double* __restrict__ len) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * E;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int d = (int)(t / E);
+    const int64_t e = t - d * E;
+    const int64_t n3 = (int64_t)n * n * n;
+    double c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        int i0, j0, k0, i1, j1, k1;
+        if (d == 0) { i0 = 0; i1 = n - 1; j0 = j1 = a; k0 = k1 = b; }
+        else if (d == 1) { j0 = 0; j1 = n - 1; i0 = i1 = a; k0 = k1 = b; }
+        else { k0 = 0; k1 = n - 1; i0 = i1 = a; j0 = j1 = b; }
+        const int64_t l0 = e * n3 + i0 + n * (j0 + n * k0);
+        const int64_t l1 = e * n3 + i1 + n * (j1 + n * k1);
+        for (int q = 0; q < 3; ++q) {
+          c0[q] += X[q * L + l0];
+          c1[q] += X[q * L + l1];
+        }
+      }
+    double s = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      const double dq = (c1[q] - c0[q]) / (n * n);
+      s += dq * dq;
+    }
+    len[d * E + e] = sqrt(s);
+  }
+}
+
+// Extended 1-D operators and their generalised eigenpairs, one thread per
+// (direction, element).  Extended index 0 = the left neighbour's node N-1,
+// 1..n = own nodes, n+1 = the right neighbour's node 1; assembled from the
+// three 1-D elements with all other nodes at zero; indices that are not
+// unknowns get identity rows.  B is diagonal, so A S = B S L with S^T B S = I
+// reduces to the symmetric eigenproblem of B^{-1/2} A B^{-1/2}, solved by
+// cyclic Jacobi rotations (Golub & Van Loan, Sec. 8.5).
+__global__ void mg_fdm_kernel(int N, int kx, int ky, int kz, int64_t E,
+                              const double* __restrict__ D, const double* __restrict__ wq,
+                              const double* __restrict__ len, double* __restrict__ S64,
+                              float* __restrict__ S32, double* __restrict__ lam64,
+                              float* __restrict__ lam32, uint8_t* __restrict__ act) {
+  const int n = N + 1, m = n + 2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * E;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int d = (int)(t / E);
+    const int64_t e = t - d * E;
+    const int ex = (int)(e % kx), ey = (int)((e / kx) % ky), ez = (int)(e / ((int64_t)kx * ky));
+    const int c = d == 0 ? ex : d == 1 ? ey : ez;
+    const int kd = d == 0 ? kx : d == 1 ? ky : kz;
+    const int64_t stride = d == 0 ? 1 : d == 1 ? kx : (int64_t)kx * ky;
+    const bool hl_ok = c > 0, hr_ok = c < kd - 1;
+    const double h = len[d * E + e];
+    const double hl = hl_ok ? len[d * E + e - stride] : h;
+    const double hr = hr_ok ? len[d * E + e + stride] : h;
+    double A[kMgMaxM][kMgMaxM];
+    double V[kMgMaxM][kMgMaxM];
+    double B[kMgMaxM];
+    for (int a = 0; a < m; ++a) {
+      B[a] = 0.0;
+      for (int b = 0; b < m; ++b) A[a][b] = 0.0;
+    }
+    // Ahat(a, b) = sum_q D(q, a) w_q D(q, b)
+    auto ahat = [&](int a, int b) {
+      double s = 0.0;
+      for (int q = 0; q < n; ++q) s += D[q * n + a] * wq[q] * D[q * n + b];
+      return s;
+    };
+    for (int a = 0; a < n; ++a) {
+      for (int b = 0; b < n; ++b) A[1 + a][1 + b] += (2.0 / h) * ahat(a, b);
+      B[1 + a] += 0.5 * h * wq[a];
+    }
+    for (int a = 0; a < 2; ++a) {
+      for (int b = 0; b < 2; ++b) {
+        A[a][b] += (2.0 / hl) * ahat(N - 1 + a, N - 1 + b);
+        A[n + a][n + b] += (2.0 / hr) * ahat(a, b);
+      }
+      B[a] += 0.5 * hl * wq[N - 1 + a];
+      B[n + a] += 0.5 * hr * wq[a];
+    }
+    bool on[kMgMaxM];
+    for (int a = 0; a < m; ++a) on[a] = true;
+    on[0] = hl_ok && N >= 2;
+    on[1] = hl_ok;
+    on[n] = hr_ok;
+    on[n + 1] = hr_ok && N >= 2;
+    for (int a = 0; a < m; ++a) {
+      if (on[a]) continue;
+      for (int b = 0; b < m; ++b) A[a][b] = A[b][a] = 0.0;
+      A[a][a] = 1.0;
+      B[a] = 1.0;
+    }
+    double bi[kMgMaxM];
+    for (int a = 0; a < m; ++a) bi[a] = 1.0 / sqrt(B[a]);
+    double nrm = 0.0;
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) {
+        A[a][b] *= bi[a] * bi[b];
+        V[a][b] = a == b ? 1.0 : 0.0;
+        nrm += A[a][b] * A[a][b];
+      }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+      double off = 0.0;
+      for (int p = 0; p < m; ++p)
+        for (int q = p + 1; q < m; ++q) off += A[p][q] * A[p][q];
+      if (off <= 1e-32 * nrm) break;
+      for (int p = 0; p < m; ++p)
+        for (int q = p + 1; q < m; ++q) {
+          const double apq = A[p][q];
+          if (apq == 0.0) continue;
+          const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
+          const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = tt * cs;
+          for (int k = 0; k < m; ++k) {   // columns p, q
+            const double akp = A[k][p], akq = A[k][q];
+            A[k][p] = cs * akp - sn * akq;
+            A[k][q] = sn * akp + cs * akq;
+          }
+          for (int k = 0; k < m; ++k) {   // rows p, q
+            const double apk = A[p][k], aqk = A[q][k];
+            A[p][k] = cs * apk - sn * aqk;
+            A[q][k] = sn * apk + cs * aqk;
+          }
+          for (int k = 0; k < m; ++k) {
+            const double vkp = V[k][p], vkq = V[k][q];
+            V[k][p] = cs * vkp - sn * vkq;
+            V[k][q] = sn * vkp + cs * vkq;
+          }
+        }
+    }
+    const int64_t so = (d * E + e) * (int64_t)m * m, lo = (d * E + e) * (int64_t)m;
+    for (int a = 0; a < m; ++a) {
+      lam64[lo + a] = A[a][a];
+      lam32[lo + a] = (float)A[a][a];
+      act[lo + a] = on[a] ? 1 : 0;
+      for (int b = 0; b < m; ++b) {
+        const double v = bi[a] * V[a][b];
+        S64[so + a * m + b] = v;
+        S32[so + a * m + b] = (float)v;
+      }
+    }
+  }
+}
+
+// Blocks holding the grid point at local index g (0..n-1) of element
+// coordinate c along one direction: up to three candidates c' = c-1, c, c+1
+// with extended index a' = c*N + g - c'*N + 1 in [0, n+1] and active.
+struct MgCand {
+  int cnt;
+  int elem[3];   // element coordinate along the direction, ascending
+  int ext[3];    // extended index in that element's block
+};
+
+__device__ __forceinline__ MgCand mg_candidates(int c, int g, int N, int kd, int64_t E,
+                                                int64_t e_of_c0, int64_t stride,
+                                                const uint8_t* __restrict__ actd) {
+  // actd: act of this direction, [E][m]; e_of_c0: element index with this
+  // direction's coordinate set to 0 (other coordinates as the node's element)
+  MgCand r;
+  r.cnt = 0;
+  const int m = N + 3;
+  for (int cc = c - 1; cc <= c + 1; ++cc) {
+    if (cc < 0 || cc >= kd) continue;
+    const int a = (c - cc) * N + g + 1;
+    if (a < 0 || a >= m) continue;
+    if (!actd[(e_of_c0 + (int64_t)cc * stride) * m + a]) continue;
+    r.elem[r.cnt] = cc;
+    r.ext[r.cnt] = a;
+    ++r.cnt;
+  }
+  return r;
+}
+
+// 1/sqrt(number of blocks holding each local node), in FP64.
+__global__ void mg_weights_kernel(int N, int kx, int ky, int kz, int64_t L,
+                                  const uint8_t* __restrict__ act, double* __restrict__ w64,
+                                  float* __restrict__ w32) {
+  const int n = N + 1, n3 = n * n * n;
+  const int64_t E = (int64_t)kx * ky * kz;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = l / n3;
+    const int rem = (int)(l - e * n3);
+    const int i = rem % n, j = (rem / n) % n, k = rem / (n * n);
+    const int ex = (int)(e % kx), ey = (int)((e / kx) % ky), ez = (int)(e / ((int64_t)kx * ky));
+    const int64_t m = N + 3;
+    const MgCand cx = mg_candidates(ex, i, N, kx, E, e - ex, 1, act);
+    const MgCand cy = mg_candidates(ey, j, N, ky, E, e - (int64_t)ey * kx, kx, act + E * m);
+    const MgCand cz = mg_candidates(ez, k, N, kz, E, e - (int64_t)ez * kx * ky, (int64_t)kx * ky,
+                                    act + 2 * E * m);
+    const double c = (double)(cx.cnt * cy.cnt * cz.cnt);
+    const double w = 1.0 / sqrt(c > 1.0 ? c : 1.0);
+    w64[l] = w;
+    w32[l] = (float)w;
+  }
+}
+
+// ---------------------------------------------------------------- cycle kernels
+
+// Block solve: gather the weighted residual on every element's extended
+// block, apply S^T along each direction, divide by lam_x + lam_y + lam_z,
+// apply S, write the block (inactive points zero).  One CTA per element.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    mg_block_solve_kernel(int N, int kx, int ky, int64_t E, const T* __restrict__ r,
+                          const T* __restrict__ wsq, const T* __restrict__ S,
+                          const T* __restrict__ lam, const uint8_t* __restrict__ act,
+                          T* __restrict__ ext) {
+  extern __shared__ __align__(16) unsigned char mg_smem[];
+  const int n = N + 1, m = n + 2, m2 = m * m, m3 = m2 * m, n3 = n * n * n;
+  T* buf = reinterpret_cast<T*>(mg_smem);
+  T* sS = buf + m3;          // 3 * m2
+  T* sl = sS + 3 * m2;       // 3 * m
+  uint8_t* sa = reinterpret_cast<uint8_t*>(sl + 3 * m);   // 3 * m
+  const int64_t kxky = (int64_t)kx * ky;
+  for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    for (int q = threadIdx.x; q < 3 * m2; q += blockDim.x) {
+      const int d = q / m2, o = q - d * m2;
+      sS[q] = S[(d * E + e) * m2 + o];
+    }
+    for (int q = threadIdx.x; q < 3 * m; q += blockDim.x) {
+      const int d = q / m, o = q - d * m;
+      sl[q] = lam[(d * E + e) * m + o];
+      sa[q] = act[(d * E + e) * m + o];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < m3; q += blockDim.x) {
+      const int a = q % m, b = (q / m) % m, c = q / m2;
+      T v = T(0);
+      if (sa[a] && sa[m + b] && sa[2 * m + c]) {
+        const int dx = a == 0 ? -1 : (a == m - 1 ? 1 : 0);
+        const int dy = b == 0 ? -1 : (b == m - 1 ? 1 : 0);
+        const int dz = c == 0 ? -1 : (c == m - 1 ? 1 : 0);
+        const int i = a == 0 ? N - 1 : (a == m - 1 ? 1 : a - 1);
+        const int j = b == 0 ? N - 1 : (b == m - 1 ? 1 : b - 1);
+        const int k = c == 0 ? N - 1 : (c == m - 1 ? 1 : c - 1);
+        const int64_t ee = e + dx + (int64_t)dy * kx + (int64_t)dz * kxky;
+        const int64_t l = ee * n3 + i + n * (j + n * k);
+        v = r[l] * wsq[l];
+      }
+      buf[q] = v;
+    }
+    __syncthreads();
+    // forward: S^T along x (rows of fixed b, c), then y, then z
+    for (int pass = 0; pass < 6; ++pass) {
+      const int d = pass % 3;
+      const bool fwd = pass < 3;
+      const T* Sd = sS + d * m2;
+      for (int row = threadIdx.x; row < m2; row += blockDim.x) {
+        const int u = row % m, v2 = row / m;
+        int base, step;
+        if (d == 0) { base = u * m + v2 * m2; step = 1; }          // (b, c) = (u, v2)
+        else if (d == 1) { base = u + v2 * m2; step = m; }         // (a, c)
+        else { base = u + v2 * m; step = m2; }                     // (a, b)
+        T in[kMgMaxM];
+        for (int t = 0; t < m; ++t) in[t] = buf[base + t * step];
+        for (int o = 0; o < m; ++o) {
+          T s = T(0);
+          if (fwd)
+            for (int t = 0; t < m; ++t) s += Sd[t * m + o] * in[t];   // (S^T in)_o
+          else
+            for (int t = 0; t < m; ++t) s += Sd[o * m + t] * in[t];   // (S in)_o
+          buf[base + o * step] = s;
+        }
+      }
+      __syncthreads();
+      if (pass == 2) {
+        for (int q = threadIdx.x; q < m3; q += blockDim.x) {
+          const int a = q % m, b = (q / m) % m, c = q / m2;
+          buf[q] = buf[q] / (sl[a] + sl[m + b] + sl[2 * m + c]);
+        }
+        __syncthreads();
+      }
+    }
+    for (int q = threadIdx.x; q < m3; q += blockDim.x) {
+      const int a = q % m, b = (q / m) % m, c = q / m2;
+      ext[e * m3 + q] = (sa[a] && sa[m + b] && sa[2 * m + c]) ? buf[q] : T(0);
+    }
+    __syncthreads();
+  }
+}
+
+// z = (acc ? z : 0) + omega * wsq * mask * sum of the blocks holding the node
+// (ascending element order: the same bits on every copy).
+template <typename T, int ACC>
+__global__ void mg_block_sum_kernel(int N, int kx, int ky, int kz, int64_t L,
+                                    const T* __restrict__ ext, const uint8_t* __restrict__ act,
+                                    const T* __restrict__ wsq, const double* __restrict__ mask,
+                                    T omega, int accumulate, T* __restrict__ z) {
+  const int n = N + 1, n3 = n * n * n, m = n + 2, m2 = m * m, m3 = m2 * m;
+  const int64_t E = (int64_t)kx * ky * kz;
+  const int64_t kxky = (int64_t)kx * ky;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = l / n3;
+    const int rem = (int)(l - e * n3);
+    const int i = rem % n, j = (rem / n) % n, k = rem / (n * n);
+    const int ex = (int)(e % kx), ey = (int)((e / kx) % ky), ez = (int)(e / kxky);
+    const int64_t ex0 = e - ex, ey0 = e - (int64_t)ey * kx, ez0 = e - (int64_t)ez * kxky;
+    const MgCand cx = mg_candidates(ex, i, N, kx, E, ex0, 1, act);
+    const MgCand cy = mg_candidates(ey, j, N, ky, E, ey0, kx, act + E * m);
+    const MgCand cz = mg_candidates(ez, k, N, kz, E, ez0, kxky, act + 2 * E * m);
+    GsSum<T, ACC> acc;
+    for (int c = 0; c < cz.cnt; ++c)
+      for (int b = 0; b < cy.cnt; ++b)
+        for (int a = 0; a < cx.cnt; ++a) {
+          const int64_t eb = cx.elem[a] + (int64_t)cy.elem[b] * kx + (int64_t)cz.elem[c] * kxky;
+          acc.add(ext[eb * m3 + cx.ext[a] + m * cy.ext[b] + m2 * cz.ext[c]]);
+        }
+    T v = (cx.cnt && cy.cnt && cz.cnt) ? acc.result() : T(0);
+    v = omega * (wsq[l] * ((T)mask[l] * v));
+    z[l] = accumulate ? z[l] + v : v;
+  }
+}
+
+// Element-wise tensor contraction out = (M x M x M) in, M: [no][ni].
+// scale (optional): in is multiplied by 1/scale first (restriction);
+// add: out += result (prolongation).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    mg_transfer_kernel(int ni, int no, int64_t E, const T* __restrict__ M, int transpose,
+                       const T* __restrict__ in, const double* __restrict__ div,
+                       T* __restrict__ out, int add) {
+  extern __shared__ __align__(16) unsigned char mg_smem[];
+  const int nmax = ni > no ? ni : no;
+  const int nb = nmax * nmax * nmax;
+  T* b0 = reinterpret_cast<T*>(mg_smem);
+  T* b1 = b0 + nb;
+  T* sM = b1 + nb;
+  const int ni3 = ni * ni * ni, no3 = no * no * no;
+  for (int q = threadIdx.x; q < ni * no; q += blockDim.x) {
+    // sM[o * ni + t] = M(o, t): rows out, cols in
+    const int o = q / ni, t = q - o * ni;
+    sM[q] = transpose ? M[t * no + o] : M[o * ni + t];
+  }
+  for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < ni3; q += blockDim.x) {
+      T v = in[e * ni3 + q];
+      if (div) v = v / (T)div[e * ni3 + q];
+      b0[q] = v;
+    }
+    __syncthreads();
+    // along i: [ni][ni][ni] -> [ni][ni][no]
+    for (int q = threadIdx.x; q < ni * ni * no; q += blockDim.x) {
+      const int o = q % no, jk = q / no;
+      T s = T(0);
+      for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * b0[jk * ni + t];
+      b1[q] = s;
+    }
+    __syncthreads();
+    // along j: [ni(k)][ni(j)][no(i)] -> [ni][no][no]
+    for (int q = threadIdx.x; q < ni * no * no; q += blockDim.x) {
+      const int i = q % no, o = (q / no) % no, k = q / (no * no);
+      T s = T(0);
+      for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * b1[(k * ni + t) * no + i];
+      b0[q] = s;
+    }
+    __syncthreads();
+    // along k: [ni][no][no] -> [no][no][no]
+    for (int q = threadIdx.x; q < no3; q += blockDim.x) {
+      const int ij = q % (no * no), o = q / (no * no);
+      T s = T(0);
+      for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * b0[t * no * no + ij];
+      if (add) out[e * no3 + q] += s;
+      else out[e * no3 + q] = s;
+    }
+  }
+}
+
+// t = r - mask * w
+template <typename T>
+__global__ void mg_residual_kernel(int64_t L, const T* __restrict__ r, const T* __restrict__ w,
+                                   const double* __restrict__ mask, T* __restrict__ t) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x)
+    t[l] = r[l] - (T)mask[l] * w[l];
+}
+
+template <typename T>
+__global__ void mg_mask_kernel(int64_t L, const double* __restrict__ mask, T* __restrict__ v) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x)
+    v[l] = (T)mask[l] * v[l];
+}
+
+// y = a x + b y
+template <typename T>
+__global__ void mg_axpby_kernel(int64_t L, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+       l += (int64_t)gridDim.x * blockDim.x)
+    y[l] = a * x[l] + b * y[l];
+}
+
+static int grid_of(const Handle& h, int64_t work) {
+  int64_t g = (work + 255) / 256;
+  const int64_t cap = (int64_t)h.num_sms * 8;
+  return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+// ---------------------------------------------------------------- level ops
+
+template <typename T>
+struct MgPrec;
+template <>
+struct MgPrec<double> {
+  static constexpr sem_precision p = SEM_FP64;
+  static double* r(MgLevel& v) { return v.r64; }
+  static double* z(MgLevel& v) { return v.z64; }
+  static double* t(MgLevel& v) { return v.t64; }
+  static double* w(MgLevel& v) { return v.w64; }
+  static double* ext(MgLevel& v) { return v.ext64; }
+  static const double* S(MgLevel& v) { return v.S64; }
+  static const double* lam(MgLevel& v) { return v.lam64; }
+  static const double* wsq(MgLevel& v) { return v.wsq64; }
+  static const double* J(MgLevel& v) { return v.J64; }
+};
+template <>
+struct MgPrec<float> {
+  static constexpr sem_precision p = SEM_MIXED_FP32;
+  static float* r(MgLevel& v) { return v.r32; }
+  static float* z(MgLevel& v) { return v.z32; }
+  static float* t(MgLevel& v) { return v.t32; }
+  static float* w(MgLevel& v) { return v.w32; }
+  static float* ext(MgLevel& v) { return v.ext32; }
+  static const float* S(MgLevel& v) { return v.S32; }
+  static const float* lam(MgLevel& v) { return v.lam32; }
+  static const float* wsq(MgLevel& v) { return v.wsq32; }
+  static const float* J(MgLevel& v) { return v.J32; }
+};
+
+static size_t block_solve_smem(int m, size_t tsz) {
+  return tsz * ((size_t)m * m * m + 3 * (size_t)m * m + 3 * m) + 3 * m + 16;
+}
+
+// z = (acc ? z : 0) + omega * Schwarz(r) on level lv
+template <typename T>
+static int mg_schwarz(MgLevel& lv, const T* r, T* z, bool accumulate) {
+  Handle& h = *lv.h;
+  using P = MgPrec<T>;
+  const int m = lv.m;
+  const size_t smem = block_solve_smem(m, sizeof(T));
+  auto k1 = mg_block_solve_kernel<T>;
+  SEM_CUDA(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int g1 = (int)std::min<int64_t>(h.E, (int64_t)h.num_sms * 8);
+  k1<<<g1, 128, smem, h.stream>>>(lv.N, h.kx, h.ky, h.E, r, P::wsq(lv), P::S(lv), P::lam(lv),
+                                  lv.act, P::ext(lv));
+  SEM_CUDA(cudaGetLastError());
+  const int acc = accumulate ? 1 : 0;
+  if (sizeof(T) == 8)
+    mg_block_sum_kernel<double, kGsFP64><<<grid_of(h, h.L), 256, 0, h.stream>>>(
+        lv.N, h.kx, h.ky, h.kz, h.L, (const double*)P::ext(lv), lv.act, (const double*)P::wsq(lv),
+        h.mask64, lv.omega, acc, (double*)z);
+  else
+    mg_block_sum_kernel<float, kGsTwoSum><<<grid_of(h, h.L), 256, 0, h.stream>>>(
+        lv.N, h.kx, h.ky, h.kz, h.L, (const float*)P::ext(lv), lv.act, (const float*)P::wsq(lv),
+        h.mask64, (float)lv.omega, acc, (float*)z);
+  h.launches += 2;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// w = mask QQ^T A_L u on level lv
+template <typename T>
+static int mg_apply_a(MgLevel& lv, const T* u, T* w) {
+  Handle& h = *lv.h;
+  int rc;
+  if (sizeof(T) == 8) {
+    if ((rc = ax_dispatch_fp64(h, (const double*)u, (double*)w, nullptr))) return rc;
+  } else {
+    if ((rc = ax_dispatch_fp32(h, (const float*)u, (float*)w, nullptr, kDotDot2))) return rc;
+  }
+  if ((rc = launch_gs(h, MgPrec<T>::p, w))) return rc;
+  mg_mask_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, h.mask64, w);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+template <typename T>
+static int mg_transfer(Handle& h, int ni, int no, int64_t E, const T* M, bool transpose,
+                       const T* in, const double* div, T* out, bool add) {
+  const int nmax = std::max(ni, no);
+  const size_t smem = sizeof(T) * (2 * (size_t)nmax * nmax * nmax + (size_t)ni * no);
+  auto k = mg_transfer_kernel<T>;
+  SEM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int g = (int)std::min<int64_t>(E, (int64_t)h.num_sms * 8);
+  k<<<g, 256, smem, h.stream>>>(ni, no, E, M, transpose ? 1 : 0, in, div, out, add ? 1 : 0);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// z_l = V-cycle(r_l)
+template <typename T>
+static int mg_vcycle(MgData& mg, int l, const T* r, T* z) {
+  MgLevel& lv = mg.lv[l];
+  Handle& h = *lv.h;
+  using P = MgPrec<T>;
+  int rc;
+  if ((rc = mg_schwarz<T>(lv, r, z, false))) return rc;
+  if (l + 1 == (int)mg.lv.size()) return 0;
+  MgLevel& cv = mg.lv[l + 1];
+  Handle& hc = *cv.h;
+  T* t = P::t(lv);
+  if ((rc = mg_apply_a<T>(lv, z, P::w(lv)))) return rc;
+  mg_residual_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, r, P::w(lv), h.mask64, t);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  // restriction: (J^T)^{x3} (t / mult), then QQ^T and mask on the coarse level
+  if ((rc = mg_transfer<T>(h, lv.n, cv.n, h.E, P::J(lv), true, t, h.mult64, P::r(cv), false)))
+    return rc;
+  if ((rc = launch_gs(hc, P::p, P::r(cv)))) return rc;
+  mg_mask_kernel<T><<<grid_of(hc, hc.L), 256, 0, h.stream>>>(hc.L, hc.mask64, P::r(cv));
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  if ((rc = mg_vcycle<T>(mg, l + 1, P::r(cv), P::z(cv)))) return rc;
+  if ((rc = mg_transfer<T>(h, cv.n, lv.n, h.E, P::J(lv), false, P::z(cv), nullptr, z, true)))
+    return rc;
+  if ((rc = mg_apply_a<T>(lv, z, P::w(lv)))) return rc;
+  mg_residual_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, r, P::w(lv), h.mask64, t);
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return mg_schwarz<T>(lv, t, z, true);
+}
+
+// ---------------------------------------------------------------- set-up
+
+static double read_dot(Handle& h, MgData& mg) {
+  cudaMemcpyAsync(mg.dot_host, mg.dot, sizeof(double), cudaMemcpyDeviceToHost, h.stream);
+  cudaStreamSynchronize(h.stream);
+  return *mg.dot_host;
+}
+
+template <typename T>
+static int mg_alloc(Handle& h, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (multigrid)");
+  return 0;
+}
+
+static void level_free(MgLevel& v) {
+  void* ptrs[] = {v.S64, v.S32, v.lam64, v.lam32, v.act, v.wsq64, v.wsq32, v.J64, v.J32,
+                  v.r64, v.z64, v.t64, v.w64, v.ext64, v.r32, v.z32, v.t32, v.w32, v.ext32};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (v.owned && v.h) sem_destroy(static_cast<sem_handle>(static_cast<sem_handle_s*>(v.h)));
+  v = MgLevel();
+}
+
+void mg_free(Handle& h) {
+  if (!h.mg) return;
+  for (auto& v : h.mg->lv) level_free(v);
+  void* ptrs[] = {h.mg->p64, h.mg->zz64, h.mg->w64, h.mg->r64, h.mg->x64, h.mg->p32,
+                  h.mg->zz32, h.mg->w32, h.mg->r32, h.mg->x32, h.mg->dot};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h.mg->dot_host) cudaFreeHost(h.mg->dot_host);
+  delete h.mg;
+  h.mg = nullptr;
+}
+
+// Interpolation matrix J[p][a] = l_a(x_p) from coarse nodes xc to fine nodes xf.
+static std::vector<double> interp(const std::vector<double>& xc, const std::vector<double>& xf) {
+  const int nc = (int)xc.size(), nf = (int)xf.size();
+  std::vector<double> J((size_t)nf * nc, 1.0);
+  for (int p = 0; p < nf; ++p)
+    for (int a = 0; a < nc; ++a)
+      for (int q = 0; q < nc; ++q)
+        if (q != a) J[(size_t)p * nc + a] *= (xf[p] - xc[q]) / (xc[a] - xc[q]);
+  return J;
+}
+
+static int level_setup(MgLevel& v) {
+  Handle& h = *v.h;
+  int rc;
+  v.N = h.N;
+  v.n = h.n;
+  v.m = h.n + 2;
+  const size_t E = (size_t)h.E, L = (size_t)h.L, m = (size_t)v.m;
+  if ((rc = mg_alloc(h, &v.S64, 3 * E * m * m)) || (rc = mg_alloc(h, &v.S32, 3 * E * m * m)) ||
+      (rc = mg_alloc(h, &v.lam64, 3 * E * m)) || (rc = mg_alloc(h, &v.lam32, 3 * E * m)) ||
+      (rc = mg_alloc(h, &v.act, 3 * E * m)) || (rc = mg_alloc(h, &v.wsq64, L)) ||
+      (rc = mg_alloc(h, &v.wsq32, L)) || (rc = mg_alloc(h, &v.r64, L)) ||
+      (rc = mg_alloc(h, &v.z64, L)) || (rc = mg_alloc(h, &v.t64, L)) ||
+      (rc = mg_alloc(h, &v.w64, L)) || (rc = mg_alloc(h, &v.ext64, E * m * m * m)) ||
+      (rc = mg_alloc(h, &v.r32, L)) || (rc = mg_alloc(h, &v.z32, L)) ||
+      (rc = mg_alloc(h, &v.t32, L)) || (rc = mg_alloc(h, &v.w32, L)) ||
+      (rc = mg_alloc(h, &v.ext32, E * m * m * m)))
+    return rc;
+  double* len = nullptr;
+  if ((rc = mg_alloc(h, &len, 3 * E))) return rc;
+  const int g = grid_of(h, 3 * h.E);
+  mg_lengths_kernel<<<g, 256, 0, h.stream>>>(h.coords, h.L, h.E, h.n, len);
+  mg_fdm_kernel<<<g, 64, 0, h.stream>>>(h.N, h.kx, h.ky, h.kz, h.E, h.D64, h.wq, len, v.S64,
+                                        v.S32, v.lam64, v.lam32, v.act);
+  mg_weights_kernel<<<grid_of(h, h.L), 256, 0, h.stream>>>(h.N, h.kx, h.ky, h.kz, h.L, v.act,
+                                                           v.wsq64, v.wsq32);
+  h.launches += 3;
+  cudaError_t ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h.stream);
+  cudaFree(len);
+  if (ce != cudaSuccess) return cuda_fail(ce, "multigrid set-up");
+  return 0;
+}
+
+// lambda_max(S A) by power iteration from the SplitMix64 vector of `seed`,
+// Rayleigh quotient in the A inner product (FP64); omega = 1 / lambda.
+static int level_omega(MgData& mg, MgLevel& v, int iters, uint64_t seed) {
+  Handle& h = *v.h;
+  int rc;
+  double* x = v.r64;
+  double* ax = v.t64;
+  double* y = v.z64;
+  double* ay = v.w64;
+  if ((rc = launch_rhs(h, 1, seed, x))) return rc;
+  v.omega = 1.0;
+  double lam = 1.0;
+  for (int it = 0; it < iters; ++it) {
+    if ((rc = mg_apply_a<double>(v, x, ax))) return rc;
+    if ((rc = mg_schwarz<double>(v, ax, y, false))) return rc;   // omega = 1 here
+    if ((rc = mg_apply_a<double>(v, y, ay))) return rc;
+    if ((rc = launch_glsc3(h, SEM_FP64, y, ay, mg.dot))) return rc;
+    const double yay = read_dot(h, mg);
+    if ((rc = launch_glsc3(h, SEM_FP64, y, ax, mg.dot))) return rc;
+    const double yax = read_dot(h, mg);
+    if ((rc = launch_glsc3(h, SEM_FP64, y, y, mg.dot))) return rc;
+    const double yy = read_dot(h, mg);
+    if (!(yax > 0.0) || !(yy > 0.0)) {
+      set_error("multigrid set-up: power iteration broke down");
+      return SEM_EINVAL;
+    }
+    lam = yay / yax;
+    mg_axpby_kernel<double><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, 1.0 / sqrt(yy), y, 0.0, x);
+    SEM_CUDA(cudaGetLastError());
+  }
+  v.omega = 1.0 / lam;
+  return 0;
+}
+
+int mg_ensure(Handle& h) {
+  if (h.mg) return 0;
+  if (h.gid_user) {
+    set_error("multigrid: needs a box mesh (sem_setup without gid)");
+    return SEM_EINVAL;
+  }
+  MgData* mg = new MgData();
+  h.mg = mg;
+  auto fail = [&](int rc) {
+    mg_free(h);
+    return rc;
+  };
+  std::vector<int> orders{h.N};
+  while (orders.back() > 1) orders.push_back(std::max(1, orders.back() / 2));
+  mg->lv.resize(orders.size());
+  int rc;
+  for (size_t l = 0; l < orders.size(); ++l) {
+    MgLevel& v = mg->lv[l];
+    if (l == 0) {
+      v.h = &h;
+    } else {
+      sem_mesh mesh;
+      memset(&mesh, 0, sizeof(mesh));
+      mesh.kx = h.kx;
+      mesh.ky = h.ky;
+      mesh.kz = h.kz;
+      for (int d = 0; d < 3; ++d) {
+        mesh.lo[d] = h.mesh_lo[d];
+        mesh.hi[d] = h.mesh_hi[d];
+      }
+      mesh.deform_amp = h.deform_amp;
+      mesh.deform_kind = h.deform_kind;
+      sem_handle sub = nullptr;
+      if ((rc = sem_setup(&mesh, orders[l], 0, h.stream, &sub))) return fail(rc);
+      v.h = sub;
+      v.owned = true;
+    }
+    if ((rc = level_setup(v))) return fail(rc);
+  }
+  // interpolation matrices (host FP64 from each level's GLL nodes)
+  for (size_t l = 0; l + 1 < orders.size(); ++l) {
+    MgLevel& f = mg->lv[l];
+    MgLevel& c = mg->lv[l + 1];
+    std::vector<double> xf(f.n), xc(c.n);
+    SEM_CUDA(cudaMemcpy(xf.data(), f.h->xi, sizeof(double) * f.n, cudaMemcpyDeviceToHost));
+    SEM_CUDA(cudaMemcpy(xc.data(), c.h->xi, sizeof(double) * c.n, cudaMemcpyDeviceToHost));
+    const std::vector<double> J = interp(xc, xf);
+    std::vector<float> J32(J.begin(), J.end());
+    if ((rc = mg_alloc(h, &f.J64, J.size())) || (rc = mg_alloc(h, &f.J32, J.size()))) return fail(rc);
+    SEM_CUDA(cudaMemcpy(f.J64, J.data(), sizeof(double) * J.size(), cudaMemcpyHostToDevice));
+    SEM_CUDA(cudaMemcpy(f.J32, J32.data(), sizeof(float) * J.size(), cudaMemcpyHostToDevice));
+  }
+  const size_t L = (size_t)h.L;
+  if ((rc = mg_alloc(h, &mg->p64, L)) || (rc = mg_alloc(h, &mg->zz64, L)) ||
+      (rc = mg_alloc(h, &mg->w64, L)) || (rc = mg_alloc(h, &mg->r64, L)) ||
+      (rc = mg_alloc(h, &mg->x64, L)) || (rc = mg_alloc(h, &mg->p32, L)) ||
+      (rc = mg_alloc(h, &mg->zz32, L)) || (rc = mg_alloc(h, &mg->w32, L)) ||
+      (rc = mg_alloc(h, &mg->r32, L)) || (rc = mg_alloc(h, &mg->x32, L)) ||
+      (rc = mg_alloc(h, &mg->dot, 1)))
+    return fail(rc);
+  if (cudaMallocHost((void**)&mg->dot_host, sizeof(double)) != cudaSuccess)
+    return fail(cuda_fail(cudaErrorMemoryAllocation, "cudaMallocHost"));
+  for (auto& v : mg->lv)
+    if ((rc = level_omega(*mg, v, 20, 12345))) return fail(rc);
+  return 0;
+}
+
+// ---------------------------------------------------------------- solves
+
+// Apply the preconditioner: z = V(r) (device vectors of the precision's type).
+int mg_apply(Handle& h, sem_precision p, const void* r, void* z) {
+  int rc;
+  if ((rc = mg_ensure(h))) return rc;
+  if (p == SEM_FP64) return mg_vcycle<double>(*h.mg, 0, (const double*)r, (double*)z);
+  return mg_vcycle<float>(*h.mg, 0, (const float*)r, (float*)z);
+}
+
+// CG preconditioned by one V-cycle per iteration (T data; dots in FP64 or
+// Dot2) on A d = r0 from d = 0, until ||r||_c <= stop (absolute) or maxit.
+// Returns the iterations done through *iters and the last ||r||_c.
+template <typename T>
+static int mg_cg(Handle& h, MgData& mg, const T* r0, T* d, double stop, int maxit, int* iters,
+                 double* rnorm) {
+  using P = MgPrec<T>;
+  MgLevel& f = mg.lv[0];
+  const sem_precision p = P::p;
+  T* r = sizeof(T) == 8 ? (T*)mg.r64 : (T*)mg.r32;
+  T* z = sizeof(T) == 8 ? (T*)mg.zz64 : (T*)mg.zz32;
+  T* pp = sizeof(T) == 8 ? (T*)mg.p64 : (T*)mg.p32;
+  T* w = sizeof(T) == 8 ? (T*)mg.w64 : (T*)mg.w32;
+  int rc;
+  const int g = grid_of(h, h.L);
+  SEM_CUDA(cudaMemcpyAsync(r, r0, sizeof(T) * h.L, cudaMemcpyDeviceToDevice, h.stream));
+  SEM_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * h.L, h.stream));
+  if ((rc = launch_glsc3(h, p, r, r, mg.dot))) return rc;
+  double rtr = read_dot(h, mg);
+  *iters = 0;
+  *rnorm = sqrt(rtr);
+  if (*rnorm <= stop) return 0;
+  if ((rc = mg_vcycle<T>(mg, 0, r, z))) return rc;
+  if ((rc = launch_glsc3(h, p, r, z, mg.dot))) return rc;
+  double rtz = read_dot(h, mg);
+  SEM_CUDA(cudaMemcpyAsync(pp, z, sizeof(T) * h.L, cudaMemcpyDeviceToDevice, h.stream));
+  for (int it = 1; it <= maxit; ++it) {
+    if ((rc = mg_apply_a<T>(f, pp, w))) return rc;
+    if ((rc = launch_glsc3(h, p, w, pp, mg.dot))) return rc;
+    const double pap = read_dot(h, mg);
+    if (!(pap > 0.0) || !(rtz > 0.0)) {
+      set_error("multigrid CG: breakdown (p.Ap or r.z not positive)");
+      return SEM_BREAKDOWN;
+    }
+    const double alpha = rtz / pap;
+    mg_axpby_kernel<T><<<g, 256, 0, h.stream>>>(h.L, (T)alpha, pp, (T)1, d);
+    mg_axpby_kernel<T><<<g, 256, 0, h.stream>>>(h.L, (T)(-alpha), w, (T)1, r);
+    h.launches += 2;
+    SEM_CUDA(cudaGetLastError());
+    if ((rc = launch_glsc3(h, p, r, r, mg.dot))) return rc;
+    rtr = read_dot(h, mg);
+    *iters = it;
+    *rnorm = sqrt(rtr);
+    if (*rnorm <= stop) return 0;
+    if ((rc = mg_vcycle<T>(mg, 0, r, z))) return rc;
+    if ((rc = launch_glsc3(h, p, r, z, mg.dot))) return rc;
+    const double rtz_new = read_dot(h, mg);
+    const double beta = rtz_new / rtz;
+    rtz = rtz_new;
+    mg_axpby_kernel<T><<<g, 256, 0, h.stream>>>(h.L, (T)1, z, (T)beta, pp);
+    ++h.launches;
+    SEM_CUDA(cudaGetLastError());
+  }
+  return SEM_MAXIT;
+}
+
+// Multigrid-preconditioned solve of A x = f (x0 optional), FP64 or mixed.
+// Mixed: FP64 outer residual r64 = f - A64 x64; inner FP32 multigrid CG on
+// A d = r64 reducing ||r|| by max(inner_floor, 0.5 tol / relres); x64 += d.
+int pcg_mg_solve(Handle& h, const double* f, const double* x0, double* x, double tol, int maxit,
+                 sem_precision prec, double inner_floor, int max_cycles, sem_info* info) {
+  int rc;
+  if ((rc = mg_ensure(h))) return rc;
+  MgData& mg = *h.mg;
+  sem_info res{};
+  const int64_t launches0 = h.launches;
+  SEM_CUDA(cudaEventRecord(h.ev0, h.stream));
+  if ((rc = launch_masked_copy64(h, x0, h.x64))) return rc;
+  double relres = 1.0, bnorm = 0.0;
+  if ((rc = fp64_residual(h, f, x0 == nullptr, &relres, &bnorm))) return rc;
+  int total = 0, cycles = 0;
+  res.status = 0;
+  if (bnorm > 0.0 && relres > tol) {
+    if (prec == SEM_FP64) {
+      int its = 0;
+      double rn = 0.0;
+      const int cg_rc = mg_cg<double>(h, mg, h.r64, mg.x64, tol * bnorm, maxit, &its, &rn);
+      if (cg_rc < 0) return cg_rc;
+      total = its;
+      const int g = grid_of(h, h.L);
+      mg_axpby_kernel<double><<<g, 256, 0, h.stream>>>(h.L, 1.0, mg.x64, 1.0, h.x64);
+      SEM_CUDA(cudaGetLastError());
+      if ((rc = fp64_residual(h, f, false, &relres, nullptr))) return rc;
+      res.status = cg_rc == SEM_MAXIT ? SEM_MAXIT : 0;
+      res.relres = rn / bnorm;
+    } else {
+      for (;;) {
+        if (relres <= tol) break;
+        if (cycles >= max_cycles) { res.status = SEM_STAGNATED; break; }
+        if (total >= maxit) { res.status = SEM_MAXIT; break; }
+        const double red = std::max(inner_floor, 0.5 * tol / relres);
+        if ((rc = launch_cast64to32(h, h.r64, mg.lv[0].t32))) return rc;
+        // the inner stop is relative to the FP32 copy of r64
+        if ((rc = launch_glsc3(h, SEM_MIXED_FP32, mg.lv[0].t32, mg.lv[0].t32, mg.dot))) return rc;
+        const double r0n = sqrt(read_dot(h, mg));
+        int its = 0;
+        double rn = 0.0;
+        rc = mg_cg<float>(h, mg, mg.lv[0].t32, mg.x32, red * r0n, maxit - total, &its, &rn);
+        if (rc < 0) return rc;
+        total += its;
+        ++cycles;
+        if ((rc = launch_add32to64(h, h.x64, mg.x32))) return rc;
+        const double prev = relres;
+        if ((rc = fp64_residual(h, f, false, &relres, nullptr))) return rc;
+        res.relres = rn / bnorm;
+        if (relres > 0.9 * prev && relres > tol) { res.status = SEM_STAGNATED; break; }
+      }
+    }
+  }
+  SEM_CUDA(cudaMemcpyAsync(x, h.x64, sizeof(double) * h.L, cudaMemcpyDeviceToDevice, h.stream));
+  SEM_CUDA(cudaEventRecord(h.ev1, h.stream));
+  SEM_CUDA(cudaStreamSynchronize(h.stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h.ev0, h.ev1);
+  res.iters = total;
+  res.refinements = cycles;
+  res.relres_true = relres;
+  res.solve_ms = ms;
+  res.launches = h.launches - launches0;
+  if (res.status == 0 && relres > tol) res.status = SEM_MAXIT;
+  if (info) *info = res;
+  return res.status;
+}
+
+double mg_omega(Handle& h, int level) {
+  if (!h.mg || level < 0 || level >= (int)h.mg->lv.size()) return -1.0;
+  return h.mg->lv[level].omega;
+}
+int mg_levels(Handle& h) { return h.mg ? (int)h.mg->lv.size() : 0; }
+
+}  // namespace sem

@@ -39,11 +39,17 @@ struct PcgScalars {
 };
 
 // Where to write residual history (device array of maxit+1 doubles) or null.
+struct MgData;
+
 struct Handle {
   int N = 0, n = 0;
   int64_t E = 0, L = 0, U = 0;
   int kx = 0, ky = 0, kz = 0;
   bool gid_user = false;               // mesh numbered by the caller (no box structure)
+  double mesh_lo[3] = {}, mesh_hi[3] = {};   // box mesh description (for multigrid levels)
+  double deform_amp = 0.0;
+  int deform_kind = 0;
+  MgData* mg = nullptr;                // multigrid preconditioner, built on first use
   cudaStream_t stream = nullptr;       // internal work stream (never the legacy stream)
   cudaStream_t user_stream = nullptr;  // stream given to sem_setup
   bool own_stream = false;
@@ -81,12 +87,13 @@ struct Handle {
   int ax_variant = 0;          // launch variant of the staged FP32 operator (plain / PCG mode)
   int ax_variant_pcg = 0;
   float ax_tune_ms[2][4] = {};  // autotuner timings [plain, PCG][variant]
-  bool l2_persist = true;      // mixed solve: keep w resident in L2 (access-policy window)
+  bool l2_persist = false;     // mixed solve: keep w resident in L2 (access-policy window)
   bool l2_hints = false;       // PCG kernels: per-access L2 eviction priorities keep w resident
   int64_t l2_window_bytes = 0;     // window of the last mixed solve (0: none set)
   int64_t l2_max_persist = 0, l2_max_window = 0;   // device limits read then
   int gs_acc = 2;              // mixed-path accumulation: 2 TwoSum (default), 0 FP64, 1 FP32
-  bool fuse_gs = true;         // FP32 PCG on box meshes: summation folded into the update
+  int fuse_gs = 1;             // FP32 PCG on box meshes: summation folded into the update
+                               // (1: n a multiple of 4, 2: every n, 0: never)
   int upd_gs_occ[4] = {};      // resident blocks per SM of the fused update kernels (0: not yet read)
 
   // Jacobi

@@ -266,8 +266,21 @@ struct L2Window {
   }
 };
 
+int pcg_mg_solve(Handle& h, const double* f, const double* x0, double* x, double tol, int maxit,
+                 sem_precision prec, double inner_floor, int max_cycles, sem_info* info);
+
 int pcg_solve(Handle& h, const double* f, const double* x0, double* x, const sem_solve_opts& o,
               sem_info* info) {
+  if (o.precond == 2) {
+    // multigrid-preconditioned CG (FP64, or mixed with FP64 restarts)
+    if (o.precision != SEM_FP64 && o.precision != SEM_MIXED_FP32) {
+      set_error("pcg: the multigrid preconditioner supports SEM_FP64 and SEM_MIXED_FP32");
+      return SEM_EINVAL;
+    }
+    return pcg_mg_solve(h, f, x0, x, o.tol > 0 ? o.tol : 1e-8, o.maxit > 0 ? o.maxit : 1000,
+                        o.precision, o.inner_tol > 0 ? o.inner_tol : 1e-4,
+                        o.max_cycles > 0 ? o.max_cycles : 20, info);
+  }
   const double tol = o.tol > 0 ? o.tol : 1e-8;
   const int maxit = o.maxit > 0 ? o.maxit : 1000;
   const int fixed = o.fixed_iters > 0 ? o.fixed_iters : 0;

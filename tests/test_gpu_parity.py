@@ -337,11 +337,12 @@ def test_fused_gather_scatter_is_bitwise(sem, dims, N):
     sem.sem_rhs(S.h, sem.RHS_UNIFORM, 5, b)
     assert sem.sem_get_option(S.h, "fuse_gs") == 1
     cases = [(sem.SEM_MIXED_FP32, acc, {}) for acc in (2, 0, 1)]
+    fused = 2   # fold the summation for every n (default: n a multiple of 4)
     cases.append((sem.SEM_FP32_ALL, 2, {"fixed_iters": 40}))
     for prec, acc, kw in cases:
         sem.sem_set_option(S.h, "gs_acc", acc)
         out = []
-        for fuse in (1, 0):
+        for fuse in (fused, 0):
             sem.sem_set_option(S.h, "fuse_gs", fuse)
             if kw:
                 x, info = S.solve(b, precision=prec, **kw)
