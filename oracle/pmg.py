@@ -239,6 +239,8 @@ class PMG:
         power iteration from a SplitMix64 vector, Rayleigh quotient in A."""
         P = lev.P
         x = P.mask * splitmix_uniform(seed, P.gid)
+        if P.glsc3(x, x) == 0.0:
+            return 1.0          # a level without interior nodes: nothing to damp
         lam = 0.0
         for _ in range(iters):
             y = lev.schwarz(P.ax(x))

@@ -691,6 +691,8 @@ static int level_omega(MgData& mg, MgLevel& v, int iters, uint64_t seed) {
   double* ay = v.w64;
   if ((rc = launch_rhs(h, 1, seed, x))) return rc;
   v.omega = 1.0;
+  if ((rc = launch_glsc3(h, SEM_FP64, x, x, mg.dot))) return rc;
+  if (read_dot(h, mg) == 0.0) return 0;   // a level without interior nodes: nothing to damp
   double lam = 1.0;
   for (int it = 0; it < iters; ++it) {
     if ((rc = mg_apply_a<double>(v, x, ax))) return rc;

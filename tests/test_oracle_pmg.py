@@ -141,6 +141,17 @@ def test_damping_against_dense_spectrum():
     assert 0.95 * lam <= est <= lam * (1 + 1e-10)
 
 
+def test_level_without_interior_nodes():
+    """ky = 1 leaves the N = 1 level without interior nodes: its smoother is
+    the zero map, omega is 1, and the cycle still converges."""
+    M = pmg.PMG(2, 1, 3, 2, deform=False)
+    assert M.levels[-1].P.mask.sum() == 0 and M.levels[-1].omega == 1.0
+    P = M.levels[0].P
+    b = P.rhs_uniform(1)
+    x, it, _ = M.pcg(b, tol=1e-10, maxit=100)
+    assert P.true_relres(b, x) <= 1e-9
+
+
 def test_mg_pcg_solution_equals_dense_solve():
     kx = ky = kz = 2
     N = 3
