@@ -257,6 +257,48 @@ def order_sweep_leg(sem, torch, hbm_gbs):
     return out
 
 
+def mg_leg(sem, torch, S, b, stream):
+    """Multigrid-preconditioned solves of the benchmark problem (FP64 and
+    mixed, to the same tolerance), the set-up time of the levels and the
+    device time of one V-cycle in each precision."""
+    out = {}
+    with torch.cuda.stream(stream):
+        x = torch.empty_like(b)
+        r = b.clone()
+        z = torch.empty_like(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sem.sem_mg_apply(S.h, r, z, sem.SEM_FP64)          # builds the levels
+    torch.cuda.synchronize()
+    out["setup_s"] = time.perf_counter() - t0
+    levels = int(sem.sem_get_option(S.h, "mg_levels"))
+    out["levels"] = levels
+    out["omega"] = [sem.sem_get_option(S.h, f"mg_omega_{l}") for l in range(levels)]
+    for name, prec, dt in (("fp64", sem.SEM_FP64, torch.float64),
+                           ("mixed", sem.SEM_MIXED_FP32, torch.float32)):
+        with torch.cuda.stream(stream):
+            rr = r.to(dt)
+            zz = torch.empty_like(rr)
+        sem.sem_mg_apply(S.h, rr, zz, prec)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            sem.sem_mg_apply(S.h, rr, zz, prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(2):
+            _, inf = S.solve(b, tol=WORKLOAD["tol"], maxit=2000, precision=prec, x=x, precond="mg")
+            if best is None or inf["solve_ms"] < best["solve_ms"]:
+                best = inf
+        out[name] = {"vcycle_ms": e0.elapsed_time(e1) / 5, "solve_ms": best["solve_ms"],
+                     "iterations": best["iters"], "restarts": best["refinements"],
+                     "relres_true": best["relres_true"], "converged": best["rc"] == 0}
+    return out
+
+
 def learned_leg(sem, torch, train_pairs=128, epochs=20):
     """Deformed 16^3 elements, N = 7, random Fourier right-hand sides: train
     the element network on pairs solved by the mixed solver, then compare
@@ -329,6 +371,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the order sweep N = 5..15")
+    ap.add_argument("--no-mg", action="store_true", help="skip the multigrid-preconditioner leg")
     ap.add_argument("--profile", action="store_true",
                     help="small run for ncu captures: 3 fixed mixed iterations + 2 FP32 operator calls")
     ap.add_argument("--profile-k", type=int, default=0,
@@ -594,6 +637,8 @@ def main():
                           "ax_tune_ms_pcg_2", "l2_window_bytes", "l2_max_persist", "l2_max_window")},
             "gpu_launches": launches,
         }
+        if not args.no_mg:
+            line["multigrid"] = mg_leg(sem, torch, S, b, stream)
         if not args.no_batched:
             line["batched"] = batched_leg(sem, torch)
         if not args.no_learned:
