@@ -275,84 +275,154 @@ __global__ void mg_weights_kernel(int N, int kx, int ky, int kz, int64_t L,
 
 // Block solve: gather the weighted residual on every element's extended
 // block, apply S^T along each direction, divide by lam_x + lam_y + lam_z,
-// apply S, write the block (inactive points zero).  One CTA per element.
-template <typename T>
-__global__ void __launch_bounds__(256)
-    mg_block_solve_kernel(int N, int kx, int ky, int64_t E, const T* __restrict__ r,
-                          const T* __restrict__ wsq, const T* __restrict__ S,
-                          const T* __restrict__ lam, const uint8_t* __restrict__ act,
-                          T* __restrict__ ext) {
+// apply S, write the block (inactive points zero).
+// The same block solve with the order fixed at compile time: rows held in
+// registers, contractions unrolled, EPB elements per CTA at low order.
+template <int N>
+struct MgShape {
+  static constexpr int n = N + 1, m = n + 2, m2 = m * m, m3 = m2 * m, n3 = n * n * n;
+  static constexpr int NT = 128;
+  static constexpr int EPB = (NT / m2) > 0 ? (NT / m2) : 1;
+};
+
+template <typename T, int N>
+constexpr size_t mg_block_smem() {
+  using Sh = MgShape<N>;
+  return sizeof(T) * ((size_t)Sh::EPB * (Sh::m3 + 3 * Sh::m2 + 3 * Sh::m)) + 3 * Sh::EPB * Sh::m + 16;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(MgShape<N>::NT)
+    mg_block_solve_t(int kx, int ky, int64_t E, const T* __restrict__ r, const T* __restrict__ wsq,
+                     const T* __restrict__ S, const T* __restrict__ lam,
+                     const uint8_t* __restrict__ act, T* __restrict__ ext) {
+  using Sh = MgShape<N>;
+  constexpr int n = Sh::n, m = Sh::m, m2 = Sh::m2, m3 = Sh::m3, n3 = Sh::n3, EPB = Sh::EPB;
   extern __shared__ __align__(16) unsigned char mg_smem[];
-  const int n = N + 1, m = n + 2, m2 = m * m, m3 = m2 * m, n3 = n * n * n;
-  T* buf = reinterpret_cast<T*>(mg_smem);
-  T* sS = buf + m3;          // 3 * m2
-  T* sl = sS + 3 * m2;       // 3 * m
-  uint8_t* sa = reinterpret_cast<uint8_t*>(sl + 3 * m);   // 3 * m
+  T* buf = reinterpret_cast<T*>(mg_smem);   // [EPB][m3]
+  T* sS = buf + EPB * m3;                     // [EPB][3][m2]
+  T* sl = sS + EPB * 3 * m2;                  // [EPB][3][m]
+  uint8_t* sa = reinterpret_cast<uint8_t*>(sl + EPB * 3 * m);   // [EPB][3][m]
   const int64_t kxky = (int64_t)kx * ky;
-  for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
-    for (int q = threadIdx.x; q < 3 * m2; q += blockDim.x) {
-      const int d = q / m2, o = q - d * m2;
-      sS[q] = S[(d * E + e) * m2 + o];
+  const int64_t ngroups = (E + EPB - 1) / EPB;
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const int64_t e0 = g * EPB;
+    for (int q = threadIdx.x; q < EPB * 3 * m2; q += blockDim.x) {
+      const int le = q / (3 * m2), o = q - le * 3 * m2, d = o / m2, oo = o - d * m2;
+      const int64_t e = e0 + le;
+      sS[q] = e < E ? S[(d * E + e) * m2 + oo] : T(0);
     }
-    for (int q = threadIdx.x; q < 3 * m; q += blockDim.x) {
-      const int d = q / m, o = q - d * m;
-      sl[q] = lam[(d * E + e) * m + o];
-      sa[q] = act[(d * E + e) * m + o];
+    for (int q = threadIdx.x; q < EPB * 3 * m; q += blockDim.x) {
+      const int le = q / (3 * m), o = q - le * 3 * m, d = o / m, oo = o - d * m;
+      const int64_t e = e0 + le;
+      sl[q] = e < E ? lam[(d * E + e) * m + oo] : T(1);
+      sa[q] = e < E ? act[(d * E + e) * m + oo] : 0;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-      const int a = q % m, b = (q / m) % m, c = q / m2;
+    for (int q = threadIdx.x; q < EPB * m3; q += blockDim.x) {
+      const int le = q / m3, p = q - le * m3;
+      const int a = p % m, b = (p / m) % m, c = p / m2;
+      const uint8_t* A = sa + le * 3 * m;
       T v = T(0);
-      if (sa[a] && sa[m + b] && sa[2 * m + c]) {
+      if (A[a] && A[m + b] && A[2 * m + c]) {
         const int dx = a == 0 ? -1 : (a == m - 1 ? 1 : 0);
         const int dy = b == 0 ? -1 : (b == m - 1 ? 1 : 0);
         const int dz = c == 0 ? -1 : (c == m - 1 ? 1 : 0);
         const int i = a == 0 ? N - 1 : (a == m - 1 ? 1 : a - 1);
         const int j = b == 0 ? N - 1 : (b == m - 1 ? 1 : b - 1);
         const int k = c == 0 ? N - 1 : (c == m - 1 ? 1 : c - 1);
-        const int64_t ee = e + dx + (int64_t)dy * kx + (int64_t)dz * kxky;
+        const int64_t ee = e0 + le + dx + (int64_t)dy * kx + (int64_t)dz * kxky;
         const int64_t l = ee * n3 + i + n * (j + n * k);
         v = r[l] * wsq[l];
       }
       buf[q] = v;
     }
     __syncthreads();
-    // forward: S^T along x (rows of fixed b, c), then y, then z
+#pragma unroll 1
     for (int pass = 0; pass < 6; ++pass) {
       const int d = pass % 3;
       const bool fwd = pass < 3;
-      const T* Sd = sS + d * m2;
-      for (int row = threadIdx.x; row < m2; row += blockDim.x) {
-        const int u = row % m, v2 = row / m;
+      for (int row = threadIdx.x; row < EPB * m2; row += blockDim.x) {
+        const int le = row / m2, rr = row - le * m2;
+        const int u = rr % m, v2 = rr / m;
         int base, step;
-        if (d == 0) { base = u * m + v2 * m2; step = 1; }          // (b, c) = (u, v2)
-        else if (d == 1) { base = u + v2 * m2; step = m; }         // (a, c)
-        else { base = u + v2 * m; step = m2; }                     // (a, b)
-        T in[kMgMaxM];
-        for (int t = 0; t < m; ++t) in[t] = buf[base + t * step];
-        for (int o = 0; o < m; ++o) {
-          T s = T(0);
-          if (fwd)
-            for (int t = 0; t < m; ++t) s += Sd[t * m + o] * in[t];   // (S^T in)_o
-          else
-            for (int t = 0; t < m; ++t) s += Sd[o * m + t] * in[t];   // (S in)_o
-          buf[base + o * step] = s;
+        if (d == 0) { base = u * m + v2 * m2; step = 1; }
+        else if (d == 1) { base = u + v2 * m2; step = m; }
+        else { base = u + v2 * m; step = m2; }
+        T* bl = buf + le * m3 + base;
+        const T* Sd = sS + le * 3 * m2 + d * m2;
+        T in[m];
+#pragma unroll
+        for (int t = 0; t < m; ++t) in[t] = bl[t * step];
+        if (fwd) {
+#pragma unroll
+          for (int o = 0; o < m; ++o) {
+            T acc = T(0);
+#pragma unroll
+            for (int t = 0; t < m; ++t) acc += Sd[t * m + o] * in[t];
+            bl[o * step] = acc;
+          }
+        } else {
+#pragma unroll
+          for (int o = 0; o < m; ++o) {
+            T acc = T(0);
+#pragma unroll
+            for (int t = 0; t < m; ++t) acc += Sd[o * m + t] * in[t];
+            bl[o * step] = acc;
+          }
         }
       }
       __syncthreads();
       if (pass == 2) {
-        for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-          const int a = q % m, b = (q / m) % m, c = q / m2;
-          buf[q] = buf[q] / (sl[a] + sl[m + b] + sl[2 * m + c]);
+        for (int q = threadIdx.x; q < EPB * m3; q += blockDim.x) {
+          const int le = q / m3, p = q - le * m3;
+          const int a = p % m, b = (p / m) % m, c = p / m2;
+          const T* L = sl + le * 3 * m;
+          buf[q] = buf[q] / (L[a] + L[m + b] + L[2 * m + c]);
         }
         __syncthreads();
       }
     }
-    for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-      const int a = q % m, b = (q / m) % m, c = q / m2;
-      ext[e * m3 + q] = (sa[a] && sa[m + b] && sa[2 * m + c]) ? buf[q] : T(0);
+    for (int q = threadIdx.x; q < EPB * m3; q += blockDim.x) {
+      const int le = q / m3, p = q - le * m3;
+      const int a = p % m, b = (p / m) % m, c = p / m2;
+      const uint8_t* A = sa + le * 3 * m;
+      const int64_t e = e0 + le;
+      if (e < E) ext[e * m3 + p] = (A[a] && A[m + b] && A[2 * m + c]) ? buf[q] : T(0);
     }
     __syncthreads();
+  }
+}
+
+template <typename T, int N>
+static int mg_block_solve_launch(Handle& h, const T* r, const T* wsq, const T* S, const T* lam,
+                                 const uint8_t* act, T* ext) {
+  using Sh = MgShape<N>;
+  auto k = mg_block_solve_t<T, N>;
+  constexpr size_t smem = mg_block_smem<T, N>();
+  SEM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Sh::NT, smem));
+  const int64_t groups = (h.E + Sh::EPB - 1) / Sh::EPB;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)h.num_sms * std::max(per_sm, 1)));
+  k<<<grid, Sh::NT, smem, h.stream>>>(h.kx, h.ky, h.E, r, wsq, S, lam, act, ext);
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+template <typename T>
+static int mg_block_solve_dispatch(Handle& h, const T* r, const T* wsq, const T* S, const T* lam,
+                                   const uint8_t* act, T* ext) {
+  switch (h.N) {
+#define SEM_MG_N(NN) \
+  case NN: return mg_block_solve_launch<T, NN>(h, r, wsq, S, lam, act, ext);
+    SEM_MG_N(1) SEM_MG_N(2) SEM_MG_N(3) SEM_MG_N(4) SEM_MG_N(5) SEM_MG_N(6) SEM_MG_N(7)
+    SEM_MG_N(8) SEM_MG_N(9) SEM_MG_N(10) SEM_MG_N(11) SEM_MG_N(12) SEM_MG_N(13) SEM_MG_N(14)
+    SEM_MG_N(15)
+#undef SEM_MG_N
+    default:
+      set_error("multigrid: order out of range");
+      return SEM_EINVAL;
   }
 }
 
@@ -505,23 +575,14 @@ struct MgPrec<float> {
   static const float* J(MgLevel& v) { return v.J32; }
 };
 
-static size_t block_solve_smem(int m, size_t tsz) {
-  return tsz * ((size_t)m * m * m + 3 * (size_t)m * m + 3 * m) + 3 * m + 16;
-}
-
 // z = (acc ? z : 0) + omega * Schwarz(r) on level lv
 template <typename T>
 static int mg_schwarz(MgLevel& lv, const T* r, T* z, bool accumulate) {
   Handle& h = *lv.h;
   using P = MgPrec<T>;
-  const int m = lv.m;
-  const size_t smem = block_solve_smem(m, sizeof(T));
-  auto k1 = mg_block_solve_kernel<T>;
-  SEM_CUDA(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int g1 = (int)std::min<int64_t>(h.E, (int64_t)h.num_sms * 8);
-  k1<<<g1, 128, smem, h.stream>>>(lv.N, h.kx, h.ky, h.E, r, P::wsq(lv), P::S(lv), P::lam(lv),
-                                  lv.act, P::ext(lv));
-  SEM_CUDA(cudaGetLastError());
+  int rc;
+  if ((rc = mg_block_solve_dispatch<T>(h, r, P::wsq(lv), P::S(lv), P::lam(lv), lv.act, P::ext(lv))))
+    return rc;
   const int acc = accumulate ? 1 : 0;
   if (sizeof(T) == 8)
     mg_block_sum_kernel<double, kGsFP64><<<grid_of(h, h.L), 256, 0, h.stream>>>(
