@@ -288,7 +288,7 @@ struct MgShape {
 template <typename T, int N>
 constexpr size_t mg_block_smem() {
   using Sh = MgShape<N>;
-  return sizeof(T) * ((size_t)Sh::EPB * (Sh::m3 + 3 * Sh::m2 + 3 * Sh::m)) + 3 * Sh::EPB * Sh::m + 16;
+  return sizeof(T) * ((size_t)Sh::EPB * (Sh::m3 + 6 * Sh::m2 + 3 * Sh::m)) + 3 * Sh::EPB * Sh::m + 16;
 }
 
 template <typename T, int N>
@@ -300,8 +300,9 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
   constexpr int n = Sh::n, m = Sh::m, m2 = Sh::m2, m3 = Sh::m3, n3 = Sh::n3, EPB = Sh::EPB;
   extern __shared__ __align__(16) unsigned char mg_smem[];
   T* buf = reinterpret_cast<T*>(mg_smem);   // [EPB][m3]
-  T* sS = buf + EPB * m3;                     // [EPB][3][m2]
-  T* sl = sS + EPB * 3 * m2;                  // [EPB][3][m]
+  T* sS = buf + EPB * m3;                     // [EPB][3][m2]: S_d(a, b) at a*m + b
+  T* sT = sS + EPB * 3 * m2;                  // [EPB][3][m2]: S_d(b, a) at a*m + b
+  T* sl = sT + EPB * 3 * m2;                  // [EPB][3][m]
   uint8_t* sa = reinterpret_cast<uint8_t*>(sl + EPB * 3 * m);   // [EPB][3][m]
   const int64_t kxky = (int64_t)kx * ky;
   const int64_t ngroups = (E + EPB - 1) / EPB;
@@ -310,7 +311,9 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
     for (int q = threadIdx.x; q < EPB * 3 * m2; q += blockDim.x) {
       const int le = q / (3 * m2), o = q - le * 3 * m2, d = o / m2, oo = o - d * m2;
       const int64_t e = e0 + le;
-      sS[q] = e < E ? S[(d * E + e) * m2 + oo] : T(0);
+      const T v = e < E ? S[(d * E + e) * m2 + oo] : T(0);
+      sS[q] = v;
+      sT[le * 3 * m2 + d * m2 + (oo % m) * m + oo / m] = v;
     }
     for (int q = threadIdx.x; q < EPB * 3 * m; q += blockDim.x) {
       const int le = q / (3 * m), o = q - le * 3 * m, d = o / m, oo = o - d * m;
@@ -350,26 +353,17 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
         else if (d == 1) { base = u + v2 * m2; step = m; }
         else { base = u + v2 * m; step = m2; }
         T* bl = buf + le * m3 + base;
-        const T* Sd = sS + le * 3 * m2 + d * m2;
+        // row o of S^T (forward) or of S (backward): contiguous in shared memory
+        const T* Md = (fwd ? sT : sS) + le * 3 * m2 + d * m2;
         T in[m];
 #pragma unroll
         for (int t = 0; t < m; ++t) in[t] = bl[t * step];
-        if (fwd) {
 #pragma unroll
-          for (int o = 0; o < m; ++o) {
-            T acc = T(0);
+        for (int o = 0; o < m; ++o) {
+          T acc = T(0);
 #pragma unroll
-            for (int t = 0; t < m; ++t) acc += Sd[t * m + o] * in[t];
-            bl[o * step] = acc;
-          }
-        } else {
-#pragma unroll
-          for (int o = 0; o < m; ++o) {
-            T acc = T(0);
-#pragma unroll
-            for (int t = 0; t < m; ++t) acc += Sd[o * m + t] * in[t];
-            bl[o * step] = acc;
-          }
+          for (int t = 0; t < m; ++t) acc += Md[o * m + t] * in[t];
+          bl[o * step] = acc;
         }
       }
       __syncthreads();
@@ -426,101 +420,157 @@ static int mg_block_solve_dispatch(Handle& h, const T* r, const T* wsq, const T*
   }
 }
 
-// z = (acc ? z : 0) + omega * wsq * mask * sum of the blocks holding the node
-// (ascending element order: the same bits on every copy).
-template <typename T, int ACC>
-__global__ void mg_block_sum_kernel(int N, int kx, int ky, int kz, int64_t L,
-                                    const T* __restrict__ ext, const uint8_t* __restrict__ act,
-                                    const T* __restrict__ wsq, const double* __restrict__ mask,
-                                    T omega, int accumulate, T* __restrict__ z) {
-  const int n = N + 1, n3 = n * n * n, m = n + 2, m2 = m * m, m3 = m2 * m;
-  const int64_t E = (int64_t)kx * ky * kz;
+// Blocks holding node g (0..N) of an element along one direction, from the
+// element's face bits (lo/hi: the face on that side lies on the domain
+// boundary): the lower neighbour's block at extended index n (g = 0) or n+1
+// (g = 1, N >= 2), the element's own at g+1 (unless g is a boundary-face
+// node), the upper neighbour's at 0 (g = N-1, N >= 2) or 1 (g = N); listed
+// in ascending element order (offsets -1, 0, +1).
+template <int N>
+struct MgCand1 {
+  int cnt;
+  int off[3];
+  int ext[3];
+};
+
+template <int N>
+__device__ __forceinline__ MgCand1<N> mg_cand1(int g, bool lo_bnd, bool hi_bnd) {
+  constexpr int n = N + 1;
+  MgCand1<N> c;
+  c.cnt = 0;
+  if (!lo_bnd && g == 0) { c.off[c.cnt] = -1; c.ext[c.cnt++] = n; }
+  if (!lo_bnd && N >= 2 && g == 1) { c.off[c.cnt] = -1; c.ext[c.cnt++] = n + 1; }
+  if (!((g == 0 && lo_bnd) || (g == N && hi_bnd))) { c.off[c.cnt] = 0; c.ext[c.cnt++] = g + 1; }
+  if (!hi_bnd && N >= 2 && g == N - 1) { c.off[c.cnt] = 1; c.ext[c.cnt++] = 0; }
+  if (!hi_bnd && g == N) { c.off[c.cnt] = 1; c.ext[c.cnt++] = 1; }
+  return c;
+}
+
+// Block sum with the order fixed at compile time; cw: multiplicity code
+// (0 on the Dirichlet boundary).
+template <typename T, int ACC, int N>
+__global__ void __launch_bounds__(256)
+    mg_block_sum_t(int kx, int ky, int64_t L, const T* __restrict__ ext,
+                   const uint8_t* __restrict__ faces, const T* __restrict__ wsq,
+                   const uint8_t* __restrict__ cw, T omega, int accumulate, T* __restrict__ z) {
+  constexpr int n = N + 1, n3 = n * n * n, m = n + 2, m2 = m * m, m3 = m2 * m;
   const int64_t kxky = (int64_t)kx * ky;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
        l += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = l / n3;
-    const int rem = (int)(l - e * n3);
-    const int i = rem % n, j = (rem / n) % n, k = rem / (n * n);
-    const int ex = (int)(e % kx), ey = (int)((e / kx) % ky), ez = (int)(e / kxky);
-    const int64_t ex0 = e - ex, ey0 = e - (int64_t)ey * kx, ez0 = e - (int64_t)ez * kxky;
-    const MgCand cx = mg_candidates(ex, i, N, kx, E, ex0, 1, act);
-    const MgCand cy = mg_candidates(ey, j, N, ky, E, ey0, kx, act + E * m);
-    const MgCand cz = mg_candidates(ez, k, N, kz, E, ez0, kxky, act + 2 * E * m);
-    GsSum<T, ACC> acc;
-    for (int c = 0; c < cz.cnt; ++c)
-      for (int b = 0; b < cy.cnt; ++b)
-        for (int a = 0; a < cx.cnt; ++a) {
-          const int64_t eb = cx.elem[a] + (int64_t)cy.elem[b] * kx + (int64_t)cz.elem[c] * kxky;
-          acc.add(ext[eb * m3 + cx.ext[a] + m * cy.ext[b] + m2 * cz.ext[c]]);
-        }
-    T v = (cx.cnt && cy.cnt && cz.cnt) ? acc.result() : T(0);
-    v = omega * (wsq[l] * ((T)mask[l] * v));
+    T v = T(0);
+    if (cw[l]) {
+      const int64_t e = l / n3;
+      const int rem = (int)(l - e * n3);
+      const int i = rem % n, j = (rem / n) % n, k = rem / (n * n);
+      const uint8_t f = __ldg(faces + e);
+      const MgCand1<N> cx = mg_cand1<N>(i, f & 1, f & 2);
+      const MgCand1<N> cy = mg_cand1<N>(j, f & 4, f & 8);
+      const MgCand1<N> cz = mg_cand1<N>(k, f & 16, f & 32);
+      GsSum<T, ACC> acc;
+      for (int c = 0; c < cz.cnt; ++c)
+        for (int b = 0; b < cy.cnt; ++b)
+          for (int a = 0; a < cx.cnt; ++a) {
+            const int64_t eb = e + cx.off[a] + (int64_t)cy.off[b] * kx + (int64_t)cz.off[c] * kxky;
+            acc.add(__ldg(ext + eb * m3 + cx.ext[a] + m * cy.ext[b] + m2 * cz.ext[c]));
+          }
+      v = omega * (wsq[l] * acc.result());
+    }
     z[l] = accumulate ? z[l] + v : v;
   }
 }
 
-// Element-wise tensor contraction out = (M x M x M) in, M: [no][ni].
-// scale (optional): in is multiplied by 1/scale first (restriction);
-// add: out += result (prolongation).
-template <typename T>
+// Transfers with the orders fixed at compile time: fine order NF, coarse
+// order max(1, NF/2).  RESTRICT: out(coarse) = (J^T)^{x3}(in(fine) / m_f)
+// with 1/m_f from the multiplicity code (exact: powers of two; 0 on the
+// Dirichlet boundary, where in is zero); otherwise out(fine) += J^{x3} in(coarse).
+template <typename T, int NF, bool RESTRICT>
 __global__ void __launch_bounds__(256)
-    mg_transfer_kernel(int ni, int no, int64_t E, const T* __restrict__ M, int transpose,
-                       const T* __restrict__ in, const double* __restrict__ div,
-                       T* __restrict__ out, int add) {
+    mg_transfer_t(int64_t E, const T* __restrict__ J, const T* __restrict__ in,
+                  const uint8_t* __restrict__ cw, T* __restrict__ out) {
+  constexpr int NC = NF / 2 > 1 ? NF / 2 : 1;
+  constexpr int nf = NF + 1, nc = NC + 1;
+  constexpr int ni = RESTRICT ? nf : nc, no = RESTRICT ? nc : nf;
+  constexpr int ni3 = ni * ni * ni, no3 = no * no * no;
   extern __shared__ __align__(16) unsigned char mg_smem[];
-  const int nmax = ni > no ? ni : no;
-  const int nb = nmax * nmax * nmax;
-  T* b0 = reinterpret_cast<T*>(mg_smem);
-  T* b1 = b0 + nb;
-  T* sM = b1 + nb;
-  const int ni3 = ni * ni * ni, no3 = no * no * no;
+  T* b0 = reinterpret_cast<T*>(mg_smem);   // nf^3
+  T* b1 = b0 + nf * nf * nf;               // nf^3
+  T* sM = b1 + nf * nf * nf;               // ni * no
   for (int q = threadIdx.x; q < ni * no; q += blockDim.x) {
-    // sM[o * ni + t] = M(o, t): rows out, cols in
-    const int o = q / ni, t = q - o * ni;
-    sM[q] = transpose ? M[t * no + o] : M[o * ni + t];
+    const int o = q / ni, t = q - o * ni;   // sM[o][t] = M(o, t)
+    sM[q] = RESTRICT ? J[t * nc + o] : J[o * nc + t];
   }
   for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
     __syncthreads();
     for (int q = threadIdx.x; q < ni3; q += blockDim.x) {
       T v = in[e * ni3 + q];
-      if (div) v = v / (T)div[e * ni3 + q];
+      if (RESTRICT) {
+        const uint8_t m = cw[e * ni3 + q];
+        v = m ? v * (T(1) / T(m)) : T(0);
+      }
       b0[q] = v;
     }
     __syncthreads();
-    // along i: [ni][ni][ni] -> [ni][ni][no]
     for (int q = threadIdx.x; q < ni * ni * no; q += blockDim.x) {
       const int o = q % no, jk = q / no;
       T s = T(0);
+#pragma unroll
       for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * b0[jk * ni + t];
       b1[q] = s;
     }
     __syncthreads();
-    // along j: [ni(k)][ni(j)][no(i)] -> [ni][no][no]
     for (int q = threadIdx.x; q < ni * no * no; q += blockDim.x) {
       const int i = q % no, o = (q / no) % no, k = q / (no * no);
       T s = T(0);
+#pragma unroll
       for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * b1[(k * ni + t) * no + i];
       b0[q] = s;
     }
     __syncthreads();
-    // along k: [ni][no][no] -> [no][no][no]
     for (int q = threadIdx.x; q < no3; q += blockDim.x) {
       const int ij = q % (no * no), o = q / (no * no);
       T s = T(0);
+#pragma unroll
       for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * b0[t * no * no + ij];
-      if (add) out[e * no3 + q] += s;
-      else out[e * no3 + q] = s;
+      if (RESTRICT) out[e * no3 + q] = s;
+      else out[e * no3 + q] += s;
     }
   }
 }
 
-// t = r - mask * w
+template <typename T, bool RESTRICT>
+static int mg_transfer_t_launch(Handle& h, int NF, const T* J, const T* in, const uint8_t* cw,
+                                T* out) {
+  const int g = (int)std::min<int64_t>(h.E, (int64_t)h.num_sms * 8);
+  switch (NF) {
+#define SEM_MG_TR(NN)                                                                      \
+  case NN: {                                                                               \
+    constexpr int nf = NN + 1, nc = (NN / 2 > 1 ? NN / 2 : 1) + 1;                         \
+    constexpr size_t smem = sizeof(T) * (2 * (size_t)nf * nf * nf + (size_t)nf * nc);      \
+    auto k = mg_transfer_t<T, NN, RESTRICT>;                                               \
+    SEM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k<<<g, 256, smem, h.stream>>>(h.E, J, in, cw, out);                                    \
+    break;                                                                                 \
+  }
+    SEM_MG_TR(2) SEM_MG_TR(3) SEM_MG_TR(4) SEM_MG_TR(5) SEM_MG_TR(6) SEM_MG_TR(7) SEM_MG_TR(8)
+    SEM_MG_TR(9) SEM_MG_TR(10) SEM_MG_TR(11) SEM_MG_TR(12) SEM_MG_TR(13) SEM_MG_TR(14)
+    SEM_MG_TR(15)
+#undef SEM_MG_TR
+    default:
+      set_error("multigrid: order out of range");
+      return SEM_EINVAL;
+  }
+  ++h.launches;
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// t = r - w (r and w masked)
 template <typename T>
 __global__ void mg_residual_kernel(int64_t L, const T* __restrict__ r, const T* __restrict__ w,
-                                   const double* __restrict__ mask, T* __restrict__ t) {
+                                   T* __restrict__ t) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
        l += (int64_t)gridDim.x * blockDim.x)
-    t[l] = r[l] - (T)mask[l] * w[l];
+    t[l] = r[l] - w[l];
 }
 
 template <typename T>
@@ -584,14 +634,27 @@ static int mg_schwarz(MgLevel& lv, const T* r, T* z, bool accumulate) {
   if ((rc = mg_block_solve_dispatch<T>(h, r, P::wsq(lv), P::S(lv), P::lam(lv), lv.act, P::ext(lv))))
     return rc;
   const int acc = accumulate ? 1 : 0;
-  if (sizeof(T) == 8)
-    mg_block_sum_kernel<double, kGsFP64><<<grid_of(h, h.L), 256, 0, h.stream>>>(
-        lv.N, h.kx, h.ky, h.kz, h.L, (const double*)P::ext(lv), lv.act, (const double*)P::wsq(lv),
-        h.mask64, lv.omega, acc, (double*)z);
-  else
-    mg_block_sum_kernel<float, kGsTwoSum><<<grid_of(h, h.L), 256, 0, h.stream>>>(
-        lv.N, h.kx, h.ky, h.kz, h.L, (const float*)P::ext(lv), lv.act, (const float*)P::wsq(lv),
-        h.mask64, (float)lv.omega, acc, (float*)z);
+  const int g = grid_of(h, h.L);
+  switch (h.N) {
+#define SEM_MG_SUM(NN)                                                                            \
+  case NN:                                                                                        \
+    if (sizeof(T) == 8)                                                                           \
+      mg_block_sum_t<double, kGsFP64, NN><<<g, 256, 0, h.stream>>>(                               \
+          h.kx, h.ky, h.L, (const double*)P::ext(lv), h.bfaces, (const double*)P::wsq(lv), h.cw8, \
+          lv.omega, acc, (double*)z);                                                             \
+    else                                                                                          \
+      mg_block_sum_t<float, kGsTwoSum, NN><<<g, 256, 0, h.stream>>>(                              \
+          h.kx, h.ky, h.L, (const float*)P::ext(lv), h.bfaces, (const float*)P::wsq(lv), h.cw8,   \
+          (float)lv.omega, acc, (float*)z);                                                       \
+    break;
+    SEM_MG_SUM(1) SEM_MG_SUM(2) SEM_MG_SUM(3) SEM_MG_SUM(4) SEM_MG_SUM(5) SEM_MG_SUM(6)
+    SEM_MG_SUM(7) SEM_MG_SUM(8) SEM_MG_SUM(9) SEM_MG_SUM(10) SEM_MG_SUM(11) SEM_MG_SUM(12)
+    SEM_MG_SUM(13) SEM_MG_SUM(14) SEM_MG_SUM(15)
+#undef SEM_MG_SUM
+    default:
+      set_error("multigrid: order out of range");
+      return SEM_EINVAL;
+  }
   h.launches += 2;
   SEM_CUDA(cudaGetLastError());
   return 0;
@@ -607,25 +670,9 @@ static int mg_apply_a(MgLevel& lv, const T* u, T* w) {
   } else {
     if ((rc = ax_dispatch_fp32(h, (const float*)u, (float*)w, nullptr, kDotDot2))) return rc;
   }
-  if ((rc = launch_gs(h, MgPrec<T>::p, w))) return rc;
-  mg_mask_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, h.mask64, w);
-  ++h.launches;
-  SEM_CUDA(cudaGetLastError());
-  return 0;
-}
-
-template <typename T>
-static int mg_transfer(Handle& h, int ni, int no, int64_t E, const T* M, bool transpose,
-                       const T* in, const double* div, T* out, bool add) {
-  const int nmax = std::max(ni, no);
-  const size_t smem = sizeof(T) * (2 * (size_t)nmax * nmax * nmax + (size_t)ni * no);
-  auto k = mg_transfer_kernel<T>;
-  SEM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int g = (int)std::min<int64_t>(E, (int64_t)h.num_sms * 8);
-  k<<<g, 256, smem, h.stream>>>(ni, no, E, M, transpose ? 1 : 0, in, div, out, add ? 1 : 0);
-  ++h.launches;
-  SEM_CUDA(cudaGetLastError());
-  return 0;
+  // the operator kernels zero w on the Dirichlet boundary and the summation
+  // keeps those zeros: w is masked
+  return launch_gs(h, MgPrec<T>::p, w);
 }
 
 // z_l = V-cycle(r_l)
@@ -641,21 +688,19 @@ static int mg_vcycle(MgData& mg, int l, const T* r, T* z) {
   Handle& hc = *cv.h;
   T* t = P::t(lv);
   if ((rc = mg_apply_a<T>(lv, z, P::w(lv)))) return rc;
-  mg_residual_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, r, P::w(lv), h.mask64, t);
+  mg_residual_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, r, P::w(lv), t);
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
   // restriction: (J^T)^{x3} (t / mult), then QQ^T and mask on the coarse level
-  if ((rc = mg_transfer<T>(h, lv.n, cv.n, h.E, P::J(lv), true, t, h.mult64, P::r(cv), false)))
-    return rc;
+  if ((rc = mg_transfer_t_launch<T, true>(h, lv.N, P::J(lv), t, h.cw8, P::r(cv)))) return rc;
   if ((rc = launch_gs(hc, P::p, P::r(cv)))) return rc;
   mg_mask_kernel<T><<<grid_of(hc, hc.L), 256, 0, h.stream>>>(hc.L, hc.mask64, P::r(cv));
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
   if ((rc = mg_vcycle<T>(mg, l + 1, P::r(cv), P::z(cv)))) return rc;
-  if ((rc = mg_transfer<T>(h, cv.n, lv.n, h.E, P::J(lv), false, P::z(cv), nullptr, z, true)))
-    return rc;
+  if ((rc = mg_transfer_t_launch<T, false>(h, lv.N, P::J(lv), P::z(cv), nullptr, z))) return rc;
   if ((rc = mg_apply_a<T>(lv, z, P::w(lv)))) return rc;
-  mg_residual_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, r, P::w(lv), h.mask64, t);
+  mg_residual_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, r, P::w(lv), t);
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
   return mg_schwarz<T>(lv, t, z, true);
