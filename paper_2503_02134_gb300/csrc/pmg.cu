@@ -322,23 +322,36 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
       sa[q] = e < E ? act[(d * E + e) * m + oo] : 0;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < EPB * m3; q += blockDim.x) {
-      const int le = q / m3, p = q - le * m3;
-      const int a = p % m, b = (p / m) % m, c = p / m2;
+    // gather by rows along x: extended row (b, c) is the neighbour's node
+    // N-1, the n nodes of the element row (j, k) -- contiguous in memory --
+    // and the next neighbour's node 1
+    for (int row = threadIdx.x; row < EPB * m2; row += blockDim.x) {
+      const int le = row / m2, rr = row - le * m2;
+      const int b = rr % m, c = rr / m;
       const uint8_t* A = sa + le * 3 * m;
-      T v = T(0);
-      if (A[a] && A[m + b] && A[2 * m + c]) {
-        const int dx = a == 0 ? -1 : (a == m - 1 ? 1 : 0);
-        const int dy = b == 0 ? -1 : (b == m - 1 ? 1 : 0);
-        const int dz = c == 0 ? -1 : (c == m - 1 ? 1 : 0);
-        const int i = a == 0 ? N - 1 : (a == m - 1 ? 1 : a - 1);
-        const int j = b == 0 ? N - 1 : (b == m - 1 ? 1 : b - 1);
-        const int k = c == 0 ? N - 1 : (c == m - 1 ? 1 : c - 1);
-        const int64_t ee = e0 + le + dx + (int64_t)dy * kx + (int64_t)dz * kxky;
-        const int64_t l = ee * n3 + i + n * (j + n * k);
-        v = r[l] * wsq[l];
+      T* out = buf + le * m3 + b * m + c * m2;
+      if (!(A[m + b] && A[2 * m + c])) {
+#pragma unroll
+        for (int a = 0; a < m; ++a) out[a] = T(0);
+        continue;
       }
-      buf[q] = v;
+      const int dy = b == 0 ? -1 : (b == m - 1 ? 1 : 0);
+      const int dz = c == 0 ? -1 : (c == m - 1 ? 1 : 0);
+      const int j = b == 0 ? N - 1 : (b == m - 1 ? 1 : b - 1);
+      const int k = c == 0 ? N - 1 : (c == m - 1 ? 1 : c - 1);
+      const int64_t ee = e0 + le + (int64_t)dy * kx + (int64_t)dz * kxky;
+      const int64_t l0 = ee * n3 + n * (j + n * k);     // node (0, j, k) of element ee
+      const T* rp = r + l0;
+      const T* wp = wsq + l0;
+#pragma unroll
+      for (int a = 1; a <= n; ++a)
+        out[a] = A[a] ? rp[a - 1] * wp[a - 1] : T(0);
+      // the x neighbours exist only where their extended index is active
+      T lo = T(0), hi = T(0);
+      if (A[0]) lo = rp[N - 1 - n3] * wp[N - 1 - n3];   // element ee-1, i = N-1
+      if (A[m - 1]) hi = rp[1 + n3] * wp[1 + n3];       // element ee+1, i = 1
+      out[0] = lo;
+      out[m - 1] = hi;
     }
     __syncthreads();
 #pragma unroll 1
@@ -467,12 +480,22 @@ __global__ void __launch_bounds__(256)
       const MgCand1<N> cy = mg_cand1<N>(j, f & 4, f & 8);
       const MgCand1<N> cz = mg_cand1<N>(k, f & 16, f & 32);
       GsSum<T, ACC> acc;
-      for (int c = 0; c < cz.cnt; ++c)
-        for (int b = 0; b < cy.cnt; ++b)
-          for (int a = 0; a < cx.cnt; ++a) {
+      // fully unrolled over the at most 3 x 3 x 3 candidates (the lists stay
+      // in registers); ascending element order
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (c >= cz.cnt) break;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          if (b >= cy.cnt) break;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            if (a >= cx.cnt) break;
             const int64_t eb = e + cx.off[a] + (int64_t)cy.off[b] * kx + (int64_t)cz.off[c] * kxky;
             acc.add(__ldg(ext + eb * m3 + cx.ext[a] + m * cy.ext[b] + m2 * cz.ext[c]));
           }
+        }
+      }
       v = omega * (wsq[l] * acc.result());
     }
     z[l] = accumulate ? z[l] + v : v;
