@@ -130,6 +130,23 @@ def box_coords(kx, ky, kz, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
     return X
 
 
+def box_coords_elements(kx, ky, kz, N, elems, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """Node coordinates X[m, q, k, j, i] of the listed elements of the same
+    box mesh (elems[q] = ex + kx*(ey + ky*ez)), for meshes too large to build
+    whole; the same formula as box_coords."""
+    xi, _ = gll(N)
+    n = N + 1
+    elems = np.asarray(elems, dtype=np.int64)
+    X = np.zeros((3, len(elems), n, n, n))
+    h = [(hi[d] - lo[d]) / k for d, k in enumerate((kx, ky, kz))]
+    for q, e in enumerate(elems):
+        ex, ey, ez = e % kx, (e // kx) % ky, e // (kx * ky)
+        X[0, q] = (lo[0] + (ex + (1.0 + xi) / 2.0) * h[0])[None, None, :]
+        X[1, q] = (lo[1] + (ey + (1.0 + xi) / 2.0) * h[1])[None, :, None]
+        X[2, q] = (lo[2] + (ez + (1.0 + xi) / 2.0) * h[2])[:, None, None]
+    return X
+
+
 def deform_cyclic(X, amp=0.05):
     """x += amp sin(2 pi y) sin(2 pi z), and its cyclic permutations, all
     evaluated from the undeformed coordinates at every GLL node."""

@@ -245,3 +245,9 @@ def test_uniform_rhs_is_per_global_node_and_in_range():
     assert abs(u.mean()) < 0.05
     # every copy of a global node carries the same value
     np.testing.assert_allclose(P.dssum(b) / P.mult, b, rtol=1e-15, atol=1e-16)
+
+
+def test_box_coords_elements_match_whole_mesh():
+    X = so.box_coords(3, 2, 4, 5)
+    elems = [0, 5, 7, 23, 11]
+    np.testing.assert_array_equal(so.box_coords_elements(3, 2, 4, 5, elems), X[:, elems])
