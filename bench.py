@@ -374,6 +374,9 @@ def main():
     ap.add_argument("--no-mg", action="store_true", help="skip the multigrid-preconditioner leg")
     ap.add_argument("--profile", action="store_true",
                     help="small run for ncu captures: 3 fixed mixed iterations + 2 FP32 operator calls")
+    ap.add_argument("--profile-mg", action="store_true",
+                    help="ncu run of the multigrid preconditioner: one FP32 and one FP64 V-cycle "
+                         "on the benchmark mesh inside the NVTX range mg_cycle")
     ap.add_argument("--profile-k", type=int, default=0,
                     help="with --profile: a k^3-element mesh instead of the benchmark's (smaller ncu captures)")
     ap.add_argument("--profile-batched", action="store_true",
@@ -423,7 +426,7 @@ def main():
 
     stream = torch.cuda.Stream()
     W = dict(WORKLOAD)
-    if args.profile and args.profile_k > 0:
+    if (args.profile or args.profile_mg) and args.profile_k > 0:
         W.update(kx=args.profile_k, ky=args.profile_k, kz=args.profile_k)
     S = sem.Solver(W["kx"], W["ky"], W["kz"], W["N"], deform=W["deform"], stream=stream.cuda_stream)
     L = S.L
@@ -436,6 +439,23 @@ def main():
     def step(prec=sem.SEM_MIXED_FP32):
         _, info = S.solve(b, tol=W["tol"], maxit=5000, precision=prec, x=x)
         return info
+
+    if args.profile_mg:
+        with torch.cuda.stream(stream):
+            z = torch.empty_like(b)
+            b32 = b.float()
+            z32 = torch.empty_like(b32)
+        sem.sem_mg_apply(S.h, b, z, sem.SEM_FP64)            # set-up and warm-up
+        sem.sem_mg_apply(S.h, b32, z32, sem.SEM_MIXED_FP32)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("mg_cycle")
+        sem.sem_mg_apply(S.h, b32, z32, sem.SEM_MIXED_FP32)
+        sem.sem_mg_apply(S.h, b, z, sem.SEM_FP64)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        S.close()
+        print(json.dumps({"profile_mg": "ok"}))
+        return 0
 
     if args.profile:
         with torch.cuda.stream(stream):
