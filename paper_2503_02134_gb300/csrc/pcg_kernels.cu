@@ -195,8 +195,8 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
-template <int n, int DM, int ACC>
-__global__ void __launch_bounds__(kVecThreads)
+template <int n, int DM, int ACC, int MINB>
+__global__ void __launch_bounds__(kVecThreads, MINB)
     cg_update32_gs_row4_kernel(float* __restrict__ x, float* __restrict__ r,
                                const float* __restrict__ p, const float* __restrict__ w,
                                const uint8_t* __restrict__ cw, const float* __restrict__ minv,
@@ -516,8 +516,9 @@ static void update_gs_dispatch(Handle& h, float* x, float* r, const float* p, co
   const int64_t kx = h.kx, kxky = (int64_t)h.kx * h.ky;
 #define SEM_UPD_ROW4(NN)                                                                  \
   case NN: {                                                                              \
-    auto kern = cg_update32_gs_row4_kernel<NN, DM, ACC>;                                  \
-    const int grid = fused_grid(h, kern, slot);                                           \
+    auto kern = h.upd_minb == 4 ? cg_update32_gs_row4_kernel<NN, DM, ACC, 4>              \
+                                : cg_update32_gs_row4_kernel<NN, DM, ACC, 1>;             \
+    const int grid = fused_grid(h, kern, slot + (h.upd_minb == 4 ? 4 : 0));               \
     kern<<<grid, kVecThreads, 0, h.stream>>>(x, r, p, w, h.cw8, minv, h.bfaces, kx, kxky, \
                                              h.L, s, h.partials, hist, h.l2_hints ? 1 : 0); \
     return;                                                                               \

@@ -282,7 +282,10 @@ template <int N>
 struct MgShape {
   static constexpr int n = N + 1, m = n + 2, m2 = m * m, m3 = m2 * m, n3 = n * n * n;
   static constexpr int NT = 128;
-  static constexpr int EPB = (NT / m2) > 0 ? (NT / m2) : 1;
+  // rows per thread in the contraction passes: two when a block has an even
+  // number of rows (each matrix entry read from shared memory feeds two FMAs)
+  static constexpr int RPT = m2 % 2 == 0 ? 2 : 1;
+  static constexpr int EPB = (RPT * NT / m2) > 0 ? (RPT * NT / m2) : 1;
 };
 
 template <typename T, int N>
@@ -358,25 +361,42 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
     for (int pass = 0; pass < 6; ++pass) {
       const int d = pass % 3;
       const bool fwd = pass < 3;
-      for (int row = threadIdx.x; row < EPB * m2; row += blockDim.x) {
-        const int le = row / m2, rr = row - le * m2;
-        const int u = rr % m, v2 = rr / m;
-        int base, step;
-        if (d == 0) { base = u * m + v2 * m2; step = 1; }
-        else if (d == 1) { base = u + v2 * m2; step = m; }
-        else { base = u + v2 * m; step = m2; }
-        T* bl = buf + le * m3 + base;
+      constexpr int RPT = Sh::RPT;
+      for (int pr = threadIdx.x; pr < EPB * m2 / RPT; pr += blockDim.x) {
+        const int row0 = pr * RPT;   // RPT consecutive rows of one element
+        const int le = row0 / m2;
+        T* bl[RPT];
+        int step = 1;
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          const int rr = row0 + q - le * m2;
+          const int u = rr % m, v2 = rr / m;
+          int base;
+          if (d == 0) { base = u * m + v2 * m2; step = 1; }
+          else if (d == 1) { base = u + v2 * m2; step = m; }
+          else { base = u + v2 * m; step = m2; }
+          bl[q] = buf + le * m3 + base;
+        }
         // row o of S^T (forward) or of S (backward): contiguous in shared memory
         const T* Md = (fwd ? sT : sS) + le * 3 * m2 + d * m2;
-        T in[m];
+        T in[RPT][m];
 #pragma unroll
-        for (int t = 0; t < m; ++t) in[t] = bl[t * step];
+        for (int q = 0; q < RPT; ++q)
+#pragma unroll
+          for (int t = 0; t < m; ++t) in[q][t] = bl[q][t * step];
 #pragma unroll
         for (int o = 0; o < m; ++o) {
-          T acc = T(0);
+          T acc[RPT];
 #pragma unroll
-          for (int t = 0; t < m; ++t) acc += Md[o * m + t] * in[t];
-          bl[o * step] = acc;
+          for (int q = 0; q < RPT; ++q) acc[q] = T(0);
+#pragma unroll
+          for (int t = 0; t < m; ++t) {
+            const T mv = Md[o * m + t];
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) acc[q] += mv * in[q][t];
+          }
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) bl[q][o * step] = acc[q];
         }
       }
       __syncthreads();
