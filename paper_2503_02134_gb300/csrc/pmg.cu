@@ -479,46 +479,66 @@ __device__ __forceinline__ MgCand1<N> mg_cand1(int g, bool lo_bnd, bool hi_bnd) 
   return c;
 }
 
-// Block sum with the order fixed at compile time; cw: multiplicity code
-// (0 on the Dirichlet boundary).
+// Block sum with the order fixed at compile time.  The node's element
+// coordinates give its boundary flags (a box mesh is Dirichlet on all six
+// faces), so no load precedes the block loads; each thread sums four nodes
+// per trip, whose loads are independent.
+template <typename T, int ACC, int N>
+__device__ __forceinline__ T mg_block_sum_node(int64_t l, int kx, int ky, int kz,
+                                               const T* __restrict__ ext) {
+  constexpr int n = N + 1, n3 = n * n * n, m = n + 2, m2 = m * m, m3 = m2 * m;
+  const int64_t e = l / n3;
+  const int rem = (int)(l - e * n3);
+  const int i = rem % n, j = (rem / n) % n, k = rem / (n * n);
+  const int ex = (int)(e % kx), exy = (int)(e / kx), ey = exy % ky, ez = exy / ky;
+  const bool xl = ex == 0, xh = ex == kx - 1, yl = ey == 0, yh = ey == ky - 1;
+  const bool zl = ez == 0, zh = ez == kz - 1;
+  if ((i == 0 && xl) || (i == N && xh) || (j == 0 && yl) || (j == N && yh) ||
+      (k == 0 && zl) || (k == N && zh))
+    return T(0);                                    // Dirichlet node
+  const int64_t kxky = (int64_t)kx * ky;
+  const MgCand1<N> cx = mg_cand1<N>(i, xl, xh);
+  const MgCand1<N> cy = mg_cand1<N>(j, yl, yh);
+  const MgCand1<N> cz = mg_cand1<N>(k, zl, zh);
+  GsSum<T, ACC> acc;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (c >= cz.cnt) break;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b >= cy.cnt) break;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (a >= cx.cnt) break;
+        const int64_t eb = e + cx.off[a] + (int64_t)cy.off[b] * kx + (int64_t)cz.off[c] * kxky;
+        acc.add(__ldg(ext + eb * m3 + cx.ext[a] + m * cy.ext[b] + m2 * cz.ext[c]));
+      }
+    }
+  }
+  return acc.result();
+}
+
 template <typename T, int ACC, int N>
 __global__ void __launch_bounds__(256)
-    mg_block_sum_t(int kx, int ky, int64_t L, const T* __restrict__ ext,
-                   const uint8_t* __restrict__ faces, const T* __restrict__ wsq,
-                   const uint8_t* __restrict__ cw, T omega, int accumulate, T* __restrict__ z) {
-  constexpr int n = N + 1, n3 = n * n * n, m = n + 2, m2 = m * m, m3 = m2 * m;
-  const int64_t kxky = (int64_t)kx * ky;
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
-       l += (int64_t)gridDim.x * blockDim.x) {
-    T v = T(0);
-    if (cw[l]) {
-      const int64_t e = l / n3;
-      const int rem = (int)(l - e * n3);
-      const int i = rem % n, j = (rem / n) % n, k = rem / (n * n);
-      const uint8_t f = __ldg(faces + e);
-      const MgCand1<N> cx = mg_cand1<N>(i, f & 1, f & 2);
-      const MgCand1<N> cy = mg_cand1<N>(j, f & 4, f & 8);
-      const MgCand1<N> cz = mg_cand1<N>(k, f & 16, f & 32);
-      GsSum<T, ACC> acc;
-      // fully unrolled over the at most 3 x 3 x 3 candidates (the lists stay
-      // in registers); ascending element order
+    mg_block_sum_t(int kx, int ky, int kz, int64_t L, const T* __restrict__ ext,
+                   const T* __restrict__ wsq, T omega, int accumulate, T* __restrict__ z) {
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t l0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l0 < L; l0 += U * stride) {
+    T v[U];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (c >= cz.cnt) break;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          if (b >= cy.cnt) break;
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            if (a >= cx.cnt) break;
-            const int64_t eb = e + cx.off[a] + (int64_t)cy.off[b] * kx + (int64_t)cz.off[c] * kxky;
-            acc.add(__ldg(ext + eb * m3 + cx.ext[a] + m * cy.ext[b] + m2 * cz.ext[c]));
-          }
-        }
-      }
-      v = omega * (wsq[l] * acc.result());
+    for (int u = 0; u < U; ++u) {
+      const int64_t l = l0 + u * stride;
+      v[u] = l < L ? mg_block_sum_node<T, ACC, N>(l, kx, ky, kz, ext) : T(0);
     }
-    z[l] = accumulate ? z[l] + v : v;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t l = l0 + u * stride;
+      if (l < L) {
+        const T val = omega * (wsq[l] * v[u]);
+        z[l] = accumulate ? z[l] + val : val;
+      }
+    }
   }
 }
 
@@ -683,11 +703,11 @@ static int mg_schwarz(MgLevel& lv, const T* r, T* z, bool accumulate) {
   case NN:                                                                                        \
     if (sizeof(T) == 8)                                                                           \
       mg_block_sum_t<double, kGsFP64, NN><<<g, 256, 0, h.stream>>>(                               \
-          h.kx, h.ky, h.L, (const double*)P::ext(lv), h.bfaces, (const double*)P::wsq(lv), h.cw8, \
-          lv.omega, acc, (double*)z);                                                             \
+          h.kx, h.ky, h.kz, h.L, (const double*)P::ext(lv), (const double*)P::wsq(lv), lv.omega,  \
+          acc, (double*)z);                                                                       \
     else                                                                                          \
       mg_block_sum_t<float, kGsTwoSum, NN><<<g, 256, 0, h.stream>>>(                              \
-          h.kx, h.ky, h.L, (const float*)P::ext(lv), h.bfaces, (const float*)P::wsq(lv), h.cw8,   \
+          h.kx, h.ky, h.kz, h.L, (const float*)P::ext(lv), (const float*)P::wsq(lv),             \
           (float)lv.omega, acc, (float*)z);                                                       \
     break;
     SEM_MG_SUM(1) SEM_MG_SUM(2) SEM_MG_SUM(3) SEM_MG_SUM(4) SEM_MG_SUM(5) SEM_MG_SUM(6)
