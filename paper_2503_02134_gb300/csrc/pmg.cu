@@ -483,6 +483,29 @@ __device__ __forceinline__ MgCand1<N> mg_cand1(int g, bool lo_bnd, bool hi_bnd) 
 // coordinates give its boundary flags (a box mesh is Dirichlet on all six
 // faces), so no load precedes the block loads; each thread sums four nodes
 // per trip, whose loads are independent.
+// Blocks holding node g along one direction, in three fixed slots (the
+// lower neighbour's, the element's own, the upper neighbour's -- ascending
+// element order): offsets into the block array (element stride es,
+// extended-index stride xs) and whether the lower / upper slots are used.
+template <int N>
+struct MgSlots {
+  int64_t lo, own, hi;
+  bool has_lo, has_hi;
+};
+
+template <int N>
+__device__ __forceinline__ MgSlots<N> mg_slots(int g, bool lo_bnd, bool hi_bnd, int64_t es,
+                                               int xs) {
+  constexpr int n = N + 1;
+  MgSlots<N> r;
+  r.own = (int64_t)(g + 1) * xs;                     // g is not a boundary node here
+  r.has_lo = !lo_bnd && (g == 0 || (N >= 2 && g == 1));
+  r.lo = -es + (int64_t)(g == 0 ? n : n + 1) * xs;
+  r.has_hi = !hi_bnd && (g == N || (N >= 2 && g == N - 1));
+  r.hi = es + (int64_t)(g == N ? 1 : 0) * xs;
+  return r;
+}
+
 template <typename T, int ACC, int N>
 __device__ __forceinline__ T mg_block_sum_node(int64_t l, int kx, int ky, int kz,
                                                const T* __restrict__ ext) {
@@ -496,23 +519,29 @@ __device__ __forceinline__ T mg_block_sum_node(int64_t l, int kx, int ky, int kz
   if ((i == 0 && xl) || (i == N && xh) || (j == 0 && yl) || (j == N && yh) ||
       (k == 0 && zl) || (k == N && zh))
     return T(0);                                    // Dirichlet node
-  const int64_t kxky = (int64_t)kx * ky;
-  const MgCand1<N> cx = mg_cand1<N>(i, xl, xh);
-  const MgCand1<N> cy = mg_cand1<N>(j, yl, yh);
-  const MgCand1<N> cz = mg_cand1<N>(k, zl, zh);
+  const MgSlots<N> sx = mg_slots<N>(i, xl, xh, m3, 1);
+  const MgSlots<N> sy = mg_slots<N>(j, yl, yh, (int64_t)kx * m3, m);
+  const MgSlots<N> sz = mg_slots<N>(k, zl, zh, (int64_t)kx * ky * m3, m2);
+  const T* base = ext + e * m3;
   GsSum<T, ACC> acc;
+  if (!(sx.has_lo | sx.has_hi | sy.has_lo | sy.has_hi | sz.has_lo | sz.has_hi)) {
+    acc.add(__ldg(base + sx.own + sy.own + sz.own));   // most nodes: the own block only
+    return acc.result();
+  }
+  const int64_t xo[3] = {sx.lo, sx.own, sx.hi}, yo[3] = {sy.lo, sy.own, sy.hi},
+                zo[3] = {sz.lo, sz.own, sz.hi};
+  const bool xu[3] = {sx.has_lo, true, sx.has_hi}, yu[3] = {sy.has_lo, true, sy.has_hi},
+             zu[3] = {sz.has_lo, true, sz.has_hi};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    if (c >= cz.cnt) break;
+    if (!zu[c]) continue;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      if (b >= cy.cnt) break;
+      if (!yu[b]) continue;
+      const int64_t yz = yo[b] + zo[c];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (a >= cx.cnt) break;
-        const int64_t eb = e + cx.off[a] + (int64_t)cy.off[b] * kx + (int64_t)cz.off[c] * kxky;
-        acc.add(__ldg(ext + eb * m3 + cx.ext[a] + m * cy.ext[b] + m2 * cz.ext[c]));
-      }
+      for (int a = 0; a < 3; ++a)
+        if (xu[a]) acc.add(__ldg(base + xo[a] + yz));
     }
   }
   return acc.result();

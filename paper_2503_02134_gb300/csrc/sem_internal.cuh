@@ -95,7 +95,7 @@ struct Handle {
   int fuse_gs = 1;             // FP32 PCG on box meshes: summation folded into the update
                                // (1: n a multiple of 4, 2: every n, 0: never)
   int upd_gs_occ[8] = {};      // resident blocks per SM of the fused update kernels (0: not yet read)
-  int upd_minb = 1;            // fused update: minimum resident blocks the compiler targets (1 or 4)
+  int upd_minb = 4;            // fused update: minimum resident blocks the compiler targets (4 or 1)
 
   // Jacobi
   double* minv64 = nullptr;
