@@ -286,12 +286,18 @@ struct MgShape {
   // number of rows (each matrix entry read from shared memory feeds two FMAs)
   static constexpr int RPT = m2 % 2 == 0 ? 2 : 1;
   static constexpr int EPB = (RPT * NT / m2) > 0 ? (RPT * NT / m2) : 1;
+  // shared-memory layout of a block: index a + P1 b + P2 c with an odd row
+  // stride P1, so that threads on consecutive rows of any direction hit
+  // distinct banks
+  static constexpr int P1 = m % 2 == 0 ? m + 1 : m;
+  static constexpr int P2 = P1 * m;
+  static constexpr int BUF = P2 * m;
 };
 
 template <typename T, int N>
 constexpr size_t mg_block_smem() {
   using Sh = MgShape<N>;
-  return sizeof(T) * ((size_t)Sh::EPB * (Sh::m3 + 6 * Sh::m2 + 3 * Sh::m)) + 3 * Sh::EPB * Sh::m + 16;
+  return sizeof(T) * ((size_t)Sh::EPB * (Sh::BUF + 6 * Sh::m2 + 3 * Sh::m)) + 3 * Sh::EPB * Sh::m + 16;
 }
 
 template <typename T, int N>
@@ -301,9 +307,10 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
                      const uint8_t* __restrict__ act, T* __restrict__ ext) {
   using Sh = MgShape<N>;
   constexpr int n = Sh::n, m = Sh::m, m2 = Sh::m2, m3 = Sh::m3, n3 = Sh::n3, EPB = Sh::EPB;
+  constexpr int P1 = Sh::P1, P2 = Sh::P2, BUF = Sh::BUF;
   extern __shared__ __align__(16) unsigned char mg_smem[];
-  T* buf = reinterpret_cast<T*>(mg_smem);   // [EPB][m3]
-  T* sS = buf + EPB * m3;                     // [EPB][3][m2]: S_d(a, b) at a*m + b
+  T* buf = reinterpret_cast<T*>(mg_smem);   // [EPB][BUF], point (a, b, c) at a + P1 b + P2 c
+  T* sS = buf + EPB * BUF;                    // [EPB][3][m2]: S_d(a, b) at a*m + b
   T* sT = sS + EPB * 3 * m2;                  // [EPB][3][m2]: S_d(b, a) at a*m + b
   T* sl = sT + EPB * 3 * m2;                  // [EPB][3][m]
   uint8_t* sa = reinterpret_cast<uint8_t*>(sl + EPB * 3 * m);   // [EPB][3][m]
@@ -332,8 +339,8 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
       const int le = row / m2, rr = row - le * m2;
       const int b = rr % m, c = rr / m;
       const uint8_t* A = sa + le * 3 * m;
-      T* out = buf + le * m3 + b * m + c * m2;
-      if (!(A[m + b] && A[2 * m + c])) {
+      T* out = buf + le * BUF + P1 * b + P2 * c;
+      if (!(A[m + b] && A[2 * m + c]) || e0 + le >= E) {
 #pragma unroll
         for (int a = 0; a < m; ++a) out[a] = T(0);
         continue;
@@ -357,25 +364,23 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
       out[m - 1] = hi;
     }
     __syncthreads();
+    // contraction passes: S^T along x, y, z, then S along x, y, z; a thread
+    // holds RPT rows (rows r and r + m2/2 of one element) in registers
+    constexpr int RPT = Sh::RPT, H = m2 / RPT;
 #pragma unroll 1
     for (int pass = 0; pass < 6; ++pass) {
       const int d = pass % 3;
       const bool fwd = pass < 3;
-      constexpr int RPT = Sh::RPT;
-      for (int pr = threadIdx.x; pr < EPB * m2 / RPT; pr += blockDim.x) {
-        const int row0 = pr * RPT;   // RPT consecutive rows of one element
-        const int le = row0 / m2;
+      const int step = d == 0 ? 1 : (d == 1 ? P1 : P2);
+      for (int pr = threadIdx.x; pr < EPB * H; pr += blockDim.x) {
+        const int le = pr / H, r0 = pr - le * H;
         T* bl[RPT];
-        int step = 1;
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
-          const int rr = row0 + q - le * m2;
+          const int rr = r0 + q * H;
           const int u = rr % m, v2 = rr / m;
-          int base;
-          if (d == 0) { base = u * m + v2 * m2; step = 1; }
-          else if (d == 1) { base = u + v2 * m2; step = m; }
-          else { base = u + v2 * m; step = m2; }
-          bl[q] = buf + le * m3 + base;
+          const int base = d == 0 ? P1 * u + P2 * v2 : (d == 1 ? u + P2 * v2 : u + P1 * v2);
+          bl[q] = buf + le * BUF + base;
         }
         // row o of S^T (forward) or of S (backward): contiguous in shared memory
         const T* Md = (fwd ? sT : sS) + le * 3 * m2 + d * m2;
@@ -405,7 +410,8 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
           const int le = q / m3, p = q - le * m3;
           const int a = p % m, b = (p / m) % m, c = p / m2;
           const T* L = sl + le * 3 * m;
-          buf[q] = buf[q] / (L[a] + L[m + b] + L[2 * m + c]);
+          T& v = buf[le * BUF + a + P1 * b + P2 * c];
+          v = v / (L[a] + L[m + b] + L[2 * m + c]);
         }
         __syncthreads();
       }
@@ -415,7 +421,9 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
       const int a = p % m, b = (p / m) % m, c = p / m2;
       const uint8_t* A = sa + le * 3 * m;
       const int64_t e = e0 + le;
-      if (e < E) ext[e * m3 + p] = (A[a] && A[m + b] && A[2 * m + c]) ? buf[q] : T(0);
+      if (e < E)
+        ext[e * m3 + p] =
+            (A[a] && A[m + b] && A[2 * m + c]) ? buf[le * BUF + a + P1 * b + P2 * c] : T(0);
     }
     __syncthreads();
   }
@@ -507,15 +515,16 @@ __device__ __forceinline__ MgSlots<N> mg_slots(int g, bool lo_bnd, bool hi_bnd, 
 }
 
 template <typename T, int ACC, int N>
-__device__ __forceinline__ T mg_block_sum_node(int64_t l, int kx, int ky, int kz,
+__device__ __forceinline__ T mg_block_sum_node(int64_t l, int kx, int ky,
+                                               const uint8_t* __restrict__ faces,
                                                const T* __restrict__ ext) {
   constexpr int n = N + 1, n3 = n * n * n, m = n + 2, m2 = m * m, m3 = m2 * m;
   const int64_t e = l / n3;
   const int rem = (int)(l - e * n3);
   const int i = rem % n, j = (rem / n) % n, k = rem / (n * n);
-  const int ex = (int)(e % kx), exy = (int)(e / kx), ey = exy % ky, ez = exy / ky;
-  const bool xl = ex == 0, xh = ex == kx - 1, yl = ey == 0, yh = ey == ky - 1;
-  const bool zl = ez == 0, zh = ez == kz - 1;
+  // the element's boundary faces (a small table that stays in L1)
+  const uint8_t f = __ldg(faces + e);
+  const bool xl = f & 1, xh = f & 2, yl = f & 4, yh = f & 8, zl = f & 16, zh = f & 32;
   if ((i == 0 && xl) || (i == N && xh) || (j == 0 && yl) || (j == N && yh) ||
       (k == 0 && zl) || (k == N && zh))
     return T(0);                                    // Dirichlet node
@@ -549,8 +558,9 @@ __device__ __forceinline__ T mg_block_sum_node(int64_t l, int kx, int ky, int kz
 
 template <typename T, int ACC, int N>
 __global__ void __launch_bounds__(256)
-    mg_block_sum_t(int kx, int ky, int kz, int64_t L, const T* __restrict__ ext,
-                   const T* __restrict__ wsq, T omega, int accumulate, T* __restrict__ z) {
+    mg_block_sum_t(int kx, int ky, int64_t L, const uint8_t* __restrict__ faces,
+                   const T* __restrict__ ext, const T* __restrict__ wsq, T omega, int accumulate,
+                   T* __restrict__ z) {
   constexpr int U = 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t l0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l0 < L; l0 += U * stride) {
@@ -558,7 +568,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t l = l0 + u * stride;
-      v[u] = l < L ? mg_block_sum_node<T, ACC, N>(l, kx, ky, kz, ext) : T(0);
+      v[u] = l < L ? mg_block_sum_node<T, ACC, N>(l, kx, ky, faces, ext) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -732,11 +742,11 @@ static int mg_schwarz(MgLevel& lv, const T* r, T* z, bool accumulate) {
   case NN:                                                                                        \
     if (sizeof(T) == 8)                                                                           \
       mg_block_sum_t<double, kGsFP64, NN><<<g, 256, 0, h.stream>>>(                               \
-          h.kx, h.ky, h.kz, h.L, (const double*)P::ext(lv), (const double*)P::wsq(lv), lv.omega,  \
-          acc, (double*)z);                                                                       \
+          h.kx, h.ky, h.L, h.bfaces, (const double*)P::ext(lv), (const double*)P::wsq(lv),        \
+          lv.omega, acc, (double*)z);                                                             \
     else                                                                                          \
       mg_block_sum_t<float, kGsTwoSum, NN><<<g, 256, 0, h.stream>>>(                              \
-          h.kx, h.ky, h.kz, h.L, (const float*)P::ext(lv), (const float*)P::wsq(lv),             \
+          h.kx, h.ky, h.L, h.bfaces, (const float*)P::ext(lv), (const float*)P::wsq(lv),          \
           (float)lv.omega, acc, (float*)z);                                                       \
     break;
     SEM_MG_SUM(1) SEM_MG_SUM(2) SEM_MG_SUM(3) SEM_MG_SUM(4) SEM_MG_SUM(5) SEM_MG_SUM(6)
