@@ -585,56 +585,77 @@ __global__ void __launch_bounds__(256)
 // order max(1, NF/2).  RESTRICT: out(coarse) = (J^T)^{x3}(in(fine) / m_f)
 // with 1/m_f from the multiplicity code (exact: powers of two; 0 on the
 // Dirichlet boundary, where in is zero); otherwise out(fine) += J^{x3} in(coarse).
+template <int NF>
+struct MgTransferShape {
+  static constexpr int NC = NF / 2 > 1 ? NF / 2 : 1;
+  static constexpr int nf = NF + 1, nc = NC + 1, nf3 = nf * nf * nf;
+  // elements per CTA iteration: about 1024 fine values, so the loads and
+  // the three contraction stages of several elements overlap
+  static constexpr int EPB = 1024 / nf3 > 1 ? 1024 / nf3 : 1;
+};
+
 template <typename T, int NF, bool RESTRICT>
 __global__ void __launch_bounds__(256)
     mg_transfer_t(int64_t E, const T* __restrict__ J, const T* __restrict__ in,
                   const uint8_t* __restrict__ cw, T* __restrict__ out) {
-  constexpr int NC = NF / 2 > 1 ? NF / 2 : 1;
-  constexpr int nf = NF + 1, nc = NC + 1;
+  using Sh = MgTransferShape<NF>;
+  constexpr int nf = Sh::nf, nc = Sh::nc, EPB = Sh::EPB;
   constexpr int ni = RESTRICT ? nf : nc, no = RESTRICT ? nc : nf;
   constexpr int ni3 = ni * ni * ni, no3 = no * no * no;
+  constexpr int S1 = ni * ni * no, S2 = ni * no * no;   // stage sizes per element
+  constexpr int BUF = nf * nf * nf;                      // >= every stage
   extern __shared__ __align__(16) unsigned char mg_smem[];
-  T* b0 = reinterpret_cast<T*>(mg_smem);   // nf^3
-  T* b1 = b0 + nf * nf * nf;               // nf^3
-  T* sM = b1 + nf * nf * nf;               // ni * no
+  T* b0 = reinterpret_cast<T*>(mg_smem);   // [EPB][BUF]
+  T* b1 = b0 + EPB * BUF;                  // [EPB][BUF]
+  T* sM = b1 + EPB * BUF;                  // ni * no
   for (int q = threadIdx.x; q < ni * no; q += blockDim.x) {
     const int o = q / ni, t = q - o * ni;   // sM[o][t] = M(o, t)
     sM[q] = RESTRICT ? J[t * nc + o] : J[o * nc + t];
   }
-  for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+  const int64_t ngroups = (E + EPB - 1) / EPB;
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const int64_t e0 = g * EPB;
+    const int ne = (int)(E - e0 < EPB ? E - e0 : EPB);
     __syncthreads();
-    for (int q = threadIdx.x; q < ni3; q += blockDim.x) {
-      T v = in[e * ni3 + q];
+    for (int q = threadIdx.x; q < ne * ni3; q += blockDim.x) {
+      const int le = q / ni3, p = q - le * ni3;
+      T v = in[e0 * ni3 + q];
       if (RESTRICT) {
-        const uint8_t m = cw[e * ni3 + q];
+        const uint8_t m = cw[e0 * ni3 + q];
         v = m ? v * (T(1) / T(m)) : T(0);
       }
-      b0[q] = v;
+      b0[le * BUF + p] = v;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < ni * ni * no; q += blockDim.x) {
-      const int o = q % no, jk = q / no;
+    for (int q = threadIdx.x; q < ne * S1; q += blockDim.x) {
+      const int le = q / S1, p = q - le * S1;
+      const int o = p % no, jk = p / no;
+      const T* src = b0 + le * BUF + jk * ni;
       T s = T(0);
 #pragma unroll
-      for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * b0[jk * ni + t];
-      b1[q] = s;
+      for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * src[t];
+      b1[le * BUF + p] = s;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < ni * no * no; q += blockDim.x) {
-      const int i = q % no, o = (q / no) % no, k = q / (no * no);
+    for (int q = threadIdx.x; q < ne * S2; q += blockDim.x) {
+      const int le = q / S2, p = q - le * S2;
+      const int i = p % no, o = (p / no) % no, k = p / (no * no);
+      const T* src = b1 + le * BUF + k * ni * no + i;
       T s = T(0);
 #pragma unroll
-      for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * b1[(k * ni + t) * no + i];
-      b0[q] = s;
+      for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * src[t * no];
+      b0[le * BUF + p] = s;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < no3; q += blockDim.x) {
-      const int ij = q % (no * no), o = q / (no * no);
+    for (int q = threadIdx.x; q < ne * no3; q += blockDim.x) {
+      const int le = q / no3, p = q - le * no3;
+      const int ij = p % (no * no), o = p / (no * no);
+      const T* src = b0 + le * BUF + ij;
       T s = T(0);
 #pragma unroll
-      for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * b0[t * no * no + ij];
-      if (RESTRICT) out[e * no3 + q] = s;
-      else out[e * no3 + q] += s;
+      for (int t = 0; t < ni; ++t) s += sM[o * ni + t] * src[t * no * no];
+      if (RESTRICT) out[e0 * no3 + q] = s;
+      else out[e0 * no3 + q] += s;
     }
   }
 }
@@ -642,15 +663,20 @@ __global__ void __launch_bounds__(256)
 template <typename T, bool RESTRICT>
 static int mg_transfer_t_launch(Handle& h, int NF, const T* J, const T* in, const uint8_t* cw,
                                 T* out) {
-  const int g = (int)std::min<int64_t>(h.E, (int64_t)h.num_sms * 8);
   switch (NF) {
 #define SEM_MG_TR(NN)                                                                      \
   case NN: {                                                                               \
-    constexpr int nf = NN + 1, nc = (NN / 2 > 1 ? NN / 2 : 1) + 1;                         \
-    constexpr size_t smem = sizeof(T) * (2 * (size_t)nf * nf * nf + (size_t)nf * nc);      \
+    using TS = MgTransferShape<NN>;                                                        \
+    constexpr size_t smem =                                                                \
+        sizeof(T) * (2 * (size_t)TS::EPB * TS::nf3 + (size_t)TS::nf * TS::nc);             \
     auto k = mg_transfer_t<T, NN, RESTRICT>;                                               \
     SEM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    k<<<g, 256, smem, h.stream>>>(h.E, J, in, cw, out);                                    \
+    int per_sm = 0;                                                                        \
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));        \
+    const int64_t groups = (h.E + TS::EPB - 1) / TS::EPB;                                  \
+    const int gg = (int)std::max<int64_t>(                                                 \
+        1, std::min<int64_t>(groups, (int64_t)h.num_sms * std::max(per_sm, 1)));           \
+    k<<<gg, 256, smem, h.stream>>>(h.E, J, in, cw, out);                                   \
     break;                                                                                 \
   }
     SEM_MG_TR(2) SEM_MG_TR(3) SEM_MG_TR(4) SEM_MG_TR(5) SEM_MG_TR(6) SEM_MG_TR(7) SEM_MG_TR(8)
