@@ -514,70 +514,62 @@ __device__ __forceinline__ MgSlots<N> mg_slots(int g, bool lo_bnd, bool hi_bnd, 
   return r;
 }
 
-template <typename T, int ACC, int N>
-__device__ __forceinline__ T mg_block_sum_node(int64_t l, int kx, int ky,
-                                               const uint8_t* __restrict__ faces,
-                                               const T* __restrict__ ext) {
-  constexpr int n = N + 1, n3 = n * n * n, m = n + 2, m2 = m * m, m3 = m2 * m;
-  const int64_t e = l / n3;
-  const int rem = (int)(l - e * n3);
-  const int i = rem % n, j = (rem / n) % n, k = rem / (n * n);
-  // the element's boundary faces (a small table that stays in L1)
-  const uint8_t f = __ldg(faces + e);
-  const bool xl = f & 1, xh = f & 2, yl = f & 4, yh = f & 8, zl = f & 16, zh = f & 32;
-  if ((i == 0 && xl) || (i == N && xh) || (j == 0 && yl) || (j == N && yh) ||
-      (k == 0 && zl) || (k == N && zh))
-    return T(0);                                    // Dirichlet node
-  const MgSlots<N> sx = mg_slots<N>(i, xl, xh, m3, 1);
-  const MgSlots<N> sy = mg_slots<N>(j, yl, yh, (int64_t)kx * m3, m);
-  const MgSlots<N> sz = mg_slots<N>(k, zl, zh, (int64_t)kx * ky * m3, m2);
-  const T* base = ext + e * m3;
-  GsSum<T, ACC> acc;
-  if (!(sx.has_lo | sx.has_hi | sy.has_lo | sy.has_hi | sz.has_lo | sz.has_hi)) {
-    acc.add(__ldg(base + sx.own + sy.own + sz.own));   // most nodes: the own block only
-    return acc.result();
-  }
-  const int64_t xo[3] = {sx.lo, sx.own, sx.hi}, yo[3] = {sy.lo, sy.own, sy.hi},
-                zo[3] = {sz.lo, sz.own, sz.hi};
-  const bool xu[3] = {sx.has_lo, true, sx.has_hi}, yu[3] = {sy.has_lo, true, sy.has_hi},
-             zu[3] = {sz.has_lo, true, sz.has_hi};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (!zu[c]) continue;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      if (!yu[b]) continue;
-      const int64_t yz = yo[b] + zo[c];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (xu[a]) acc.add(__ldg(base + xo[a] + yz));
-    }
-  }
-  return acc.result();
-}
-
+// Block sum by element rows: one thread per row (e, j, k), all n nodes of
+// the row.  The y/z candidate blocks are the same for the whole row (no
+// divergence between the nodes of a row), the x candidates are fixed per
+// node index; each (z, y) combination contributes a contiguous row of the
+// block array plus the two x-neighbour values.  Every copy of a node sums
+// the same blocks in the same order (ascending element: lower, own, upper
+// in z, then y, then x), so all copies get the same bits.
 template <typename T, int ACC, int N>
 __global__ void __launch_bounds__(256)
-    mg_block_sum_t(int kx, int ky, int64_t L, const uint8_t* __restrict__ faces,
-                   const T* __restrict__ ext, const T* __restrict__ wsq, T omega, int accumulate,
-                   T* __restrict__ z) {
-  constexpr int U = 4;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t l0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l0 < L; l0 += U * stride) {
-    T v[U];
+    mg_block_sum_rows(int kx, int ky, int64_t E, const uint8_t* __restrict__ faces,
+                      const T* __restrict__ ext, const T* __restrict__ wsq, T omega,
+                      int accumulate, T* __restrict__ z) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, m = n + 2, m2 = m * m, m3 = m2 * m;
+  const int64_t rows = E * n2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < rows;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / n2;
+    const int jk = (int)(t - e * n2), j = jk % n, k = jk / n;
+    const uint8_t f = __ldg(faces + e);
+    const bool xl = f & 1, xh = f & 2, yl = f & 4, yh = f & 8, zl = f & 16, zh = f & 32;
+    T* zr = z + e * n3 + n * jk;
+    const T* wr = wsq + e * n3 + n * jk;
+    const bool row_dirichlet = (j == 0 && yl) || (j == N && yh) || (k == 0 && zl) || (k == N && zh);
+    T out[n];
+    if (row_dirichlet) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t l = l0 + u * stride;
-      v[u] = l < L ? mg_block_sum_node<T, ACC, N>(l, kx, ky, faces, ext) : T(0);
-    }
+      for (int i = 0; i < n; ++i) out[i] = T(0);
+    } else {
+      const MgSlots<N> sy = mg_slots<N>(j, yl, yh, (int64_t)kx * m3, m);
+      const MgSlots<N> sz = mg_slots<N>(k, zl, zh, (int64_t)kx * ky * m3, m2);
+      const int64_t yo[3] = {sy.lo, sy.own, sy.hi}, zo[3] = {sz.lo, sz.own, sz.hi};
+      const bool yu[3] = {sy.has_lo, true, sy.has_hi}, zu[3] = {sz.has_lo, true, sz.has_hi};
+      GsSum<T, ACC> acc[n];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t l = l0 + u * stride;
-      if (l < L) {
-        const T val = omega * (wsq[l] * v[u]);
-        z[l] = accumulate ? z[l] + val : val;
+      for (int c = 0; c < 3; ++c) {
+        if (!zu[c]) continue;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          if (!yu[b]) continue;
+          const T* rp = ext + e * m3 + zo[c] + yo[b];   // block row, extended index a = 0
+#pragma unroll
+          for (int i = 0; i < n; ++i) {
+            if (i == 0 && !xl) acc[i].add(__ldg(rp - m3 + n));
+            if (N >= 2 && i == 1 && !xl) acc[i].add(__ldg(rp - m3 + n + 1));
+            acc[i].add(__ldg(rp + i + 1));
+            if (N >= 2 && i == N - 1 && !xh) acc[i].add(__ldg(rp + m3));
+            if (i == N && !xh) acc[i].add(__ldg(rp + m3 + 1));
+          }
+        }
       }
+#pragma unroll
+      for (int i = 0; i < n; ++i)
+        out[i] = ((i == 0 && xl) || (i == N && xh)) ? T(0) : omega * (wr[i] * acc[i].result());
     }
+#pragma unroll
+    for (int i = 0; i < n; ++i) zr[i] = accumulate ? zr[i] + out[i] : out[i];
   }
 }
 
@@ -762,17 +754,17 @@ static int mg_schwarz(MgLevel& lv, const T* r, T* z, bool accumulate) {
   if ((rc = mg_block_solve_dispatch<T>(h, r, P::wsq(lv), P::S(lv), P::lam(lv), lv.act, P::ext(lv))))
     return rc;
   const int acc = accumulate ? 1 : 0;
-  const int g = grid_of(h, h.L);
+  const int gr = grid_of(h, h.E * (int64_t)h.n * h.n);
   switch (h.N) {
 #define SEM_MG_SUM(NN)                                                                            \
   case NN:                                                                                        \
     if (sizeof(T) == 8)                                                                           \
-      mg_block_sum_t<double, kGsFP64, NN><<<g, 256, 0, h.stream>>>(                               \
-          h.kx, h.ky, h.L, h.bfaces, (const double*)P::ext(lv), (const double*)P::wsq(lv),        \
+      mg_block_sum_rows<double, kGsFP64, NN><<<gr, 256, 0, h.stream>>>(                           \
+          h.kx, h.ky, h.E, h.bfaces, (const double*)P::ext(lv), (const double*)P::wsq(lv),        \
           lv.omega, acc, (double*)z);                                                             \
     else                                                                                          \
-      mg_block_sum_t<float, kGsTwoSum, NN><<<g, 256, 0, h.stream>>>(                              \
-          h.kx, h.ky, h.L, h.bfaces, (const float*)P::ext(lv), (const float*)P::wsq(lv),          \
+      mg_block_sum_rows<float, kGsTwoSum, NN><<<gr, 256, 0, h.stream>>>(                          \
+          h.kx, h.ky, h.E, h.bfaces, (const float*)P::ext(lv), (const float*)P::wsq(lv),          \
           (float)lv.omega, acc, (float*)z);                                                       \
     break;
     SEM_MG_SUM(1) SEM_MG_SUM(2) SEM_MG_SUM(3) SEM_MG_SUM(4) SEM_MG_SUM(5) SEM_MG_SUM(6)
