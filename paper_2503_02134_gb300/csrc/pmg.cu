@@ -300,6 +300,49 @@ constexpr size_t mg_block_smem() {
   return sizeof(T) * ((size_t)Sh::EPB * (Sh::BUF + 6 * Sh::m2 + 3 * Sh::m)) + 3 * Sh::EPB * Sh::m + 16;
 }
 
+// One contraction pass of the block solve along direction D: every row
+// along D of every block in shared memory is replaced by (S^T row) when FWD
+// or (S row); a thread holds RPT rows (r and r + m2/2 of one element).
+template <typename T, int N, int D, bool FWD>
+__device__ __forceinline__ void mg_pass(T* buf, const T* sT, const T* sS) {
+  using Sh = MgShape<N>;
+  constexpr int m = Sh::m, m2 = Sh::m2, EPB = Sh::EPB, P1 = Sh::P1, P2 = Sh::P2, BUF = Sh::BUF;
+  constexpr int RPT = Sh::RPT, H = m2 / RPT;
+  constexpr int step = D == 0 ? 1 : (D == 1 ? P1 : P2);
+  for (int pr = threadIdx.x; pr < EPB * H; pr += blockDim.x) {
+    const int le = pr / H, r0 = pr - le * H;
+    T* bl[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int rr = r0 + q * H;
+      const int u = rr % m, v2 = rr / m;
+      const int base = D == 0 ? P1 * u + P2 * v2 : (D == 1 ? u + P2 * v2 : u + P1 * v2);
+      bl[q] = buf + le * BUF + base;
+    }
+    // row o of S^T (forward) or of S (backward): contiguous in shared memory
+    const T* Md = (FWD ? sT : sS) + le * 3 * m2 + D * m2;
+    T in[RPT][m];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+      for (int t = 0; t < m; ++t) in[q][t] = bl[q][t * step];
+#pragma unroll
+    for (int o = 0; o < m; ++o) {
+      T acc[RPT];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) acc[q] = T(0);
+#pragma unroll
+      for (int t = 0; t < m; ++t) {
+        const T mv = Md[o * m + t];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) acc[q] += mv * in[q][t];
+      }
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) bl[q][o * step] = acc[q];
+    }
+  }
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(MgShape<N>::NT)
     mg_block_solve_t(int kx, int ky, int64_t E, const T* __restrict__ r, const T* __restrict__ wsq,
@@ -364,58 +407,28 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
       out[m - 1] = hi;
     }
     __syncthreads();
-    // contraction passes: S^T along x, y, z, then S along x, y, z; a thread
-    // holds RPT rows (rows r and r + m2/2 of one element) in registers
-    constexpr int RPT = Sh::RPT, H = m2 / RPT;
-#pragma unroll 1
-    for (int pass = 0; pass < 6; ++pass) {
-      const int d = pass % 3;
-      const bool fwd = pass < 3;
-      const int step = d == 0 ? 1 : (d == 1 ? P1 : P2);
-      for (int pr = threadIdx.x; pr < EPB * H; pr += blockDim.x) {
-        const int le = pr / H, r0 = pr - le * H;
-        T* bl[RPT];
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-          const int rr = r0 + q * H;
-          const int u = rr % m, v2 = rr / m;
-          const int base = d == 0 ? P1 * u + P2 * v2 : (d == 1 ? u + P2 * v2 : u + P1 * v2);
-          bl[q] = buf + le * BUF + base;
-        }
-        // row o of S^T (forward) or of S (backward): contiguous in shared memory
-        const T* Md = (fwd ? sT : sS) + le * 3 * m2 + d * m2;
-        T in[RPT][m];
-#pragma unroll
-        for (int q = 0; q < RPT; ++q)
-#pragma unroll
-          for (int t = 0; t < m; ++t) in[q][t] = bl[q][t * step];
-#pragma unroll
-        for (int o = 0; o < m; ++o) {
-          T acc[RPT];
-#pragma unroll
-          for (int q = 0; q < RPT; ++q) acc[q] = T(0);
-#pragma unroll
-          for (int t = 0; t < m; ++t) {
-            const T mv = Md[o * m + t];
-#pragma unroll
-            for (int q = 0; q < RPT; ++q) acc[q] += mv * in[q][t];
-          }
-#pragma unroll
-          for (int q = 0; q < RPT; ++q) bl[q][o * step] = acc[q];
-        }
-      }
-      __syncthreads();
-      if (pass == 2) {
-        for (int q = threadIdx.x; q < EPB * m3; q += blockDim.x) {
-          const int le = q / m3, p = q - le * m3;
-          const int a = p % m, b = (p / m) % m, c = p / m2;
-          const T* L = sl + le * 3 * m;
-          T& v = buf[le * BUF + a + P1 * b + P2 * c];
-          v = v / (L[a] + L[m + b] + L[2 * m + c]);
-        }
-        __syncthreads();
-      }
+    // contraction passes: S^T along x, y, z, the eigenvalue scaling, then S
+    // along x, y, z (direction and stride fixed at compile time per pass)
+    mg_pass<T, N, 0, true>(buf, sT, sS);
+    __syncthreads();
+    mg_pass<T, N, 1, true>(buf, sT, sS);
+    __syncthreads();
+    mg_pass<T, N, 2, true>(buf, sT, sS);
+    __syncthreads();
+    for (int q = threadIdx.x; q < EPB * m3; q += blockDim.x) {
+      const int le = q / m3, p = q - le * m3;
+      const int a = p % m, b = (p / m) % m, c = p / m2;
+      const T* L = sl + le * 3 * m;
+      T& v = buf[le * BUF + a + P1 * b + P2 * c];
+      v = v / (L[a] + L[m + b] + L[2 * m + c]);
     }
+    __syncthreads();
+    mg_pass<T, N, 0, false>(buf, sT, sS);
+    __syncthreads();
+    mg_pass<T, N, 1, false>(buf, sT, sS);
+    __syncthreads();
+    mg_pass<T, N, 2, false>(buf, sT, sS);
+    __syncthreads();
     for (int q = threadIdx.x; q < EPB * m3; q += blockDim.x) {
       const int le = q / m3, p = q - le * m3;
       const int a = p % m, b = (p / m) % m, c = p / m2;
