@@ -281,7 +281,7 @@ __global__ void mg_weights_kernel(int N, int kx, int ky, int kz, int64_t L,
 template <int N>
 struct MgShape {
   static constexpr int n = N + 1, m = n + 2, m2 = m * m, m3 = m2 * m, n3 = n * n * n;
-  static constexpr int NT = 128;
+  static constexpr int NT = 256;
   // rows per thread in the contraction passes: two when a block has an even
   // number of rows (each matrix entry read from shared memory feeds two FMAs)
   static constexpr int RPT = m2 % 2 == 0 ? 2 : 1;
@@ -415,12 +415,19 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
     __syncthreads();
     mg_pass<T, N, 2, true>(buf, sT, sS);
     __syncthreads();
-    for (int q = threadIdx.x; q < EPB * m3; q += blockDim.x) {
-      const int le = q / m3, p = q - le * m3;
-      const int a = p % m, b = (p / m) % m, c = p / m2;
+    // divide by lam_x + lam_y + lam_z, by rows along x (FP32: times the
+    // correctly rounded reciprocal)
+    for (int row = threadIdx.x; row < EPB * m2; row += blockDim.x) {
+      const int le = row / m2, rr = row - le * m2;
+      const int b = rr % m, c = rr / m;
       const T* L = sl + le * 3 * m;
-      T& v = buf[le * BUF + a + P1 * b + P2 * c];
-      v = v / (L[a] + L[m + b] + L[2 * m + c]);
+      const T lbc = L[m + b] + L[2 * m + c];
+      T* v = buf + le * BUF + P1 * b + P2 * c;
+#pragma unroll
+      for (int a = 0; a < m; ++a) {
+        if constexpr (sizeof(T) == 4) v[a] = v[a] * __frcp_rn(L[a] + lbc);
+        else v[a] = v[a] / (L[a] + lbc);
+      }
     }
     __syncthreads();
     mg_pass<T, N, 0, false>(buf, sT, sS);
@@ -429,14 +436,18 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
     __syncthreads();
     mg_pass<T, N, 2, false>(buf, sT, sS);
     __syncthreads();
-    for (int q = threadIdx.x; q < EPB * m3; q += blockDim.x) {
-      const int le = q / m3, p = q - le * m3;
-      const int a = p % m, b = (p / m) % m, c = p / m2;
-      const uint8_t* A = sa + le * 3 * m;
+    // write the blocks (inactive points zero), by rows along x
+    for (int row = threadIdx.x; row < EPB * m2; row += blockDim.x) {
+      const int le = row / m2, rr = row - le * m2;
+      const int b = rr % m, c = rr / m;
       const int64_t e = e0 + le;
-      if (e < E)
-        ext[e * m3 + p] =
-            (A[a] && A[m + b] && A[2 * m + c]) ? buf[le * BUF + a + P1 * b + P2 * c] : T(0);
+      if (e >= E) continue;
+      const uint8_t* A = sa + le * 3 * m;
+      const bool on = A[m + b] && A[2 * m + c];
+      const T* v = buf + le * BUF + P1 * b + P2 * c;
+      T* out = ext + e * m3 + m * b + m2 * c;
+#pragma unroll
+      for (int a = 0; a < m; ++a) out[a] = (on && A[a]) ? v[a] : T(0);
     }
     __syncthreads();
   }
