@@ -236,8 +236,8 @@ void sem_x0_destroy(sem_x0_model m);
  * N in 1..9), all on one stream, and the work lists of the batched kernels:
  * each phase of a PCG iteration (operator, gather-scatter, update + dots) is
  * ONE persistent launch over every problem's work items (for box-mesh
- * problems the gather-scatter is folded into the update, as with the
- * handle option "fuse_gs"), and chunks of
+ * problems with N = 7 the gather-scatter is folded into the update, as with
+ * the handle option "fuse_gs"), and chunks of
  * iterations are replayed as a CUDA graph.  A project autotuner picks the
  * operator's pipeline depth and grid at set-up.  The solve is the mixed
  * path with reliable updates (as sem_pcg_solve_ex, refine_mode 0), per

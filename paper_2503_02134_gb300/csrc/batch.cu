@@ -347,18 +347,16 @@ __global__ void __launch_bounds__(256)
 
 __device__ __forceinline__ float batch_weight(uint8_t m) { return m ? __frcp_rn((float)m) : 0.f; }
 
-// QQ^T w at float4 group q of a box-mesh problem with n = 4 or 8, gathered
-// from the copies' positions (the separate pass's order and TwoSum
-// accumulation).
+// QQ^T w at float4 group q of a box-mesh problem with n = 8, gathered from
+// the copies' positions (the separate pass's order and TwoSum accumulation).
 __device__ __forceinline__ float4 batch_gather(const BatchProb& P, int64_t q) {
-  if (P.n == 8) return gs_gather_row4<8, kGsTwoSum>(P.w, q, P.faces, P.kx, P.kxky);
-  return gs_gather_row4<4, kGsTwoSum>(P.w, q, P.faces, P.kx, P.kxky);
+  return gs_gather_row4<8, kGsTwoSum>(P.w, q, P.faces, P.kx, P.kxky);
 }
 
 // add2s2 x 2 + glsc3(r,c,r) + glsc3(r,c,z) for one range of every problem
 // (for box-mesh problems with the summation QQ^T folded in).
 template <bool FUSED>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     batch_update_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ uitems,
                         const int* __restrict__ nuitems_dev) {
   const int nuitems = *nuitems_dev;
@@ -801,9 +799,10 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
     P.nupd = (int)(((h.L >> 2) + kUpdItem4 - 1) / kUpdItem4);
     P.kx = h.kx;
     P.kxky = (int64_t)h.kx * h.ky;
-    // folded summation for n a multiple of 4 (whole float4 rows); the
-    // per-node gather of other orders measured slower than the separate pass
-    P.fuse = gs_fusable(h) && (h.n == 4 || h.n == 8) ? 1 : 0;
+    // folded summation for n = 8 (whole float4 rows; the batch's orders are
+    // N = 5, 7, 9 and the per-node gather of other orders measured slower
+    // than the separate pass)
+    P.fuse = gs_fusable(h) && h.n == 8 ? 1 : 0;
     b->present[order_slot(h.n)] = true;
     ax_off[p] = part_total;
     part_total += h.E;

@@ -29,8 +29,8 @@ def test_batch_matches_standalone_and_oracle(sem):
         assert sem.sem_batch_get_option(b, f"variant_n{N + 1}") in (0, 1, 2)
         assert sem.sem_batch_get_option(b, f"grid_n{N + 1}") >= 1
     assert sem.sem_batch_get_option(b, "variant_n4") == -1 or 3 in Ns
-    # box meshes with n = 4 or 8: the gather-scatter is folded into the update
-    assert sem.sem_batch_get_option(b, "fused_problems") == sum(N in (3, 7) for N in Ns)
+    # box meshes with n = 8: the gather-scatter is folded into the update
+    assert sem.sem_batch_get_option(b, "fused_problems") == sum(N == 7 for N in Ns)
     fs, xs = [], []
     for i, c in enumerate(CASES):
         h = sem.sem_batch_problem(b, i)
