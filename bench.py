@@ -217,7 +217,8 @@ def order_sweep_leg(sem, torch, hbm_gbs):
         S = sem.Solver(c.kx, c.ky, c.kz, N, deform=True, stream=stream.cuda_stream)
         L = S.L
         with torch.cuda.stream(stream):
-            u64 = torch.rand(L, dtype=torch.float64, device="cuda") * 2 - 1
+            gen = torch.Generator(device="cuda").manual_seed(N)
+            u64 = torch.rand(L, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
             u32 = u64.float()
             w64 = torch.empty_like(u64)
             w32 = torch.empty_like(u32)
@@ -459,7 +460,8 @@ def main():
 
     if args.profile:
         with torch.cuda.stream(stream):
-            u = torch.rand(L, dtype=torch.float32, device="cuda")
+            u = torch.rand(L, dtype=torch.float32, device="cuda",
+                           generator=torch.Generator(device="cuda").manual_seed(1))
             w = torch.empty_like(u)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("bench_profile")
@@ -555,7 +557,8 @@ def main():
     def time_ax(prec, reps=20, local_only=True):
         dt = torch.float64 if prec == sem.SEM_FP64 else torch.float32
         with torch.cuda.stream(stream):
-            u = torch.rand(L, dtype=dt, device="cuda")
+            u = torch.rand(L, dtype=dt, device="cuda",
+                           generator=torch.Generator(device="cuda").manual_seed(2))
             w = torch.empty_like(u)
         fn = sem.sem_ax_local if local_only else sem.sem_ax
         for _ in range(3):

@@ -102,3 +102,45 @@ def test_mixed_solve_full_size_residual(setup):
     # ||r||_c <= tol ||b||_c
     bnorm = sem.sem_glsc3(S.h, b, b, sem.SEM_FP64) ** 0.5
     assert np.abs(r_ora).max() <= 1e-8 * bnorm * 1.0001
+
+
+@pytest.mark.parametrize("Nsw", [5, 9, 11, 13, 15])
+def test_order_sweep_full_size_sampled(Nsw):
+    """The order sweep's meshes (about 2^24 local DOFs per order, deformed),
+    as the benchmark sets them up: the FP32 operator and its two
+    tensor-core variants against the oracle on sampled elements (TF32 keeps
+    10 mantissa bits, the BF16 split about 16; bounds as in the small-case
+    tests)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2503_02134_gb300 as sem
+    import sem_inputs
+    c = sem_inputs.order_sweep_case(Nsw)
+    S = sem.Solver(c.kx, c.ky, c.kz, Nsw, deform=True)
+    nn = Nsw + 1
+    E = c.kx * c.ky * c.kz
+    g = np.random.default_rng(Nsw)
+    elems = np.array(sorted({0, E - 1, c.kx - 1, E // 2} | set(int(e) for e in g.integers(0, E, 12))))
+    X = so.deform_cyclic(so.box_coords_elements(c.kx, c.ky, c.kz, Nsw, elems))
+    G, _, _ = so.geometry(X, Nsw)
+    xi, _ = so.gll(Nsw)
+    D = so.deriv_matrix(Nsw, xi)
+    ex, ey, ez = elems % c.kx, (elems // c.kx) % c.ky, elems // (c.kx * c.ky)
+    r = np.arange(nn)
+    I = ex[:, None, None, None] * Nsw + r[None, None, None, :]
+    J = ey[:, None, None, None] * Nsw + r[None, None, :, None]
+    Kz = ez[:, None, None, None] * Nsw + r[None, :, None, None]
+    on = ((I == 0) | (I == c.kx * Nsw) | (J == 0) | (J == c.ky * Nsw) | (Kz == 0)
+          | (Kz == c.kz * Nsw))
+    mask = np.where(on, 0.0, 1.0).reshape(-1)
+    rows = (elems[:, None] * nn ** 3 + np.arange(nn ** 3)[None, :]).reshape(-1)
+    gen = torch.Generator(device="cuda").manual_seed(Nsw)
+    u = (torch.rand(S.L, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1).float()
+    ref = mask * so.ax_local(u.double().cpu().numpy()[rows], G, D)
+    w = torch.empty_like(u)
+    for prec, tol in ((sem.SEM_MIXED_FP32, 1e-6), (sem.SEM_MIXED_TF32, 2.0 ** -11 * 8 * nn),
+                      (sem.SEM_MIXED_BF16X3, 2.0 ** -16 * 8 * nn)):
+        sem.sem_ax_local(S.h, u, w, prec)
+        err = rel_maxerr(w.double().cpu().numpy()[rows], ref)
+        assert err < tol, (Nsw, prec, err, tol)
+    S.close()
