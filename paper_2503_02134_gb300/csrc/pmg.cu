@@ -343,6 +343,69 @@ __device__ __forceinline__ void mg_pass(T* buf, const T* sT, const T* sS) {
   }
 }
 
+// The middle of the block solve in one pass over the rows along z: S_z^T,
+// the division by lam_x + lam_y + lam_z (FP32: times the correctly rounded
+// reciprocal), S_z -- the row stays in registers throughout.
+template <typename T, int N>
+__device__ __forceinline__ void mg_pass_z(T* buf, const T* sT, const T* sS, const T* sl) {
+  using Sh = MgShape<N>;
+  constexpr int m = Sh::m, m2 = Sh::m2, EPB = Sh::EPB, P1 = Sh::P1, P2 = Sh::P2, BUF = Sh::BUF;
+  constexpr int RPT = Sh::RPT, H = m2 / RPT;
+  for (int pr = threadIdx.x; pr < EPB * H; pr += blockDim.x) {
+    const int le = pr / H, r0 = pr - le * H;
+    T* bl[RPT];
+    T lab[RPT];
+    const T* L = sl + le * 3 * m;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int rr = r0 + q * H;
+      const int a = rr % m, b = rr / m;
+      bl[q] = buf + le * BUF + a + P1 * b;
+      lab[q] = L[a] + L[m + b];
+    }
+    const T* Mf = sT + le * 3 * m2 + 2 * m2;   // rows of S_z^T
+    const T* Mb = sS + le * 3 * m2 + 2 * m2;   // rows of S_z
+    T v[RPT][m];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+      for (int t = 0; t < m; ++t) v[q][t] = bl[q][t * P2];
+    T w[RPT][m];
+#pragma unroll
+    for (int o = 0; o < m; ++o) {
+      T acc[RPT];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) acc[q] = T(0);
+#pragma unroll
+      for (int t = 0; t < m; ++t) {
+        const T mv = Mf[o * m + t];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) acc[q] += mv * v[q][t];
+      }
+      const T lc = L[2 * m + o];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        if constexpr (sizeof(T) == 4) w[q][o] = acc[q] * __frcp_rn(lab[q] + lc);
+        else w[q][o] = acc[q] / (lab[q] + lc);
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < m; ++o) {
+      T acc[RPT];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) acc[q] = T(0);
+#pragma unroll
+      for (int t = 0; t < m; ++t) {
+        const T mv = Mb[o * m + t];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) acc[q] += mv * w[q][t];
+      }
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) bl[q][o * P2] = acc[q];
+    }
+  }
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(MgShape<N>::NT)
     mg_block_solve_t(int kx, int ky, int64_t E, const T* __restrict__ r, const T* __restrict__ wsq,
@@ -407,34 +470,18 @@ __global__ void __launch_bounds__(MgShape<N>::NT)
       out[m - 1] = hi;
     }
     __syncthreads();
-    // contraction passes: S^T along x, y, z, the eigenvalue scaling, then S
-    // along x, y, z (direction and stride fixed at compile time per pass)
+    // contraction passes: S^T along x, y; then along z S^T, the eigenvalue
+    // scaling and S in one pass; then S along y, x (the backward
+    // contractions commute)
     mg_pass<T, N, 0, true>(buf, sT, sS);
     __syncthreads();
     mg_pass<T, N, 1, true>(buf, sT, sS);
     __syncthreads();
-    mg_pass<T, N, 2, true>(buf, sT, sS);
-    __syncthreads();
-    // divide by lam_x + lam_y + lam_z, by rows along x (FP32: times the
-    // correctly rounded reciprocal)
-    for (int row = threadIdx.x; row < EPB * m2; row += blockDim.x) {
-      const int le = row / m2, rr = row - le * m2;
-      const int b = rr % m, c = rr / m;
-      const T* L = sl + le * 3 * m;
-      const T lbc = L[m + b] + L[2 * m + c];
-      T* v = buf + le * BUF + P1 * b + P2 * c;
-#pragma unroll
-      for (int a = 0; a < m; ++a) {
-        if constexpr (sizeof(T) == 4) v[a] = v[a] * __frcp_rn(L[a] + lbc);
-        else v[a] = v[a] / (L[a] + lbc);
-      }
-    }
-    __syncthreads();
-    mg_pass<T, N, 0, false>(buf, sT, sS);
+    mg_pass_z<T, N>(buf, sT, sS, sl);
     __syncthreads();
     mg_pass<T, N, 1, false>(buf, sT, sS);
     __syncthreads();
-    mg_pass<T, N, 2, false>(buf, sT, sS);
+    mg_pass<T, N, 0, false>(buf, sT, sS);
     __syncthreads();
     // write the blocks (inactive points zero), by rows along x
     for (int row = threadIdx.x; row < EPB * m2; row += blockDim.x) {
