@@ -180,11 +180,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       float v;
       if (PCG) {
         v = sb[SV + ler * n3 + si] * sb[ler * n3 + si] + beta * su_e[si];
-        if (lane_ok) su_e[si] = v;
-        if (act) {
-          if (l2h) st_hint(pp + e * n3 + si, v, pol_first);
-          else pp[e * n3 + si] = v;
-        }
+        if (lane_ok) su_e[si] = v;   // p goes to memory with w in the epilogue
       } else {
         v = su_e[si];
       }
@@ -227,7 +223,11 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       if (act) {
         if (l2h) st_hint(wout + e * n3 + k * n2 + ij, wv, pol_last);
         else wout[e * n3 + k * n2 + ij] = wv;
-        if (PCG) acc.add(ureg[k], wv);
+        if (PCG) {
+          if (l2h) st_hint(pp + e * n3 + k * n2 + ij, ureg[k], pol_first);
+          else pp[e * n3 + k * n2 + ij] = ureg[k];
+          acc.add(ureg[k], wv);
+        }
       }
     }
     __syncthreads();   // stage st and sr/ss are free again
