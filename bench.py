@@ -656,8 +656,8 @@ def main():
             "clocks": clocks.summary(), "e2e": e2e,
             "autotune": {k: sem.sem_get_option(S.h, k) for k in
                          ("ax_variant", "ax_variant_pcg", "ax_tune_ms_plain_0", "ax_tune_ms_plain_1",
-                          "ax_tune_ms_plain_2", "ax_tune_ms_pcg_0", "ax_tune_ms_pcg_1",
-                          "ax_tune_ms_pcg_2", "l2_window_bytes", "l2_max_persist", "l2_max_window")},
+                          "ax_tune_ms_plain_2", "ax_tune_ms_plain_3", "ax_tune_ms_pcg_0",
+                          "ax_tune_ms_pcg_1", "ax_tune_ms_pcg_2", "ax_tune_ms_pcg_3")},
             "gpu_launches": launches,
         }
         if not args.no_mg:

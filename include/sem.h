@@ -278,7 +278,7 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
 
 /* Tuning knobs and diagnostics of the implementation (the paper has no
  * counterpart; they never change results beyond rounding).  Keys:
- *   "ax_variant", "ax_variant_pcg"  launch variant (0..2) of the bulk-copy
+ *   "ax_variant", "ax_variant_pcg"  launch variant (0..3) of the bulk-copy
  *                                   staged FP32 operator, plain / PCG mode;
  *                                   sem_setup's autotuner picks the fastest
  *   "use_tma"     1 (default) staged FP32 operator where it applies, 0 off

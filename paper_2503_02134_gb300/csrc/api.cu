@@ -487,7 +487,7 @@ int sem_set_option(sem_handle h, const char* key, int64_t value) {
     return SEM_EINVAL;
   }
   const std::string k(key);
-  if ((k == "ax_variant" || k == "ax_variant_pcg") && value >= 0 && value < 3) {
+  if ((k == "ax_variant" || k == "ax_variant_pcg") && value >= 0 && value < kTmaVariants) {
     (k == "ax_variant" ? h->ax_variant : h->ax_variant_pcg) = (int)value;
   } else if (k == "use_tma" && (value == 0 || value == 1)) {
     h->use_tma = value != 0;
@@ -541,9 +541,9 @@ int sem_get_option(sem_handle h, const char* key, double* value) {
     const int q = k == "kt_ms_ax" ? 0 : k == "kt_ms_gs" ? 1 : 2;
     *value = h->kt_iters ? h->kt_ms[q] / (double)h->kt_iters : 0.0;
   }
-  else if (k.rfind("ax_tune_ms_plain_", 0) == 0 && k.size() == 18 && k[17] >= '0' && k[17] <= '2')
+  else if (k.rfind("ax_tune_ms_plain_", 0) == 0 && k.size() == 18 && k[17] >= '0' && k[17] < '0' + kTmaVariants)
     *value = h->ax_tune_ms[0][k[17] - '0'];
-  else if (k.rfind("ax_tune_ms_pcg_", 0) == 0 && k.size() == 16 && k[15] >= '0' && k[15] <= '2')
+  else if (k.rfind("ax_tune_ms_pcg_", 0) == 0 && k.size() == 16 && k[15] >= '0' && k[15] < '0' + kTmaVariants)
     *value = h->ax_tune_ms[1][k[15] - '0'];
   else {
     set_error("sem_get_option: unknown key: " + k);

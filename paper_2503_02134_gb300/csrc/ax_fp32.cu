@@ -24,6 +24,7 @@ static int run32(Handle& h, const float* u, float* w, const AxPrologue* pro, int
       switch (v) {
         case 1: return tma_variant<n, 1>(h, u, w, pro, dm);
         case 2: return tma_variant<n, 2>(h, u, w, pro, dm);
+        case 3: return tma_variant<n, 3>(h, u, w, pro, dm);
         default: return tma_variant<n, 0>(h, u, w, pro, dm);
       }
     }

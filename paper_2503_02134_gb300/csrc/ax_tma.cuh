@@ -26,11 +26,12 @@ struct TmaShape {
   static constexpr int EPB_BIG = (128 / n2) > 0 ? (128 / n2) : 1;
   static constexpr int EPB_SMALL = (64 / n2) > 0 ? (64 / n2) : 1;
   static constexpr int EPB = V == 0 ? EPB_BIG : EPB_SMALL;
-  static constexpr int NS = V == 0 ? 2 : (V == 1 ? 3 : 4);     // bulk-copy stages
+  // bulk-copy stages: variant 0 two (two elements each), 1 three, 2 four,
+  // 3 two (one element each: more resident blocks, shallower prefetch)
+  static constexpr int NS = V == 0 ? 2 : (V == 1 ? 3 : (V == 2 ? 4 : 2));
   static constexpr int NT = ((n2 * EPB + 31) / 32) * 32;
   static constexpr uint32_t VEC = EPB * n3 * 4;                 // bytes of one vector per stage
 };
-constexpr int kTmaVariants = 3;
 
 template <int n, bool PCG, int V>
 constexpr size_t tma_smem_bytes() {

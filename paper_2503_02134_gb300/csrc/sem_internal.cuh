@@ -12,6 +12,7 @@
 namespace sem {
 
 constexpr int kMaxN = 15;
+constexpr int kTmaVariants = 4;   // launch variants of the bulk-copy staged FP32 operator
 constexpr int kMaxn = kMaxN + 1;
 
 // Per-iteration scalars of one PCG solve, resident on the device so that no

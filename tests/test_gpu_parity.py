@@ -417,11 +417,11 @@ def test_launch_variants_agree(sem):
     P = so.Problem(5, 4, 3, 7, deform=True)
     S = sem.Solver(5, 4, 3, 7, deform=True)
     for key in ("ax_variant", "ax_variant_pcg"):
-        assert sem.sem_get_option(S.h, key) in (0, 1, 2)
+        assert sem.sem_get_option(S.h, key) in (0, 1, 2, 3)
     assert sem.sem_get_option(S.h, "ax_tune_ms_plain_0") > 0
     u = cu(sem_inputs.uniform_local(P.L, seed=31, dtype=np.float32), torch.float32)
     outs = []
-    for v in range(3):
+    for v in range(4):
         sem.sem_set_option(S.h, "ax_variant", v)
         w = torch.empty_like(u)
         sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)
@@ -439,7 +439,7 @@ def test_launch_variants_agree(sem):
     sem.sem_rhs(S.h, sem.RHS_UNIFORM, 4, b)
     sem.sem_set_option(S.h, "use_tma", 1)
     xs = []
-    for v in range(3):
+    for v in range(4):
         sem.sem_set_option(S.h, "ax_variant_pcg", v)
         x, info = S.solve(b, tol=1e-9, maxit=3000, precision=sem.SEM_MIXED_FP32)
         assert info["rc"] == 0 and info["relres_true"] <= 1e-9
