@@ -253,7 +253,7 @@ int sem_batch_pcg_solve(sem_batch b, const double* const* f, double* const* x,
                         const sem_solve_opts* opts, sem_info* infos);
 /* keys: "work_items", "launches", "fused_problems" (problems whose
  * gather-scatter is folded into the update), and per GLL points per direction n (2..10,
- * even): "variant_n<n>", "grid_n<n>" (autotuned launch), "tune_ms_n<n>_v<0..2>" */
+ * even): "variant_n<n>", "grid_n<n>" (autotuned launch), "tune_ms_n<n>_v<0..3>" */
 int sem_batch_get_option(sem_batch b, const char* key, double* value);
 void sem_batch_destroy(sem_batch b);
 

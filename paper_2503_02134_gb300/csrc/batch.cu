@@ -273,6 +273,7 @@ int batch_ax_dispatch(int V, cudaStream_t st, int grid, const BatchProb* probs, 
   switch (V) {
     case 1: return batch_ax_launch<n, 1>(st, grid, probs, items, seg, err);
     case 2: return batch_ax_launch<n, 2>(st, grid, probs, items, seg, err);
+    case 3: return batch_ax_launch<n, 3>(st, grid, probs, items, seg, err);
     default: return batch_ax_launch<n, 0>(st, grid, probs, items, seg, err);
   }
 }
@@ -293,6 +294,7 @@ int batch_ax_occupancy_any(int n, int V, int* per_sm) {
   if (n == NN) {                                                 \
     if (V == 1) return batch_ax_occupancy<NN, 1>(per_sm);        \
     if (V == 2) return batch_ax_occupancy<NN, 2>(per_sm);        \
+    if (V == 3) return batch_ax_occupancy<NN, 3>(per_sm);        \
     return batch_ax_occupancy<NN, 0>(per_sm);                    \
   }
   SEM_OCC(2) SEM_OCC(4) SEM_OCC(6) SEM_OCC(8) SEM_OCC(10)
@@ -485,7 +487,7 @@ struct sem_batch_s {
   bool present[sem::kBatchOrders] = {};
   int variant[sem::kBatchOrders] = {};
   int grid[sem::kBatchOrders] = {};
-  float tune_ms[sem::kBatchOrders][3] = {};
+  float tune_ms[sem::kBatchOrders][sem::kTmaVariants] = {};
   std::vector<sem::BatchProb> probs_host;
   cudaGraphExec_t graph = nullptr;
   int graph_chunk = 0;
@@ -669,7 +671,7 @@ static int batch_autotune(sem_batch_s& b) {
     if (!b.present[q]) continue;
     const int n = 2 * q + 2;
     float best = 1e30f;
-    for (int V = 0; V < 3 && !rc; ++V) {
+    for (int V = 0; V < kTmaVariants && !rc; ++V) {
       for (int p = 0; p < b.count; ++p)
         if (b.subs[p]->n == n) batch_set_groups(b, p, batch_epb_of(n, V));
       SEM_CUDA(cudaMemcpyAsync(b.d_probs, b.probs_host.data(), sizeof(BatchProb) * b.count,
@@ -677,7 +679,7 @@ static int batch_autotune(sem_batch_s& b) {
       if ((rc = batch_compact(b, all))) break;
       int per_sm = 0;
       if ((rc = batch_ax_occupancy_any(n, V, &per_sm))) break;
-      per_sm = std::max(1, std::min(per_sm, 4));
+      per_sm = std::max(1, std::min(per_sm, 6));
       float best_v = 1e30f;
       for (int bps = 1; bps <= per_sm && !rc; ++bps) {
         const int grid = num_sms * bps;
@@ -896,7 +898,7 @@ extern "C" int sem_batch_get_option(sem_batch b, const char* key, double* value)
   else if (order_of("variant_n", &q)) *value = b->present[q] ? b->variant[q] : -1;
   else if (order_of("grid_n", &q)) *value = b->present[q] ? b->grid[q] : 0;
   else if (k.rfind("tune_ms_n", 0) == 0 && k.size() >= 13 && k[k.size() - 2] == 'v' &&
-           k[k.size() - 1] >= '0' && k[k.size() - 1] <= '2' &&
+           k[k.size() - 1] >= '0' && k[k.size() - 1] < '0' + kTmaVariants &&
            order_of("tune_ms_n", &q))
     *value = b->tune_ms[q][k[k.size() - 1] - '0'];
   else {
