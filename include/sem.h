@@ -127,8 +127,9 @@ typedef struct {
   int use_graph;         /* 0 (default) or 1: replay iteration chunks as CUDA graphs; -1: plain launches */
   int chunk;             /* iterations per convergence poll (default 32) */
   int precond;           /* 1 Jacobi (default), -1 identity, 2 multigrid (sem_mg_apply's
-                            V-cycle; FP64, or mixed with FP64 restarts of FP32 inner
-                            solves whose residual reduction is inner_tol, default 1e-4) */
+                            V-cycle; FP64, or mixed: reliable updates as for Jacobi,
+                            refine_mode 1 restarts FP32 inner solves whose residual
+                            reduction is inner_tol, default 1e-4) */
   double* history;       /* optional host array of maxit+1 recursive residuals (or NULL) */
   int refine_mode;       /* mixed only: 0 reliable updates (default): the FP64 true residual
                             replaces the FP32 one each time it fell by replace_factor, CG

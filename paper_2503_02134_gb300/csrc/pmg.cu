@@ -1149,8 +1149,78 @@ static int mg_cg(Handle& h, MgData& mg, const T* r0, T* d, double stop, int maxi
 // Multigrid-preconditioned solve of A x = f (x0 optional), FP64 or mixed.
 // Mixed: FP64 outer residual r64 = f - A64 x64; inner FP32 multigrid CG on
 // A d = r64 reducing ||r|| by max(inner_floor, 0.5 tol / relres); x64 += d.
+// Mixed multigrid CG with reliable updates (as the Jacobi solver's default):
+// one FP32 recursion on d with A d = r64; each time its residual has fallen
+// by `delta` (or reached the tolerance) d is folded into x64, the FP64 true
+// residual recomputed and copied into r32, and CG continues with the same
+// search direction.  Returns the iterations through *iters, replacements
+// through *repl; *relres is the final FP64 relative residual.
+static int mg_cg_reliable(Handle& h, MgData& mg, const double* f, double tol, double bnorm,
+                          int maxit, double delta, int max_repl, int* iters, int* repl,
+                          double* relres, double* rec) {
+  MgLevel& lv0 = mg.lv[0];
+  float* r = mg.r32;
+  float* z = mg.zz32;
+  float* p = mg.p32;
+  float* w = mg.w32;
+  float* d = mg.x32;
+  int rc;
+  const int g = grid_of(h, h.L);
+  *iters = 0;
+  *repl = 0;
+  if ((rc = launch_cast64to32(h, h.r64, r))) return rc;
+  SEM_CUDA(cudaMemsetAsync(d, 0, sizeof(float) * h.L, h.stream));
+  if ((rc = launch_glsc3(h, SEM_MIXED_FP32, r, r, mg.dot))) return rc;
+  double seg_ref = sqrt(read_dot(h, mg));
+  if ((rc = mg_vcycle<float>(mg, 0, r, z))) return rc;
+  if ((rc = launch_glsc3(h, SEM_MIXED_FP32, r, z, mg.dot))) return rc;
+  double rtz = read_dot(h, mg);
+  SEM_CUDA(cudaMemcpyAsync(p, z, sizeof(float) * h.L, cudaMemcpyDeviceToDevice, h.stream));
+  for (int it = 1; it <= maxit; ++it) {
+    if ((rc = mg_apply_a<float>(lv0, p, w))) return rc;
+    if ((rc = launch_glsc3(h, SEM_MIXED_FP32, w, p, mg.dot))) return rc;
+    const double pap = read_dot(h, mg);
+    if (!(pap > 0.0) || !(rtz > 0.0)) {
+      set_error("multigrid CG: breakdown (p.Ap or r.z not positive)");
+      return SEM_BREAKDOWN;
+    }
+    const double alpha = rtz / pap;
+    mg_axpby_kernel<float><<<g, 256, 0, h.stream>>>(h.L, (float)alpha, p, 1.f, d);
+    mg_axpby_kernel<float><<<g, 256, 0, h.stream>>>(h.L, (float)(-alpha), w, 1.f, r);
+    h.launches += 2;
+    SEM_CUDA(cudaGetLastError());
+    if ((rc = launch_glsc3(h, SEM_MIXED_FP32, r, r, mg.dot))) return rc;
+    const double rn = sqrt(read_dot(h, mg));
+    *iters = it;
+    *rec = rn / bnorm;
+    if (rn <= delta * seg_ref || rn <= tol * bnorm) {
+      // reliable update: fold d into x64, FP64 true residual replaces r32
+      if ((rc = launch_add32to64(h, h.x64, d))) return rc;
+      SEM_CUDA(cudaMemsetAsync(d, 0, sizeof(float) * h.L, h.stream));
+      if ((rc = fp64_residual(h, f, false, relres, nullptr))) return rc;
+      if (*relres <= tol) return 0;
+      if (++*repl > max_repl) return SEM_STAGNATED;
+      if ((rc = launch_cast64to32(h, h.r64, r))) return rc;
+      if ((rc = launch_glsc3(h, SEM_MIXED_FP32, r, r, mg.dot))) return rc;
+      seg_ref = sqrt(read_dot(h, mg));
+    }
+    if ((rc = mg_vcycle<float>(mg, 0, r, z))) return rc;
+    if ((rc = launch_glsc3(h, SEM_MIXED_FP32, r, z, mg.dot))) return rc;
+    const double rtz_new = read_dot(h, mg);
+    const double beta = rtz_new / rtz;
+    rtz = rtz_new;
+    mg_axpby_kernel<float><<<g, 256, 0, h.stream>>>(h.L, 1.f, z, (float)beta, p);
+    ++h.launches;
+    SEM_CUDA(cudaGetLastError());
+  }
+  if ((rc = launch_add32to64(h, h.x64, d))) return rc;
+  if ((rc = fp64_residual(h, f, false, relres, nullptr))) return rc;
+  return SEM_MAXIT;
+}
+
 int pcg_mg_solve(Handle& h, const double* f, const double* x0, double* x, double tol, int maxit,
-                 sem_precision prec, double inner_floor, int max_cycles, sem_info* info) {
+                 sem_precision prec, double inner_floor, int max_cycles, int refine_mode,
+                 double replace_factor, sem_info* info) {
   int rc;
   if ((rc = mg_ensure(h))) return rc;
   MgData& mg = *h.mg;
@@ -1175,6 +1245,17 @@ int pcg_mg_solve(Handle& h, const double* f, const double* x0, double* x, double
       if ((rc = fp64_residual(h, f, false, &relres, nullptr))) return rc;
       res.status = cg_rc == SEM_MAXIT ? SEM_MAXIT : 0;
       res.relres = rn / bnorm;
+    } else if (refine_mode == 0) {
+      int its = 0, repl = 0;
+      double rec = 0.0;
+      const double delta = replace_factor > 0 ? replace_factor : 1e-2;
+      const int st = mg_cg_reliable(h, mg, f, tol, bnorm, maxit, delta, 4 * max_cycles, &its,
+                                    &repl, &relres, &rec);
+      if (st < 0) return st;
+      total = its;
+      cycles = repl;
+      res.relres = rec;
+      res.status = st == SEM_MAXIT ? SEM_MAXIT : (st == SEM_STAGNATED ? SEM_STAGNATED : 0);
     } else {
       for (;;) {
         if (relres <= tol) break;

@@ -267,7 +267,8 @@ struct L2Window {
 };
 
 int pcg_mg_solve(Handle& h, const double* f, const double* x0, double* x, double tol, int maxit,
-                 sem_precision prec, double inner_floor, int max_cycles, sem_info* info);
+                 sem_precision prec, double inner_floor, int max_cycles, int refine_mode,
+                 double replace_factor, sem_info* info);
 
 int pcg_solve(Handle& h, const double* f, const double* x0, double* x, const sem_solve_opts& o,
               sem_info* info) {
@@ -279,7 +280,8 @@ int pcg_solve(Handle& h, const double* f, const double* x0, double* x, const sem
     }
     return pcg_mg_solve(h, f, x0, x, o.tol > 0 ? o.tol : 1e-8, o.maxit > 0 ? o.maxit : 1000,
                         o.precision, o.inner_tol > 0 ? o.inner_tol : 1e-4,
-                        o.max_cycles > 0 ? o.max_cycles : 20, info);
+                        o.max_cycles > 0 ? o.max_cycles : 20, o.refine_mode, o.replace_factor,
+                        info);
   }
   const double tol = o.tol > 0 ? o.tol : 1e-8;
   const int maxit = o.maxit > 0 ? o.maxit : 1000;

@@ -82,6 +82,12 @@ def test_mg_pcg_matches_oracle(sem, dims, N):
     xm, im = S.solve(bg, tol=1e-8, maxit=300, precision=sem.SEM_MIXED_FP32, precond="mg")
     assert im["rc"] == 0 and im["relres_true"] <= 1e-8
     assert P.true_relres(b, xm.cpu().numpy()) <= 1.0000001e-8
+    # reliable updates keep the search direction: about as many iterations
+    # as FP64; the restarted refinement (refine_mode 1) also converges
+    assert im["iters"] <= info["iters"] + max(5, info["iters"] // 5)
+    xr, ir = S.solve(bg, tol=1e-8, maxit=300, precision=sem.SEM_MIXED_FP32, precond="mg",
+                     refine_mode=1)
+    assert ir["rc"] == 0 and P.true_relres(b, xr.cpu().numpy()) <= 1.0000001e-8
     S.close()
 
 
