@@ -36,7 +36,7 @@ CPU_SAMPLE = dict(k=8, N=7, iters=12)
 # DRAM bytes (read + write) per local DOF of one launch, from an ncu capture
 # of the current kernels (the profile summaries under profiles/ give the
 # commands); None until measured for the kernel as it stands.
-TRAFFIC = {"operator_pcg": None, "operator_plain": None}
+TRAFFIC = {"operator_pcg": 42.75, "operator_plain": 31.16}
 
 
 class EnergyMeter:
