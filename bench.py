@@ -295,7 +295,7 @@ def mg_leg(sem, torch, S, b, stream):
             if best is None or inf["solve_ms"] < best["solve_ms"]:
                 best = inf
         out[name] = {"vcycle_ms": e0.elapsed_time(e1) / 5, "solve_ms": best["solve_ms"],
-                     "iterations": best["iters"], "restarts": best["refinements"],
+                     "iterations": best["iters"], "refinements": best["refinements"],
                      "relres_true": best["relres_true"], "converged": best["rc"] == 0}
     return out
 
