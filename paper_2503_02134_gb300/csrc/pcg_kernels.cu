@@ -195,8 +195,18 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
-template <int n, int DM, int ACC, int MINB>
-__global__ void __launch_bounds__(kVecThreads, MINB)
+// Launch shapes of the folded update: blocks per SM the register budget is
+// set for, and float4 groups per thread per trip (with two, both groups'
+// loads are issued before either is finished; the per-thread order of the
+// groups, and so of the dot sums, is the same).
+template <int VAR>
+struct UpdShape {
+  static constexpr int MINB = VAR == 0 ? 4 : (VAR == 1 ? 3 : (VAR == 2 ? 2 : 1));
+  static constexpr int GPT = (VAR == 1 || VAR == 2) ? 2 : 1;
+};
+
+template <int n, int DM, int ACC, int VAR>
+__global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
     cg_update32_gs_row4_kernel(float* __restrict__ x, float* __restrict__ r,
                                const float* __restrict__ p, const float* __restrict__ w,
                                const uint8_t* __restrict__ cw, const float* __restrict__ minv,
@@ -204,6 +214,7 @@ __global__ void __launch_bounds__(kVecThreads, MINB)
                                int64_t L, PcgScalars* __restrict__ s,
                                double* __restrict__ partials, double* __restrict__ hist,
                                int l2h) {
+  constexpr int GPT = UpdShape<VAR>::GPT;
   __shared__ double sh[kVecThreads / 32];
   if (s->done) return;
   const float alpha = (float)s->alpha;
@@ -213,23 +224,32 @@ __global__ void __launch_bounds__(kVecThreads, MINB)
   // with l2h the streams go through L2 evict-first, leaving w (written by
   // the operator evict-last) resident for the gathers
   const uint64_t pol = l2h ? l2_policy_evict_first() : 0ull;
-  auto step = [&](int64_t q) {
-    float4 xv, rv, pv, mv;
-    uchar4 cv;
+  struct Grp {
+    float4 x, r, p, m, w;
+    uchar4 c;
+  };
+  auto load = [&](int64_t q) {
+    Grp g;
     if (l2h) {
-      xv = ld_hint4_rw(reinterpret_cast<const float4*>(x) + q, pol);
-      rv = ld_hint4_rw(reinterpret_cast<const float4*>(r) + q, pol);
-      pv = ld_hint4(reinterpret_cast<const float4*>(p) + q, pol);
-      mv = ld_hint4(reinterpret_cast<const float4*>(minv) + q, pol);
-      cv = ld_hint_u8x4(reinterpret_cast<const uchar4*>(cw) + q, pol);
+      g.x = ld_hint4_rw(reinterpret_cast<const float4*>(x) + q, pol);
+      g.r = ld_hint4_rw(reinterpret_cast<const float4*>(r) + q, pol);
+      g.p = ld_hint4(reinterpret_cast<const float4*>(p) + q, pol);
+      g.m = ld_hint4(reinterpret_cast<const float4*>(minv) + q, pol);
+      g.c = ld_hint_u8x4(reinterpret_cast<const uchar4*>(cw) + q, pol);
     } else {
-      xv = reinterpret_cast<float4*>(x)[q];
-      rv = reinterpret_cast<float4*>(r)[q];
-      pv = __ldg(reinterpret_cast<const float4*>(p) + q);
-      mv = __ldg(reinterpret_cast<const float4*>(minv) + q);
-      cv = __ldg(reinterpret_cast<const uchar4*>(cw) + q);
+      g.x = reinterpret_cast<float4*>(x)[q];
+      g.r = reinterpret_cast<float4*>(r)[q];
+      g.p = __ldg(reinterpret_cast<const float4*>(p) + q);
+      g.m = __ldg(reinterpret_cast<const float4*>(minv) + q);
+      g.c = __ldg(reinterpret_cast<const uchar4*>(cw) + q);
     }
-    const float4 wv = gs_gather_row4<n, ACC>(w, q, faces, kx, kxky);
+    g.w = gs_gather_row4<n, ACC>(w, q, faces, kx, kxky);
+    return g;
+  };
+  auto finish = [&](int64_t q, Grp g) {
+    float4 xv = g.x, rv = g.r;
+    const float4 pv = g.p, wv = g.w, mv = g.m;
+    const uchar4 cv = g.c;
     xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
     rv.x -= alpha * wv.x; rv.y -= alpha * wv.y; rv.z -= alpha * wv.z; rv.w -= alpha * wv.w;
     if (l2h) {
@@ -245,8 +265,19 @@ __global__ void __launch_bounds__(kVecThreads, MINB)
     c = weight_of(cv.z) * rv.z; a_rr.add(c, rv.z); a_rz.add(c, mv.z * rv.z);
     c = weight_of(cv.w) * rv.w; a_rr.add(c, rv.w); a_rz.add(c, mv.w * rv.w);
   };
-  // one group per trip: the gathers already keep several loads in flight
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += stride) step(q);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += GPT * stride) {
+    if constexpr (GPT == 1) {
+      finish(q, load(q));
+    } else {
+      const int64_t q2 = q + stride;
+      const bool two = q2 < n4;
+      const Grp g1 = load(q);
+      Grp g2 = g1;
+      if (two) g2 = load(q2);
+      finish(q, g1);
+      if (two) finish(q2, g2);
+    }
+  }
   const double v0 = block_sum<DM>(a_rr.value(), sh);
   const double v1 = block_sum<DM>(a_rz.value(), sh);
   const double vals[2] = {v0, v1};
@@ -516,9 +547,11 @@ static void update_gs_dispatch(Handle& h, float* x, float* r, const float* p, co
   const int64_t kx = h.kx, kxky = (int64_t)h.kx * h.ky;
 #define SEM_UPD_ROW4(NN)                                                                  \
   case NN: {                                                                              \
-    auto kern = h.upd_minb == 4 ? cg_update32_gs_row4_kernel<NN, DM, ACC, 4>              \
-                                : cg_update32_gs_row4_kernel<NN, DM, ACC, 1>;             \
-    const int grid = fused_grid(h, kern, slot + (h.upd_minb == 4 ? 4 : 0));               \
+    auto kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 0>;                               \
+    if (h.upd_variant == 1) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 1>;            \
+    if (h.upd_variant == 2) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 2>;            \
+    if (h.upd_variant == 3) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 3>;            \
+    const int grid = fused_grid(h, kern, slot + 4 * h.upd_variant);                       \
     kern<<<grid, kVecThreads, 0, h.stream>>>(x, r, p, w, h.cw8, minv, h.bfaces, kx, kxky, \
                                              h.L, s, h.partials, hist, h.l2_hints ? 1 : 0); \
     return;                                                                               \

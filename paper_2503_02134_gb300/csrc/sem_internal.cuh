@@ -95,8 +95,8 @@ struct Handle {
   int gs_acc = 2;              // mixed-path accumulation: 2 TwoSum (default), 0 FP64, 1 FP32
   int fuse_gs = 1;             // FP32 PCG on box meshes: summation folded into the update
                                // (1: n a multiple of 4, 2: every n, 0: never)
-  int upd_gs_occ[8] = {};      // resident blocks per SM of the fused update kernels (0: not yet read)
-  int upd_minb = 4;            // fused update: minimum resident blocks the compiler targets (4 or 1)
+  int upd_gs_occ[16] = {};     // resident blocks per SM of the fused update kernels (0: not yet read)
+  int upd_variant = 0;         // fused update launch shape (0..3, see pcg_kernels.cu UpdShape)
 
   // Jacobi
   double* minv64 = nullptr;
