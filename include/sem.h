@@ -303,11 +303,9 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *                 accumulation "gs_acc" selects, which gives the separate
  *                 pass's bits; 2: folded for every n (slower than the
  *                 separate pass where n is not a multiple of 4); 0: separate pass
- *   "upd_variant" launch shape of the folded update kernel: 0 (default: a
- *                 register budget for four 256-thread blocks per SM, one
- *                 float4 group per thread per trip), 1 (three blocks, two
- *                 groups), 2 (two blocks, two groups), 3 (the compiler's
- *                 own register count, one group)
+ *   "upd_variant" register budget of the folded update kernel: 0 (default:
+ *                 four 256-thread blocks per SM), 1 (five), 2 (six), 3 (the
+ *                 compiler's own register count)
  *   "kernel_timing" 1: PCG solves run without graphs and time each
  *                 iteration's operator, gather-scatter and update launches
  *                 with CUDA events on the handle's stream (the events add

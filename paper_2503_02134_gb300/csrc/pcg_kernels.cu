@@ -195,14 +195,14 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
-// Launch shapes of the folded update: blocks per SM the register budget is
-// set for, and float4 groups per thread per trip (with two, both groups'
-// loads are issued before either is finished; the per-thread order of the
-// groups, and so of the dot sums, is the same).
+// Launch shapes of the folded update: the blocks per SM its register budget
+// is set for (the kernel is latency-bound on its gathers, so resident warps
+// count most; measured: two float4 groups per thread per trip at 2-3 blocks
+// were 40-50 % slower than one group at 4 blocks).
 template <int VAR>
 struct UpdShape {
-  static constexpr int MINB = VAR == 0 ? 4 : (VAR == 1 ? 3 : (VAR == 2 ? 2 : 1));
-  static constexpr int GPT = (VAR == 1 || VAR == 2) ? 2 : 1;
+  static constexpr int MINB = VAR == 0 ? 4 : (VAR == 1 ? 5 : (VAR == 2 ? 6 : 1));
+  static constexpr int GPT = 1;
 };
 
 template <int n, int DM, int ACC, int VAR>
