@@ -303,9 +303,10 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *                 accumulation "gs_acc" selects, which gives the separate
  *                 pass's bits; 2: folded for every n (slower than the
  *                 separate pass where n is not a multiple of 4); 0: separate pass
- *   "upd_variant" register budget of the folded update kernel: 0 (default:
- *                 four 256-thread blocks per SM), 1 (five), 2 (six), 3 (the
- *                 compiler's own register count)
+ *   "upd_variant" launch shape of the folded update kernel: register budget
+ *                 for 0 (default) four, 1 five, 2 six 256-thread blocks per
+ *                 SM; 3 four blocks and an L2 prefetch of each thread's next
+ *                 float4 group
  *   "kernel_timing" 1: PCG solves run without graphs and time each
  *                 iteration's operator, gather-scatter and update launches
  *                 with CUDA events on the handle's stream (the events add

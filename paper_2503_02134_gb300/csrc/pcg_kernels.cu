@@ -201,9 +201,15 @@ __global__ void __launch_bounds__(kVecThreads)
 // were 40-50 % slower than one group at 4 blocks).
 template <int VAR>
 struct UpdShape {
-  static constexpr int MINB = VAR == 0 ? 4 : (VAR == 1 ? 5 : (VAR == 2 ? 6 : 1));
+  static constexpr int MINB = VAR == 1 ? 5 : (VAR == 2 ? 6 : 4);
   static constexpr int GPT = 1;
+  // variant 3: four blocks, and an L2 prefetch of the next trip's streams
+  static constexpr bool PREFETCH = VAR == 3;
 };
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 template <int n, int DM, int ACC, int VAR>
 __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
@@ -266,6 +272,16 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
     c = weight_of(cv.w) * rv.w; a_rr.add(c, rv.w); a_rz.add(c, mv.w * rv.w);
   };
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += GPT * stride) {
+    if constexpr (UpdShape<VAR>::PREFETCH) {
+      const int64_t qn = q + stride;
+      if (qn < n4) {
+        prefetch_l2(reinterpret_cast<const float4*>(x) + qn);
+        prefetch_l2(reinterpret_cast<const float4*>(r) + qn);
+        prefetch_l2(reinterpret_cast<const float4*>(p) + qn);
+        prefetch_l2(reinterpret_cast<const float4*>(minv) + qn);
+        prefetch_l2(reinterpret_cast<const float4*>(w) + qn);
+      }
+    }
     if constexpr (GPT == 1) {
       finish(q, load(q));
     } else {
