@@ -303,6 +303,9 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *                 accumulation "gs_acc" selects, which gives the separate
  *                 pass's bits; 2: folded for every n (slower than the
  *                 separate pass where n is not a multiple of 4); 0: separate pass
+ *   "upd_tma"     1: the folded update at N = 7 stages its streams in shared
+ *                 memory by bulk copies (two stages, bounded waits) and reads
+ *                 only the other copies of shared nodes directly; 0 (default) off
  *   "upd_variant" launch shape of the folded update kernel: register budget
  *                 for 0 (default) four, 1 five, 2 six 256-thread blocks per
  *                 SM; 3 four blocks and an L2 prefetch of each thread's next

@@ -137,6 +137,42 @@ __device__ __forceinline__ float4 gs_gather_rows(const float* __restrict__ w, in
 // the copies across j and k faces are whole float4 rows of the neighbouring
 // elements; only the copies across i faces (components 0 and 3) are single
 // values.  Interior rows (no j or k face) take a short path.
+// As gs_gather_row4 below, with the group's own values supplied by the
+// caller (from shared memory in the staged update) and the element's face
+// bits f.
+template <int n, int ACC>
+__device__ __forceinline__ float4 gs_gather_row4_own(const float* __restrict__ w, int64_t q,
+                                                     uint8_t f, float4 own, int64_t kx,
+                                                     int64_t kxky) {
+  constexpr int n3 = n * n * n, g4 = n3 / 4, row4 = n / 4;
+  const int64_t e = q / g4;
+  const int rem = (int)(q - e * g4);
+  const int i0 = (rem % row4) * 4;
+  const int j = (rem / row4) % n;
+  const int k = rem / (row4 * n);
+  const int dy = (j == 0 && !(f & 4)) ? -1 : (j == n - 1 && !(f & 8)) ? 1 : 0;
+  const int dz = (k == 0 && !(f & 16)) ? -1 : (k == n - 1 && !(f & 32)) ? 1 : 0;
+  const bool xm = i0 == 0 && !(f & 1);
+  const bool xp = i0 + 3 == n - 1 && !(f & 2);
+  if (!(dy | dz)) {
+    float4 out = own;
+    if (xm) out.x = gs_sum2<ACC>(__ldg(w + 4 * q - n3 + (n - 1)), own.x);
+    if (xp) out.w = gs_sum2<ACC>(own.w, __ldg(w + 4 * q + 3 + n3 - (n - 1)));
+    return out;
+  }
+  const int64_t oy = (int64_t)dy * (kx * g4 - (int64_t)(n - 1) * row4);
+  const int64_t oz = (int64_t)dz * (kxky * g4 - (int64_t)(n - 1) * n * row4);
+  if (dy && dz) {
+    const int64_t ylo = dy < 0 ? oy : 0, yhi = dy > 0 ? oy : 0;
+    const int64_t zlo = dz < 0 ? oz : 0, zhi = dz > 0 ? oz : 0;
+    const int64_t ro[4] = {zlo + ylo, zlo + yhi, zhi + ylo, zhi + yhi};
+    return gs_gather_rows<4, n, ACC>(w, q, ro, own, xm, xp);
+  }
+  const int64_t o = dy ? oy : oz;
+  const int64_t ro[2] = {o < 0 ? o : 0, o > 0 ? o : 0};
+  return gs_gather_rows<2, n, ACC>(w, q, ro, own, xm, xp);
+}
+
 template <int n, int ACC>
 __device__ __forceinline__ float4 gs_gather_row4(const float* __restrict__ w, int64_t q,
                                                  const uint8_t* __restrict__ faces,

@@ -530,6 +530,161 @@ int launch_cg_update32(Handle& h, int dm, float* x, float* r, const float* p, co
 // Fold QQ^T into the update on box meshes; by default only where whole
 // float4 rows can be gathered (n a multiple of 4): the per-node gather of
 // other orders measured slower than the separate pass.
+// ---------------------------------------------------------------------------
+// Staged folded update (n = 8): the streams x, r, p, J^{-1}, w and the
+// multiplicity code of a group of EPB elements are brought into shared
+// memory by 1-D bulk copies, two stages deep, while the block works on the
+// previous group (the operator's pipeline: mbarrier completion, bounded
+// waits); only the other copies of shared nodes are read directly.  Same
+// arithmetic per value as cg_update32_gs_row4_kernel; the dot partial sums
+// follow the element groups instead of the grid-stride order.
+template <int n>
+struct UpdTmaShape {
+  static constexpr int n3 = n * n * n, G4 = n3 / 4;
+  static constexpr int EPB = 256 / G4 >= 1 ? 256 / G4 : 1;
+  static constexpr int NT = EPB * G4;
+  static constexpr int NS = 2;
+  static constexpr int SV = EPB * n3;                 // floats of one vector per stage
+  static constexpr size_t STAGE_BYTES = 5 * 4 * (size_t)SV + SV;   // x, r, p, J^-1, w + code
+  static constexpr size_t SMEM = NS * STAGE_BYTES + NS * 8 + 16;
+};
+
+template <int n, int DM, int ACC>
+__global__ void __launch_bounds__(UpdTmaShape<n>::NT, 4)
+    cg_update32_tma_kernel(float* __restrict__ x, float* __restrict__ r,
+                           const float* __restrict__ p, const float* __restrict__ w,
+                           const uint8_t* __restrict__ cw, const float* __restrict__ minv,
+                           const uint8_t* __restrict__ faces, int64_t E, int64_t kx,
+                           int64_t kxky, PcgScalars* __restrict__ s,
+                           double* __restrict__ partials, double* __restrict__ hist,
+                           int* __restrict__ err) {
+  using Sh = UpdTmaShape<n>;
+  constexpr int n3 = Sh::n3, G4 = Sh::G4, EPB = Sh::EPB, NS = Sh::NS, SV = Sh::SV;
+  extern __shared__ __align__(128) unsigned char upd_smem[];
+  float* const fbuf = reinterpret_cast<float*>(upd_smem);                 // [NS][5][SV]
+  uint8_t* const cbuf = upd_smem + (size_t)NS * 5 * SV * 4;               // [NS][SV]
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(cbuf + (size_t)NS * SV);
+  __shared__ double sh[Sh::NT / 32];
+  if (s->done) return;
+  const float alpha = (float)s->alpha;
+  DotAcc<float, DM> a_rr, a_rz;
+  const int tid = threadIdx.x;
+  const int64_t ngroups = (E + EPB - 1) / EPB;
+
+  auto issue = [&](int st, int64_t g) {
+    const int64_t e0 = g * EPB;
+    const int64_t cnt = E - e0 < EPB ? E - e0 : EPB;
+    const uint32_t vb = (uint32_t)(cnt * n3 * 4), cb = (uint32_t)(cnt * n3);
+    float* dst = fbuf + (size_t)st * 5 * SV;
+    mbar_arrive_expect_tx(&bar[st], 5 * vb + cb);
+    bulk_load(dst, x + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + SV, r + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + 2 * SV, p + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + 3 * SV, minv + e0 * n3, vb, &bar[st]);
+    bulk_load(dst + 4 * SV, w + e0 * n3, vb, &bar[st]);
+    bulk_load(cbuf + (size_t)st * SV, cw + e0 * n3, cb, &bar[st]);
+  };
+
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) {
+      const int64_t g0 = (int64_t)blockIdx.x + (int64_t)q * gridDim.x;
+      if (g0 < ngroups) issue(q, g0);
+    }
+  }
+  const int le = tid / G4, gq = tid - le * G4;
+  bool aborted = false;
+  int t = 0;
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, ++t) {
+    const int st = t % NS;
+    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((t / NS) & 1));
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    const int64_t e = g * EPB + le;
+    if (e < E) {
+      const float* sb = fbuf + (size_t)st * 5 * SV + le * n3 + 4 * gq;
+      float4 xv = *reinterpret_cast<const float4*>(sb);
+      float4 rv = *reinterpret_cast<const float4*>(sb + SV);
+      const float4 pv = *reinterpret_cast<const float4*>(sb + 2 * SV);
+      const float4 mv = *reinterpret_cast<const float4*>(sb + 3 * SV);
+      const float4 own = *reinterpret_cast<const float4*>(sb + 4 * SV);
+      const uchar4 cv =
+          *reinterpret_cast<const uchar4*>(cbuf + (size_t)st * SV + le * n3 + 4 * gq);
+      const int64_t q = e * G4 + gq;
+      const float4 wv = gs_gather_row4_own<n, ACC>(w, q, __ldg(faces + e), own, kx, kxky);
+      xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
+      rv.x -= alpha * wv.x; rv.y -= alpha * wv.y; rv.z -= alpha * wv.z; rv.w -= alpha * wv.w;
+      reinterpret_cast<float4*>(x)[q] = xv;
+      reinterpret_cast<float4*>(r)[q] = rv;
+      float c;
+      c = weight_of(cv.x) * rv.x; a_rr.add(c, rv.x); a_rz.add(c, mv.x * rv.x);
+      c = weight_of(cv.y) * rv.y; a_rr.add(c, rv.y); a_rz.add(c, mv.y * rv.y);
+      c = weight_of(cv.z) * rv.z; a_rr.add(c, rv.z); a_rz.add(c, mv.z * rv.z);
+      c = weight_of(cv.w) * rv.w; a_rr.add(c, rv.w); a_rz.add(c, mv.w * rv.w);
+    }
+    __syncthreads();   // stage st is free again
+    if (tid == 0) {
+      const int64_t gn = g + NS * (int64_t)gridDim.x;
+      if (gn < ngroups) {
+        fence_proxy_async_smem();
+        issue(st, gn);
+      }
+    }
+  }
+
+  if (aborted) {
+    // A bulk copy never completed: report it, give the copies this block
+    // still has in flight a bounded time to land, and leave without
+    // publishing a partial sum.
+    if (tid == 0) {
+      atomicExch(err, 1);
+      const int64_t g_abort = blockIdx.x + (int64_t)t * gridDim.x;
+      for (int s2 = 0; s2 < NS; ++s2) {
+        const int64_t g_out = g_abort + (int64_t)((s2 - t % NS + NS) % NS) * gridDim.x;
+        const int done_uses = t > s2 ? (t - 1 - s2) / NS + 1 : 0;
+        if (g_out < ngroups) mbar_wait_bounded(&bar[s2], (uint32_t)(done_uses & 1));
+      }
+    }
+    return;
+  }
+  const double v0 = block_sum<DM>(a_rr.value(), sh);
+  const double v1 = block_sum<DM>(a_rz.value(), sh);
+  const double vals[2] = {v0, v1};
+  if (publish_and_elect(vals, 2, partials, &s->counter[1])) {
+    const double rtr = reduce_partials<DM>(partials, 0, sh);
+    const double rtz = reduce_partials<DM>(partials, 1, sh);
+    if (threadIdx.x == 0) {
+      finish_iteration(s, rtr, rtz, hist);
+      s->counter[1] = 0u;
+    }
+  }
+}
+
+template <int DM, int ACC>
+static int update_tma_launch(Handle& h, float* x, float* r, const float* p, const float* w,
+                             const float* minv, PcgScalars* s, double* hist) {
+  using Sh = UpdTmaShape<8>;
+  auto kern = cg_update32_tma_kernel<8, DM, ACC>;
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
+  int per_sm = 0;
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::NT, Sh::SMEM));
+  const int64_t groups = (h.E + Sh::EPB - 1) / Sh::EPB;
+  int64_t cap = (int64_t)h.num_sms * std::max(per_sm, 1);
+  if (cap > h.max_blocks) cap = h.max_blocks;
+  const int grid = (int)std::max<int64_t>(1, std::min(groups, cap));
+  kern<<<grid, Sh::NT, Sh::SMEM, h.stream>>>(x, r, p, w, h.cw8, minv, h.bfaces, h.E, h.kx,
+                                             (int64_t)h.kx * h.ky, s, h.partials, hist,
+                                             h.dev_err);
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
 bool gs_fusable(const Handle& h) {
   if (h.gid_user || h.n < 2 || h.fuse_gs == 0) return false;
   return h.fuse_gs == 2 || h.n % 4 == 0;
@@ -561,6 +716,11 @@ template <int DM, int ACC>
 static void update_gs_dispatch(Handle& h, float* x, float* r, const float* p, const float* w,
                                const float* minv, PcgScalars* s, double* hist, int slot) {
   const int64_t kx = h.kx, kxky = (int64_t)h.kx * h.ky;
+  if (h.upd_tma && h.n == 8) {
+    // bulk-copy staged variant (its launch errors surface at the next check)
+    update_tma_launch<DM, ACC>(h, x, r, p, w, minv, s, hist);
+    return;
+  }
 #define SEM_UPD_ROW4(NN)                                                                  \
   case NN: {                                                                              \
     auto kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 0>;                               \

@@ -97,6 +97,7 @@ struct Handle {
                                // (1: n a multiple of 4, 2: every n, 0: never)
   int upd_gs_occ[16] = {};     // resident blocks per SM of the fused update kernels (0: not yet read)
   int upd_variant = 0;         // fused update launch shape (0..3, see pcg_kernels.cu UpdShape)
+  bool upd_tma = false;        // fused update (n = 8): bulk-copy staged variant
 
   // Jacobi
   double* minv64 = nullptr;

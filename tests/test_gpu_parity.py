@@ -373,6 +373,31 @@ def test_fused_gather_scatter_large_mesh(sem):
     S.close()
 
 
+@pytest.mark.parametrize("dims", [(3, 2, 2), (7, 5, 3)])
+def test_staged_update_matches_folded(sem, dims):
+    """The bulk-copy staged update (N = 7) computes every value as the
+    folded update does; only the order of the dot partial sums differs, so
+    the solves agree to rounding and converge alike (odd element counts
+    leave a partial last group)."""
+    S = sem.Solver(*dims, 7, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 9, b)
+    for prec, kw in ((sem.SEM_MIXED_FP32, dict(tol=1e-9, maxit=3000)),
+                     (sem.SEM_FP32_ALL, dict(fixed_iters=30))):
+        sem.sem_set_option(S.h, "upd_tma", 0)
+        x0, i0 = S.solve(b, precision=prec, **kw)
+        sem.sem_set_option(S.h, "upd_tma", 1)
+        x1, i1 = S.solve(b, precision=prec, **kw)
+        if "tol" in kw:
+            assert i1["rc"] == 0 and i1["relres_true"] <= 1e-9
+            assert abs(i1["iters"] - i0["iters"]) <= 2
+            assert rel_maxerr(x1.cpu(), x0.cpu()) < 1e-7
+        else:
+            assert rel_maxerr(x1.cpu(), x0.cpu()) < 1e-4
+    sem.sem_set_option(S.h, "upd_tma", 0)
+    S.close()
+
+
 def test_l2_options_change_no_bits(sem):
     """L2 residency controls (access-policy window, per-access eviction
     hints) change where data lives, not the arithmetic."""
