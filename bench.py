@@ -343,6 +343,19 @@ def learned_leg(sem, torch, train_pairs=128, epochs=20):
     return res
 
 
+def reduce_over_ranks(ms_local, iters_local, world, dist, device):
+    """Whole-job timing over the ranks: the slowest rank's time and the
+    iterations all ranks did (each rank solves its own problem)."""
+    if world == 1:
+        return ms_local, iters_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(iters_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(float(u.item())))
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -497,13 +510,10 @@ def main():
         if world > 1:
             dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms = ms_total / args.steps
     iters = sum(i["iters"] for i in infos)
-    units = L * iters * world
+    ms_total, iters_all = reduce_over_ranks(ms_total, iters, world, dist, "cuda")
+    ms = ms_total / args.steps
+    units = L * iters_all
     value = units / (ms_total * 1e-3) / 1e9
     launches = sum(i["launches"] for i in infos)
     ok = all(i["rc"] == 0 and i["relres_true"] <= W["tol"] * 1.0000001 for i in infos)
