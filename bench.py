@@ -398,7 +398,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the order sweep N = 5..15")
     ap.add_argument("--no-mg", action="store_true", help="skip the multigrid-preconditioner leg")
     ap.add_argument("--profile", action="store_true",
-                    help="small run for ncu captures: 3 fixed mixed iterations + 2 FP32 operator calls")
+                    help="small run for ncu captures: 3 fixed mixed iterations, 2 FP32 operator calls, "
+                         "1 FP64 operator call")
     ap.add_argument("--profile-mg", action="store_true",
                     help="ncu run of the multigrid preconditioner: one FP32 and one FP64 V-cycle "
                          "on the benchmark mesh inside the NVTX range mg_cycle")
@@ -487,11 +488,14 @@ def main():
             u = torch.rand(L, dtype=torch.float32, device="cuda",
                            generator=torch.Generator(device="cuda").manual_seed(1))
             w = torch.empty_like(u)
+            u64 = u.double()
+            w64 = torch.empty_like(u64)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("bench_profile")
         S.solve(b, fixed_iters=3, precision=sem.SEM_MIXED_FP32, x=x, use_graph=False, chunk=3)
         for _ in range(2):
             sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)
+        sem.sem_ax_local(S.h, u64, w64, sem.SEM_FP64)      # the FP64 operator, once
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         S.close()
