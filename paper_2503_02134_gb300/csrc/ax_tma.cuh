@@ -37,7 +37,7 @@ template <int n, bool PCG, int V>
 constexpr size_t tma_smem_bytes() {
   using S = TmaShape<n, V>;
   constexpr int NV = PCG ? 3 : 1;
-  return S::NS * (size_t)(NV + 6) * S::VEC + 2 * (size_t)S::VEC + S::NS * sizeof(uint64_t);
+  return S::NS * (size_t)(NV + 6) * S::VEC + S::NS * sizeof(uint64_t);
 }
 
 // Dot product of a row of n contiguous shared-memory floats (16- or 8-byte
@@ -83,9 +83,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   constexpr int STAGE = (NV + 6) * SV;         // floats per stage
   extern __shared__ __align__(128) float smem_f[];
   float* const stage0 = smem_f;
-  float* const sr = smem_f + NS * STAGE;
-  float* const ss = sr + SV;
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(ss + SV);
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + NS * STAGE);
   __shared__ float sD[n][n + 1];
   __shared__ double sh_red[S::NT / 32];
 
@@ -168,8 +166,12 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     float* const su = PCG ? sb + 2 * SV : sb;   // p (formed in place) or u
     const float* const Gs = sb + NV * SV + ler * 6 * n3 + ij;
     float* const su_e = su + ler * n3;
-    float* const sr_e = sr + ler * n3;
-    float* const ss_e = ss + ler * n3;
+    // the two transposed-contraction inputs overwrite G1 and G2 of the
+    // stage: each thread reads its own G entries (k, ij) before it writes
+    // the same positions, and the stage is refilled only after the last
+    // barrier of the group
+    float* const sr_e = sb + NV * SV + ler * 6 * n3;
+    float* const ss_e = sr_e + n3;
     const int64_t e = g * EPB + le;
     const bool act = lane_ok && e < E;
     const uint8_t f = act ? faces[e] : uint8_t(0);   // issued early, used in the epilogue
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         }
       }
     }
-    __syncthreads();   // stage st and sr/ss are free again
+    __syncthreads();   // stage st is free again
     if (tid == 0) {
       const int64_t gn = g + NS * (int64_t)gridDim.x;
       if (gn < ngroups) {

@@ -65,9 +65,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   const int off = seg[0], nitems = seg[1];
   extern __shared__ __align__(128) float smem_f[];
   float* const stage0 = smem_f;
-  float* const sr = smem_f + NS * STAGE;
-  float* const ss = sr + SV;
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(ss + SV);
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + NS * STAGE);
   __shared__ float sD[n][n + 1];
   __shared__ double sh_red[S::NT / 32];
   __shared__ int2 s_item[NS];   // item staged on each stage ({-1, -1} = none)
@@ -159,8 +157,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       float* const sb = stage0 + st * STAGE;
       float* const su_e = sb + 2 * SV + ler * n3;
       const float* const Gs = sb + 3 * SV + ler * 6 * n3 + ij;
-      float* const sr_e = sr + ler * n3;
-      float* const ss_e = ss + ler * n3;
+      // transposed-contraction inputs over G1, G2 of the stage (each thread
+      // reads its own entries there before writing them)
+      float* const sr_e = sb + 3 * SV + ler * 6 * n3;
+      float* const ss_e = sr_e + n3;
       const int64_t e = (int64_t)itm.y * EPB + le;
       const bool act = lane_ok && e < sP.E;
       const uint8_t f = act ? sP.faces[e] : uint8_t(0);
@@ -243,8 +243,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
 template <int n, int V>
 constexpr size_t batch_smem_bytes() {
   using S = TmaShape<n, V>;
-  return sizeof(float) * ((size_t)S::NS * 9 * S::EPB * S::n3 + 2 * S::EPB * S::n3) +
-         S::NS * sizeof(uint64_t);
+  return sizeof(float) * (size_t)S::NS * 9 * S::EPB * S::n3 + S::NS * sizeof(uint64_t);
 }
 
 template <int n, int V>
