@@ -373,6 +373,27 @@ def test_fused_gather_scatter_large_mesh(sem):
     S.close()
 
 
+@pytest.mark.parametrize("dims,N", [((3, 2, 2), 7), ((5, 4, 3), 3), ((2, 2, 3), 11),
+                                    ((2, 1, 2), 15)])
+def test_update_variants(sem, dims, N):
+    """Launch shapes of the folded update (register budgets for four, five,
+    six blocks per SM; an L2 prefetch of the next group) traverse the
+    vectors in the same order -- on these small meshes with the same grid --
+    so they give the same bits."""
+    S = sem.Solver(*dims, N, deform=True)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs(S.h, sem.RHS_UNIFORM, 3, b)
+    mixed = sem.SEM_MIXED_FP32
+    ref, iref = S.solve(b, tol=1e-9, maxit=3000, precision=mixed)
+    assert iref["rc"] == 0 and iref["relres_true"] <= 1e-9
+    for v in (1, 2, 3):
+        sem.sem_set_option(S.h, "upd_variant", v)
+        assert sem.sem_get_option(S.h, "upd_variant") == v
+        x, info = S.solve(b, tol=1e-9, maxit=3000, precision=mixed)
+        assert info["iters"] == iref["iters"] and torch.equal(x, ref), v
+    S.close()
+
+
 @pytest.mark.parametrize("dims", [(3, 2, 2), (7, 5, 3)])
 def test_staged_update_matches_folded(sem, dims):
     """The bulk-copy staged update (N = 7) computes every value as the
