@@ -40,7 +40,7 @@ _ORACLE_PROBLEMS = {}
 # DRAM bytes (read + write) per local DOF of one launch, from an ncu capture
 # of the current kernels (the profile summaries under profiles/ give the
 # commands); None until measured for the kernel as it stands.
-TRAFFIC = {"operator_pcg": 42.64, "operator_plain": 31.13}
+TRAFFIC = {"operator_pcg": 42.64, "operator_plain": 31.13, "operator_fp64": 63.28}
 
 
 class EnergyMeter:
@@ -76,6 +76,17 @@ def peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def fp64_peak(num_sms):
+    """FP64 FMA peak of the GPU in TFLOP/s: SMs x 4 flop per clock (two FP64
+    FMAs per SM and clock, the rate behind GB300's nominal 1.25 TFLOP/s) x
+    the maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
+    return num_sms * 4 * mhz * 1e6 / 1e12, f"derived: {num_sms} SMs x 4 FP64 flop/clock x {mhz:.0f} MHz"
 
 
 class Clocks:
@@ -637,6 +648,20 @@ def main():
                       "algorithmic_bytes_per_launch": L * bytes_plain, "launch_ms": ax32_ms,
                       "peak_source": peak_source}
 
+    # the FP64 operator is bound by the FP64 pipe: 12 n^4 + 15 n^3 flop per
+    # element (three derivative and three transposed contractions, the
+    # symmetric 3x3 geometric product)
+    n_gll = W["N"] + 1
+    flops64 = S.E * (12 * n_gll ** 4 + 15 * n_gll ** 3)
+    ach64 = flops64 / (ax64_ms * 1e-3) / 1e12
+    peak64, peak64_source = fp64_peak(torch.cuda.get_device_properties(0).multi_processor_count)
+    traffic64 = TRAFFIC.get("operator_fp64")
+    roofline_fp64 = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                     "frac": ach64 / peak64, "traffic": traffic64 * L if traffic64 else None,
+                     "kernel": f"ax_kernel<{n_gll},double> (sem_ax_local, FP64 operator)",
+                     "algorithmic_flops_per_launch": flops64, "launch_ms": ax64_ms,
+                     "peak_source": peak64_source}
+
     # end to end through the C-ABI with host (pinned) buffers
     fh = torch.empty(L, dtype=torch.float64, pin_memory=True)
     fh.copy_(b.cpu())
@@ -675,6 +700,7 @@ def main():
             "ax_gdofs_fp32_with_gs": L / (ax32_full_ms * 1e-3) / 1e9,
             "ax_gdofs_fp64": L / (ax64_ms * 1e-3) / 1e9,
             "roofline": roofline, "roofline_operator_plain": roofline_plain,
+            "roofline_operator_fp64": roofline_fp64,
             "kernel_ms": {"operator_pcg": kt["kt_ms_ax"], "gather_scatter": kt["kt_ms_gs"],
                           "update": kt["kt_ms_update"]},
             "kernel_share_of_step": shares,
