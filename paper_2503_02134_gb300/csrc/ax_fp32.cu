@@ -66,9 +66,9 @@ int launch_scal_setup(Handle& h, PcgScalars* s, double tol, int maxit, int fixed
 // with CUDA events and keeps the fastest.  Runs once, at set-up.
 int autotune_ax32(Handle& h) {
   if (!(h.n % 2 == 0 && h.n <= 10) || !h.use_tma) return 0;
-  cudaEvent_t a, b;
-  SEM_CUDA(cudaEventCreate(&a));
-  SEM_CUDA(cudaEventCreate(&b));
+  ScopedEvents ev;
+  SEM_CUDA(ev.create());
+  cudaEvent_t a = ev.a, b = ev.b;
   // positive data (0x3f3f3f3f ~ 0.747) so the PCG-mode pap stays positive
   SEM_CUDA(cudaMemsetAsync(h.b32, 0x3f, sizeof(float) * h.L, h.stream));
   SEM_CUDA(cudaMemsetAsync(h.x32, 0x3f, sizeof(float) * h.L, h.stream));
@@ -100,8 +100,6 @@ int autotune_ax32(Handle& h) {
     }
     if (mode == 0) h.ax_variant = best_v; else h.ax_variant_pcg = best_v;
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
   if (!rc) rc = launch_scal_setup(h, h.scal_aux, 0.0, 1, 0, 0);
   return rc;
 }

@@ -654,9 +654,9 @@ static void batch_set_groups(sem_batch_s& b, int p, int epb) {
 // the batch's own work list; the fastest is kept.
 static int batch_autotune(sem_batch_s& b) {
   const int num_sms = b.subs[0]->num_sms;
-  cudaEvent_t e0, e1;
-  SEM_CUDA(cudaEventCreate(&e0));
-  SEM_CUDA(cudaEventCreate(&e1));
+  ScopedEvents ev;
+  SEM_CUDA(ev.create());
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   for (int p = 0; p < b.count; ++p) {
     Handle& h = *b.subs[p];
     SEM_CUDA(cudaMemsetAsync(h.r32, 0x3f, sizeof(float) * h.L, b.stream));
@@ -705,8 +705,6 @@ static int batch_autotune(sem_batch_s& b) {
     for (int p = 0; p < b.count; ++p)
       if (b.subs[p]->n == n) batch_set_groups(b, p, batch_epb_of(n, b.variant[q]));
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (rc) return rc;
   SEM_CUDA(cudaMemcpyAsync(b.d_probs, b.probs_host.data(), sizeof(BatchProb) * b.count,
                            cudaMemcpyHostToDevice, b.stream));

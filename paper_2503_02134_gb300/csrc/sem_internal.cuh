@@ -153,6 +153,20 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::sem::cuda_fail(_e, #call); \
   } while (0)
 
+// Two timing events, destroyed when the scope ends (early error returns
+// included).
+struct ScopedEvents {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&a);
+    return e == cudaSuccess ? cudaEventCreate(&b) : e;
+  }
+  ~ScopedEvents() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
 // ------------------------------------------------------------------ launchers
 // setup_kernels.cu
 int launch_gll(Handle& h);
