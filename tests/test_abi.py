@@ -50,3 +50,33 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     lib.sem_ax.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int]
     assert lib.sem_ax(None, None, None, 0) == sem.SEM_EINVAL
     assert "invalid" in sem.sem_last_error()
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/sem.h compiles as strict C99, a C program links every declared
+    entry point against the library, and a call with a null handle returns
+    SEM_EINVAL with a message (no GPU touched)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    import __graft_entry__
+    so = __graft_entry__._build_module().LIB
+    refs = ",\n".join(f"    (void (*)(void)){n}" for n in declared_functions())
+    prog = tmp_path / "abi_check.c"
+    prog.write_text(
+        '#include "sem.h"\n#include <stdio.h>\n'
+        "int main(void) {\n"
+        f"  void (*fns[])(void) = {{\n{refs}\n  }};\n"
+        "  int rc = sem_ax((sem_handle)0, 0, 0, SEM_FP64);\n"
+        '  printf("%d %d %s\\n", (int)(sizeof(fns) / sizeof(fns[0])), rc, sem_last_error());\n'
+        "  return rc == SEM_EINVAL ? 0 : 1;\n}\n")
+    exe = tmp_path / "abi_check"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(prog), so,
+                    "-Wl,-rpath," + os.path.dirname(so), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
+    count, rc, msg = out.stdout.split(" ", 2)
+    assert int(count) == len(declared_functions()) and int(rc) == -1 and "invalid" in msg
