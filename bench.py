@@ -8,7 +8,8 @@ uniform in [-1, 1) per global node (seed 0), inputs resident in HBM.
 `value` = local DOFs x PCG iterations / step time (GDOF/s), summed over ranks.
 
 Extra keys: time to solution (mixed and FP64), the FP32 and FP64 operator
-throughput, the roofline of the dominant kernel (the FP32 element operator),
+throughput, the roofline of the dominant kernel (the FP32 element operator)
+and of the plain FP32 and the FP64 operators,
 the clocks seen during the timed region, the end-to-end number through the
 C-ABI with host buffers, and the CPU oracle timed on a bounded sample.
 
@@ -32,9 +33,8 @@ METRIC = "Ax GDOF/s + PCG time-to-1e-8 residual, mixed/learned vs FP64, 1 GB300"
 WORKLOAD = dict(kx=32, ky=32, kz=32, N=7, deform=True, rhs="uniform[-1,1) per global node, seed 0",
                 tol=1e-8)
 WORKLOAD_NAME = "deformed 32x32x32 hex, N=7 (16.8M local DOFs), Jacobi PCG to 1e-8, mixed FP32/FP64"
-# a bounded sample of the same work for the CPU oracle: 8x8x8 elements, N = 7, deformed
 # the CPU oracle's sample: the benchmark workload itself (deformed 32^3, N = 7),
-# a few FP64 Jacobi PCG iterations (about 4 s each on one core)
+# a few FP64 Jacobi PCG iterations (1.4 to 4 s each on one core)
 CPU_SAMPLE = dict(k=32, N=7, iters=4)
 _ORACLE_PROBLEMS = {}
 # DRAM bytes (read + write) per local DOF of one launch, from an ncu capture
