@@ -1,6 +1,6 @@
 """p-multigrid preconditioner with overlapping Schwarz smoothing (CPU oracle, numpy FP64).
 
-TEST INFRASTRUCTURE ONLY (tests and the benchmark's CPU leg).
+TEST INFRASTRUCTURE ONLY (tests, the smoke check and the benchmark's CPU legs).
 
 The paper runs Nekbone both without and with its multigrid preconditioner
 (Sec. 3.1, profiling table: `solveM` takes 70 % of the time when enabled;
