@@ -26,6 +26,10 @@ def test_gll_closed_forms():
     s = 1 / math.sqrt(5)
     np.testing.assert_allclose(x, [-1, -s, s, 1], atol=1e-15)
     np.testing.assert_allclose(w, [1 / 6, 5 / 6, 5 / 6, 1 / 6], rtol=1e-14)
+    x, w = so.gll(4)                       # nodes 0, +-sqrt(3/7), +-1
+    s = math.sqrt(3 / 7)
+    np.testing.assert_allclose(x, [-1, -s, 0, s, 1], atol=1e-15)
+    np.testing.assert_allclose(w, [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10], rtol=1e-14)
 
 
 @pytest.mark.parametrize("N", list(range(1, 19)))
