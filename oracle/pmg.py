@@ -26,9 +26,16 @@ the spirit of Nekbone's hybrid Schwarz multigrid, is:
     subdomain corrections are summed with symmetric weights 1/sqrt(c), c the
     number of blocks holding the node -- the square root the paper moves to
     FP64 -- and damped by omega = 1/lambda_max(S A) (power iteration);
+  * h-levels below the N = 1 level: while kx, ky, kz are all even and their
+    halves all at least 2, the next level is the N = 1 discretisation of the
+    box with kx/2 x ky/2 x kz/2 elements (same domain and deformation, each
+    coarse element holding 2 x 2 x 2 fine ones); prolongation = trilinear
+    interpolation of the coarse element's eight vertex values at the fine
+    nodes (reference positions 0, 1/2, 1), restriction its adjoint on unique
+    nodes; the h-levels use the same smoother;
   * cycle: symmetric V-cycle (pre-smooth, coarse correction, post-smooth);
-    the coarsest level (N = 1) applies the smoother only (no global coarse
-    solve), so the preconditioner is linear, symmetric and positive definite.
+    the coarsest level applies the smoother only (no direct coarse solve),
+    so the preconditioner is linear, symmetric and positive definite.
 
 On an undeformed uniform mesh the separable local operator equals the
 assembled stiffness matrix restricted to the block, so each local solve is
@@ -49,6 +56,21 @@ def level_orders(N):
     while out[-1] > 1:
         out.append(max(1, out[-1] // 2))
     return out
+
+
+def h_levels(kx, ky, kz):
+    """Mesh sizes of the h-levels below the N = 1 level, finest first."""
+    out = []
+    while kx % 2 == 0 and ky % 2 == 0 and kz % 2 == 0 and min(kx, ky, kz) >= 4:
+        kx, ky, kz = kx // 2, ky // 2, kz // 2
+        out.append((kx, ky, kz))
+    return out
+
+
+# trilinear interpolation inside a coarse element: H[s][i][a] = weight of
+# coarse vertex a (0, 1) at fine node i (0, 1) of the fine element in half s
+_H = np.array([[[1.0, 0.0], [0.5, 0.5]],
+               [[0.5, 0.5], [0.0, 1.0]]])
 
 
 def interp_matrix(Nc, Nf):
@@ -226,10 +248,14 @@ class Level:
 class PMG:
     """The V-cycle preconditioner over all levels of a box problem."""
 
-    def __init__(self, kx, ky, kz, N, deform=False, power_iters=20, seed=12345):
+    def __init__(self, kx, ky, kz, N, deform=False, power_iters=20, seed=12345, hcoarsen=True):
         self.levels = [Level(kx, ky, kz, Nl, deform) for Nl in level_orders(N)]
         self.J = [interp_matrix(self.levels[l + 1].N, self.levels[l].N)
                   for l in range(len(self.levels) - 1)]
+        self.n_p = len(self.levels)          # levels 0 .. n_p-1: orders N .. 1
+        if hcoarsen:
+            for dims in h_levels(kx, ky, kz):
+                self.levels.append(Level(*dims, 1, deform))
         for lev in self.levels:
             lev.omega = 1.0 / self.lambda_max(lev, power_iters, seed)
 
@@ -249,15 +275,37 @@ class PMG:
             x = y / math.sqrt(P.glsc3(y, y))
         return lam
 
+    def _children(self, l):
+        """h-pair (l, l+1): for every fine element its coarse element and
+        its half (sx, sy, sz) in each direction."""
+        f, c = self.levels[l].P, self.levels[l + 1].P
+        e = np.arange(f.E)
+        ex, ey, ez = e % f.kx, (e // f.kx) % f.ky, e // (f.kx * f.ky)
+        ce = ex // 2 + c.kx * (ey // 2 + c.ky * (ez // 2))
+        return ce, ex % 2, ey % 2, ez % 2
+
     def prolong(self, l, zc):
         """Coarse level l+1 -> fine level l, element by element."""
         f, c = self.levels[l], self.levels[l + 1]
+        if l + 1 >= self.n_p:
+            # trilinear: fine node (i, j, k) of the child in half (sx, sy, sz)
+            ce, sx, sy, sz = self._children(l)
+            u = zc.reshape(c.P.E, 2, 2, 2)[ce]                   # [Ef, c, b, a]
+            out = np.einsum('eia,ejb,ekc,ecba->ekji', _H[sx], _H[sy], _H[sz], u)
+            return out.reshape(-1)
         u = zc.reshape(c.P.E, c.n, c.n, c.n)
         return _apply3(self.J[l], u).reshape(-1)
 
     def restrict(self, l, r):
         """Fine level l -> coarse level l+1: P^T on unique nodes."""
         f, c = self.levels[l], self.levels[l + 1]
+        if l + 1 >= self.n_p:
+            ce, sx, sy, sz = self._children(l)
+            u = (r / f.P.mult).reshape(f.P.E, 2, 2, 2)           # [Ef, k, j, i]
+            t = np.einsum('eia,ejb,ekc,ekji->ecba', _H[sx], _H[sy], _H[sz], u)
+            rc = np.zeros((c.P.E, 2, 2, 2))
+            np.add.at(rc, ce, t)
+            return c.P.mask * c.P.dssum(rc.reshape(-1))
         u = (r / f.P.mult).reshape(f.P.E, f.n, f.n, f.n)
         rc = _apply3(self.J[l].T, u).reshape(-1)
         return c.P.mask * c.P.dssum(rc)

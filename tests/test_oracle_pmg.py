@@ -177,3 +177,80 @@ def test_mg_needs_far_fewer_iterations_than_jacobi():
     _, itj, _ = P.pcg(b, tol=1e-10, maxit=5000)
     assert P.true_relres(b, x) <= 1e-9
     assert it * 5 <= itj, (it, itj)
+
+
+def test_h_level_sizes():
+    assert pmg.h_levels(32, 32, 32) == [(16, 16, 16), (8, 8, 8), (4, 4, 4), (2, 2, 2)]
+    assert pmg.h_levels(8, 4, 4) == [(4, 2, 2)]
+    assert pmg.h_levels(4, 3, 3) == [] and pmg.h_levels(2, 2, 2) == []
+    M = pmg.PMG(4, 4, 4, 3, deform=False, power_iters=2)
+    assert [(lv.P.kx, lv.N) for lv in M.levels] == [(4, 3), (4, 1), (2, 1)] and M.n_p == 2
+    assert len(pmg.PMG(4, 4, 4, 3, power_iters=2, hcoarsen=False).levels) == 2
+
+
+def test_h_prolongation_reproduces_trilinear_functions():
+    """Undeformed mesh: a global trilinear function sampled at the coarse
+    N = 1 nodes and prolongated equals its values at the fine nodes."""
+    M = pmg.PMG(4, 4, 4, 1, deform=False, power_iters=2)
+    f, c = M.levels[0].P, M.levels[1].P
+    poly = lambda X: (1 + X[0] + 2 * X[1] - X[2] + X[0] * X[1] - X[1] * X[2]
+                      + 3 * X[0] * X[2] + X[0] * X[1] * X[2])
+    np.testing.assert_allclose(M.prolong(0, poly(c.X).reshape(-1)), poly(f.X).reshape(-1),
+                               atol=1e-14)
+
+
+def test_h_restriction_is_adjoint_of_prolongation():
+    M = pmg.PMG(8, 4, 4, 2, deform=True, power_iters=2)
+    l = M.n_p - 1                                     # the N = 1 level and its h-level
+    f, c = M.levels[l].P, M.levels[l + 1].P
+    assert (c.kx, c.ky, c.kz, c.N) == (4, 2, 2, 1)
+    g = np.random.default_rng(3)
+    r = f.mask * f.dssum(g.standard_normal(f.L)) / f.mult
+    v = c.mask * c.dssum(g.standard_normal(c.L)) / c.mult
+    pv = M.prolong(l, v)
+    np.testing.assert_allclose(f.dssum(pv) / f.mult, pv, atol=1e-13)   # continuous
+    assert np.abs(pv[f.mask == 0]).max() == 0.0                        # masked
+    lhs, rhs = c.glsc3(M.restrict(l, r), v), f.glsc3(r, pv)
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_h_levels_vcycle_symmetric_positive():
+    M = pmg.PMG(4, 4, 4, 3, deform=True, power_iters=10)
+    assert len(M.levels) == 3
+    for lev in M.levels:
+        _sym_pos(lev.schwarz, lev.P, 4)
+    _sym_pos(M.vcycle, M.levels[0].P, 5)
+
+
+def test_h_levels_solution_equals_dense_solve():
+    kx = ky = kz = 4
+    N = 1
+    M = pmg.PMG(kx, ky, kz, N, deform=True)
+    assert len(M.levels) == 2
+    P = M.levels[0].P
+    b = P.rhs_uniform(2)
+    x, it, _ = M.pcg(b, tol=1e-13, maxit=200)
+    A, gid_local = dense_box_matrix(kx, ky, kz, N, deform_amp=0.05)
+    on = boundary_unique(kx, ky, kz, N, gid_local)
+    inner = np.nonzero(~on)[0]
+    bu = np.zeros(A.shape[0])
+    bu[gid_local] = b
+    xu = np.zeros(A.shape[0])
+    xu[inner] = np.linalg.solve(A[np.ix_(inner, inner)], bu[inner])
+    np.testing.assert_allclose(x, xu[gid_local], rtol=1e-9, atol=1e-11 * np.abs(xu).max())
+
+
+def test_h_levels_make_iterations_mesh_independent():
+    """With the h-levels the iteration count barely grows from 4^3 to 8^3
+    elements; with the p-levels alone it grows by half."""
+    its = {}
+    for k in (4, 8):
+        for h in (True, False):
+            M = pmg.PMG(k, k, k, 3, deform=True, hcoarsen=h)
+            P = M.levels[0].P
+            b = P.rhs_uniform(0)
+            x, its[k, h], _ = M.pcg(b, tol=1e-8, maxit=300)
+            assert P.true_relres(b, x) <= 1e-8
+    assert its[8, True] <= its[4, True] + 2
+    assert its[8, False] >= its[4, False] + 4
+    assert its[8, True] < its[8, False]
