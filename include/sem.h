@@ -310,6 +310,9 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *                 for 0 (default) four, 1 five, 2 six 256-thread blocks per
  *                 SM; 3 four blocks and an L2 prefetch of each thread's next
  *                 float4 group
+ *   "mg_hcoarsen" 1 (default): the multigrid preconditioner continues below
+ *                 its N = 1 level on halved meshes (see sem_mg_apply); 0:
+ *                 orders only.  Changing it discards the built levels.
  *   "kernel_timing" 1: PCG solves run without graphs and time each
  *                 iteration's operator, gather-scatter and update launches
  *                 with CUDA events on the handle's stream (the events add
@@ -326,13 +329,17 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
 /* Multigrid preconditioner z = M^{-1} r (box meshes only).  The paper runs
  * Nekbone with its multigrid preconditioner (Sec. 3.1, profiling table;
  * Sec. 4, the Schwarz weights' square roots kept in FP64) without giving
- * its algorithm; this one is a symmetric p-multigrid V-cycle over orders
- * N, floor(N/2), ..., 1 on the same mesh: tensor-product interpolation
- * between orders (restriction its adjoint on unique nodes), additive
- * overlapping Schwarz smoothing (each element extended by one node layer,
- * separable local operator solved by fast diagonalisation, weights
- * 1/sqrt(blocks holding the node) computed in FP64, damping 1/lambda_max
- * from a power iteration), smoothing only on the N = 1 level.  r, z: L
+ * its algorithm; this one is a symmetric V-cycle over orders N,
+ * floor(N/2), ..., 1 on the same mesh (tensor-product interpolation between
+ * orders) and then, with option "mg_hcoarsen" (default), over the N = 1
+ * problem on the mesh halved in every direction while kx, ky, kz are even
+ * and their halves at least 2 (trilinear interpolation between meshes);
+ * restriction is the adjoint of interpolation on unique nodes; additive
+ * overlapping Schwarz smoothing on every level (each element extended by
+ * one node layer, separable local operator solved by fast diagonalisation,
+ * weights 1/sqrt(blocks holding the node) computed in FP64, damping
+ * 1/lambda_max from a power iteration), smoothing only on the coarsest
+ * level.  r, z: L
  * device values, FP64 for SEM_FP64 or FP32 for SEM_MIXED_FP32 (the FP32
  * cycle sums shared nodes error-free); r continuous and masked.  Builds
  * the levels on first use (handles of their own, kept with this one). */

@@ -497,6 +497,9 @@ int sem_set_option(sem_handle h, const char* key, int64_t value) {
     h->l2_persist = value != 0;
   } else if (k == "upd_tma" && (value == 0 || value == 1)) {
     h->upd_tma = value != 0;
+  } else if (k == "mg_hcoarsen" && (value == 0 || value == 1)) {
+    if (h->mg_hcoarsen != (value != 0)) mg_free(*h);   // rebuilt on next use
+    h->mg_hcoarsen = value != 0;
   } else if (k == "upd_variant" && value >= 0 && value <= 3) {
     h->upd_variant = (int)value;
   } else if (k == "l2_hints" && (value == 0 || value == 1)) {
@@ -531,6 +534,7 @@ int sem_get_option(sem_handle h, const char* key, double* value) {
   else if (k == "l2_hints") *value = h->l2_hints ? 1 : 0;
   else if (k == "upd_variant") *value = h->upd_variant;
   else if (k == "upd_tma") *value = h->upd_tma ? 1 : 0;
+  else if (k == "mg_hcoarsen") *value = h->mg_hcoarsen ? 1 : 0;
   else if (k == "mg_levels") *value = mg_levels(*h);
   else if (k.rfind("mg_omega_", 0) == 0 && k.size() == 10 && k[9] >= '0' && k[9] <= '9')
     *value = mg_omega(*h, k[9] - '0');

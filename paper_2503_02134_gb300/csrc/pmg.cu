@@ -18,6 +18,11 @@
 //    zero); block solutions summed with weights 1/sqrt(c), c = blocks
 //    holding the node (computed in FP64, also for the FP32 smoother), and
 //    damped by omega = 1/lambda_max(S A) from a power iteration;
+//  * h-levels: below the N = 1 level, while kx, ky, kz are all even and their
+//    halves at least 2, the N = 1 discretisation of the box with half as many
+//    elements per direction (each coarse element holds 2 x 2 x 2 fine ones);
+//    prolongation = trilinear interpolation of the coarse element's eight
+//    vertex values, restriction its adjoint on unique nodes; same smoother;
 //  * cycle: symmetric V-cycle; the coarsest level applies the smoother.
 //
 // The block sum is a gather over the blocks that hold a node, found from its
@@ -54,6 +59,7 @@ struct MgLevel {
   double* wsq64 = nullptr;  // [L] 1/sqrt(blocks holding the node)
   float* wsq32 = nullptr;
   double omega = 1.0;
+  bool h_to_next = false;   // the next coarser level is this mesh halved (both N = 1)
   double* J64 = nullptr;    // interpolation from the next coarser level: [n][nc]
   float* J32 = nullptr;
   // work vectors of this level (both precisions)
@@ -755,6 +761,81 @@ static int mg_transfer_t_launch(Handle& h, int NF, const T* J, const T* in, cons
   return 0;
 }
 
+// h-transfers between two N = 1 levels: fine mesh kx x ky x kz, coarse mesh
+// halved.  Fine element e lies in coarse element (ex/2, ey/2, ez/2), in half
+// (ex%2, ey%2, ez%2); its node i (0, 1) sits at t = (s + i)/2 in the coarse
+// element, where the coarse vertex a has weight 1 - t (a = 0) or t (a = 1):
+// weights 1, 1/2 or 0, exact in either precision.
+__device__ __forceinline__ int mg_hw2(int s, int i, int a) {   // 2 x weight
+  const int t2 = s + i;
+  return a == 0 ? 2 - t2 : t2;
+}
+
+// zf += P zc, one thread per fine local node
+template <typename T>
+__global__ void mg_hprolong_kernel(int kx, int ky, int64_t Ef, const T* __restrict__ zc,
+                                   T* __restrict__ zf) {
+  const int kxc = kx / 2, kyc = ky / 2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 8 * Ef;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t >> 3;
+    const int node = (int)(t & 7);
+    const int i = node & 1, j = (node >> 1) & 1, k = node >> 2;
+    const int64_t ex = e % kx, ey = (e / kx) % ky, ez = e / ((int64_t)kx * ky);
+    const int sx = (int)(ex & 1), sy = (int)(ey & 1), sz = (int)(ez & 1);
+    const T* u = zc + (ex / 2 + kxc * (ey / 2 + (int64_t)kyc * (ez / 2))) * 8;
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const int w8 = mg_hw2(sx, i, a) * mg_hw2(sy, j, b) * mg_hw2(sz, k, c);
+          if (w8) s += (T)(w8 * 0.125) * u[a + 2 * b + 4 * c];
+        }
+    zf[t] += s;
+  }
+}
+
+// rc = P^T (rf / m_f) element by element (before the coarse summation), one
+// thread per coarse local node gathering from the eight children
+template <typename T>
+__global__ void mg_hrestrict_kernel(int kxc, int kyc, int64_t Ec, const T* __restrict__ rf,
+                                    const uint8_t* __restrict__ cwf, T* __restrict__ rc) {
+  const int64_t kx = 2 * (int64_t)kxc, ky = 2 * (int64_t)kyc;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 8 * Ec;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ce = t >> 3;
+    const int node = (int)(t & 7);
+    const int a = node & 1, b = (node >> 1) & 1, c = node >> 2;
+    const int64_t cx = ce % kxc, cy = (ce / kxc) % kyc, cz = ce / ((int64_t)kxc * kyc);
+    T s = T(0);
+#pragma unroll
+    for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
+      for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+        for (int sx = 0; sx < 2; ++sx) {
+          const int64_t ef = (2 * cx + sx) + kx * ((2 * cy + sy) + ky * (2 * cz + sz));
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+              for (int i = 0; i < 2; ++i) {
+                const int w8 = mg_hw2(sx, i, a) * mg_hw2(sy, j, b) * mg_hw2(sz, k, c);
+                if (!w8) continue;
+                const int64_t l = ef * 8 + i + 2 * j + 4 * k;
+                const uint8_t m = cwf[l];
+                const T v = m ? rf[l] * (T(1) / T(m)) : T(0);
+                s += (T)(w8 * 0.125) * v;
+              }
+        }
+    rc[t] = s;
+  }
+}
+
 // t = r - w (r and w masked)
 template <typename T>
 __global__ void mg_residual_kernel(int64_t L, const T* __restrict__ r, const T* __restrict__ w,
@@ -882,14 +963,28 @@ static int mg_vcycle(MgData& mg, int l, const T* r, T* z) {
   mg_residual_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, r, P::w(lv), t);
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
-  // restriction: (J^T)^{x3} (t / mult), then QQ^T and mask on the coarse level
-  if ((rc = mg_transfer_t_launch<T, true>(h, lv.N, P::J(lv), t, h.cw8, P::r(cv)))) return rc;
+  // restriction: (J^T)^{x3} (t / mult) -- or its trilinear h-counterpart --,
+  // then QQ^T and mask on the coarse level
+  if (lv.h_to_next) {
+    mg_hrestrict_kernel<T><<<grid_of(hc, 8 * hc.E), 256, 0, h.stream>>>(hc.kx, hc.ky, hc.E, t,
+                                                                        h.cw8, P::r(cv));
+    ++h.launches;
+    SEM_CUDA(cudaGetLastError());
+  } else if ((rc = mg_transfer_t_launch<T, true>(h, lv.N, P::J(lv), t, h.cw8, P::r(cv)))) {
+    return rc;
+  }
   if ((rc = launch_gs(hc, P::p, P::r(cv)))) return rc;
   mg_mask_kernel<T><<<grid_of(hc, hc.L), 256, 0, h.stream>>>(hc.L, hc.mask64, P::r(cv));
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
   if ((rc = mg_vcycle<T>(mg, l + 1, P::r(cv), P::z(cv)))) return rc;
-  if ((rc = mg_transfer_t_launch<T, false>(h, lv.N, P::J(lv), P::z(cv), nullptr, z))) return rc;
+  if (lv.h_to_next) {
+    mg_hprolong_kernel<T><<<grid_of(h, 8 * h.E), 256, 0, h.stream>>>(h.kx, h.ky, h.E, P::z(cv), z);
+    ++h.launches;
+    SEM_CUDA(cudaGetLastError());
+  } else if ((rc = mg_transfer_t_launch<T, false>(h, lv.N, P::J(lv), P::z(cv), nullptr, z))) {
+    return rc;
+  }
   if ((rc = mg_apply_a<T>(lv, z, P::w(lv)))) return rc;
   mg_residual_kernel<T><<<grid_of(h, h.L), 256, 0, h.stream>>>(h.L, r, P::w(lv), t);
   ++h.launches;
@@ -1025,20 +1120,36 @@ int mg_ensure(Handle& h) {
     mg_free(h);
     return rc;
   };
-  std::vector<int> orders{h.N};
-  while (orders.back() > 1) orders.push_back(std::max(1, orders.back() / 2));
-  mg->lv.resize(orders.size());
+  // levels: orders N, N/2, ..., 1 on the mesh, then (h-levels) N = 1 on the
+  // mesh halved while every dimension is even and its half at least 2
+  struct Spec {
+    int N, kx, ky, kz;
+  };
+  std::vector<Spec> specs{{h.N, h.kx, h.ky, h.kz}};
+  while (specs.back().N > 1) specs.push_back({std::max(1, specs.back().N / 2), h.kx, h.ky, h.kz});
+  const size_t n_p = specs.size();
+  if (h.mg_hcoarsen) {
+    int kx = h.kx, ky = h.ky, kz = h.kz;
+    while (kx % 2 == 0 && ky % 2 == 0 && kz % 2 == 0 && std::min(kx, std::min(ky, kz)) >= 4) {
+      kx /= 2;
+      ky /= 2;
+      kz /= 2;
+      specs.push_back({1, kx, ky, kz});
+    }
+  }
+  mg->lv.resize(specs.size());
   int rc;
-  for (size_t l = 0; l < orders.size(); ++l) {
+  for (size_t l = 0; l < specs.size(); ++l) {
     MgLevel& v = mg->lv[l];
+    v.h_to_next = l + 1 < specs.size() && l + 1 >= n_p;
     if (l == 0) {
       v.h = &h;
     } else {
       sem_mesh mesh;
       memset(&mesh, 0, sizeof(mesh));
-      mesh.kx = h.kx;
-      mesh.ky = h.ky;
-      mesh.kz = h.kz;
+      mesh.kx = specs[l].kx;
+      mesh.ky = specs[l].ky;
+      mesh.kz = specs[l].kz;
       for (int d = 0; d < 3; ++d) {
         mesh.lo[d] = h.mesh_lo[d];
         mesh.hi[d] = h.mesh_hi[d];
@@ -1046,14 +1157,14 @@ int mg_ensure(Handle& h) {
       mesh.deform_amp = h.deform_amp;
       mesh.deform_kind = h.deform_kind;
       sem_handle sub = nullptr;
-      if ((rc = sem_setup(&mesh, orders[l], 0, h.stream, &sub))) return fail(rc);
+      if ((rc = sem_setup(&mesh, specs[l].N, 0, h.stream, &sub))) return fail(rc);
       v.h = sub;
       v.owned = true;
     }
     if ((rc = level_setup(v))) return fail(rc);
   }
-  // interpolation matrices (host FP64 from each level's GLL nodes)
-  for (size_t l = 0; l + 1 < orders.size(); ++l) {
+  // interpolation matrices of the p-pairs (host FP64 from each level's GLL nodes)
+  for (size_t l = 0; l + 1 < n_p; ++l) {
     MgLevel& f = mg->lv[l];
     MgLevel& c = mg->lv[l + 1];
     std::vector<double> xf(f.n), xc(c.n);

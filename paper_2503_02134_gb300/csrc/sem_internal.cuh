@@ -98,6 +98,7 @@ struct Handle {
   int upd_gs_occ[16] = {};     // resident blocks per SM of the fused update kernels (0: not yet read)
   int upd_variant = 0;         // fused update launch shape (0..3, see pcg_kernels.cu UpdShape)
   bool upd_tma = false;        // fused update (n = 8): bulk-copy staged variant
+  bool mg_hcoarsen = true;     // multigrid: h-levels below the N = 1 level
 
   // Jacobi
   double* minv64 = nullptr;

@@ -12,7 +12,9 @@ from oracle import pmg  # noqa: E402
 from oracle import sem_oracle as so  # noqa: E402
 from tests.gpu_util import rel_maxerr  # noqa: E402
 
-CASES = [((3, 3, 2), 5, True), ((4, 3, 3), 7, True), ((2, 1, 3), 2, False), ((3, 2, 2), 9, True)]
+CASES = [((3, 3, 2), 5, True), ((4, 3, 3), 7, True), ((2, 1, 3), 2, False), ((3, 2, 2), 9, True),
+         # with h-levels below N = 1: 4^3 -> 2^3; 8x4x4 -> 4x2x2; 8^3 -> 4^3 -> 2^3
+         ((4, 4, 4), 3, True), ((8, 4, 4), 5, True), ((8, 8, 8), 1, False)]
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +66,7 @@ def test_vcycle_symmetric_on_device(sem):
     S.close()
 
 
-@pytest.mark.parametrize("dims,N", [((4, 3, 3), 7), ((3, 3, 2), 5)])
+@pytest.mark.parametrize("dims,N", [((4, 3, 3), 7), ((3, 3, 2), 5), ((8, 4, 4), 5), ((4, 4, 4), 7)])
 def test_mg_pcg_matches_oracle(sem, dims, N):
     M = pmg.PMG(*dims, N, deform=True)
     P = M.levels[0].P
@@ -88,6 +90,25 @@ def test_mg_pcg_matches_oracle(sem, dims, N):
     xr, ir = S.solve(bg, tol=1e-8, maxit=300, precision=sem.SEM_MIXED_FP32, precond="mg",
                      refine_mode=1)
     assert ir["rc"] == 0 and P.true_relres(b, xr.cpu().numpy()) <= 1.0000001e-8
+    S.close()
+
+
+def test_h_coarsening_option(sem):
+    """Option "mg_hcoarsen" 0 keeps the orders-only hierarchy (the oracle's
+    hcoarsen=False), 1 (default) adds the halved N = 1 meshes; switching
+    rebuilds the levels."""
+    dims, N = (8, 4, 4), 3
+    S = sem.Solver(*dims, N, deform=True)
+    P = so.Problem(*dims, N, deform=True)
+    r = torch.tensor(_continuous(P, 9), device="cuda")
+    z = torch.empty_like(r)
+    for hc in (0, 1):
+        sem.sem_set_option(S.h, "mg_hcoarsen", hc)
+        assert sem.sem_get_option(S.h, "mg_hcoarsen") == hc
+        M = pmg.PMG(*dims, N, deform=True, hcoarsen=bool(hc))
+        sem.sem_mg_apply(S.h, r, z, sem.SEM_FP64)
+        assert sem.sem_get_option(S.h, "mg_levels") == len(M.levels) == 2 + hc
+        assert rel_maxerr(z.cpu(), M.vcycle(r.cpu().numpy())) < 1e-10
     S.close()
 
 
