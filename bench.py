@@ -273,7 +273,9 @@ def order_sweep_leg(sem, torch, hbm_gbs):
                     "fp32_tflops": flops / (ms32 * 1e-3) / 1e12,
                     "fp64_gdofs": L / ms64 / 1e6, "fp64_tflops": flops / (ms64 * 1e-3) / 1e12,
                     "fp32_rel_err_vs_fp64": err, "tensor_cores": tc,
-                    "fp32_kernel": "bulk-copy staged" if n <= 10 else "register/shared (unstaged)"})
+                    "fp32_kernel": "bulk-copy staged" if n % 2 == 0 else "register/shared (unstaged)",
+                    "fp32_variant": int(sem.sem_get_option(S.h, "ax_variant")),
+                    "fp32_tune_ms": [sem.sem_get_option(S.h, f"ax_tune_ms_plain_{v}") for v in range(4)]})
         S.close()
         del u64, u32, w64, w32
     return out
@@ -416,6 +418,10 @@ def main():
                          "on the benchmark mesh inside the NVTX range mg_cycle")
     ap.add_argument("--profile-k", type=int, default=0,
                     help="with --profile: a k^3-element mesh instead of the benchmark's (smaller ncu captures)")
+    ap.add_argument("--profile-sweep", type=int, default=0, metavar="N",
+                    help="ncu run of the FP32 operator at order N (the order sweep's mesh, or a "
+                         "k^3 mesh with --profile-k): two plain calls inside the NVTX range "
+                         "bench_profile_sweep")
     ap.add_argument("--profile-batched", action="store_true",
                     help="ncu run of the 64-problem batch: one solve inside an NVTX range")
     ap.add_argument("--profile-batched-small", action="store_true",
@@ -436,6 +442,27 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     import paper_2503_02134_gb300 as sem
+
+    if args.profile_sweep:
+        import sem_inputs
+        N = args.profile_sweep
+        c = sem_inputs.order_sweep_case(N)
+        k3 = (args.profile_k,) * 3 if args.profile_k > 0 else (c.kx, c.ky, c.kz)
+        S = sem.Solver(*k3, N, deform=True)
+        u = torch.rand(S.L, dtype=torch.float32, device="cuda",
+                       generator=torch.Generator(device="cuda").manual_seed(N))
+        w = torch.empty_like(u)
+        sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)      # warm-up
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bench_profile_sweep")
+        for _ in range(2):
+            sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_sweep": N, "elements": S.E,
+                          "variant": int(sem.sem_get_option(S.h, "ax_variant"))}))
+        S.close()
+        return 0
 
     if args.profile_batched or args.profile_batched_small:
         import sem_inputs

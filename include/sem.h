@@ -270,7 +270,11 @@ void sem_batch_destroy(sem_batch b);
  * pointers to n doubles; result: device pointer to one double; stream: a
  * cudaStream_t (NULL = legacy default stream); the call is asynchronous.
  * The first call on a device looks up the array's device address on the
- * current device; make that first call before any stream capture.  All calls
+ * current device and keeps it for the life of the process; make that first
+ * call before any stream capture.  The kept address belongs to the device's
+ * context of that moment: after cudaDeviceReset the library's module may be
+ * loaded at another address, so do not call this entry point on a device
+ * after resetting it.  All calls
  * share the one array (the call zeroes its counter first), so calls that
  * overlap on the GPU -- on different streams, or from several threads --
  * race and must be serialised by the caller. */
@@ -319,8 +323,10 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  *                 small gaps between launches); 0 (default) off.  Setting
  *                 it, either way, clears the sums.
  * sem_get_option also reads "ax_tune_ms_plain_<v>", "ax_tune_ms_pcg_<v>"
- * (autotuner timings, ms), "launches" (kernels enqueued so far),
- * "mg_levels", "mg_omega_<l>" (multigrid levels and damping, 0 before first use),
+ * (autotuner timings, ms; -1 for a variant whose stages do not fit in shared
+ * memory at this order), "launches" (kernels enqueued so far),
+ * "mg_levels" (0 before the first multigrid use), "mg_omega_<l>" (damping of
+ * level l, any number of digits; -1 for a level that does not exist),
  * "l2_window_bytes", "l2_max_persist", "l2_max_window" (the L2 window of
  * the last mixed solve and the device limits it was cut to),
  * "kt_iters" (iterations timed) and "kt_ms_ax", "kt_ms_gs",
@@ -338,8 +344,8 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
  * overlapping Schwarz smoothing on every level (each element extended by
  * one node layer, separable local operator solved by fast diagonalisation,
  * weights 1/sqrt(blocks holding the node) computed in FP64, damping
- * 1/lambda_max from a power iteration), smoothing only on the coarsest
- * level.  r, z: L
+ * 1/lambda_max from a power iteration); the coarsest level applies the
+ * smoother only (no direct coarse solve).  r, z: L
  * device values, FP64 for SEM_FP64 or FP32 for SEM_MIXED_FP32 (the FP32
  * cycle sums shared nodes error-free); r continuous and masked.  Builds
  * the levels on first use (handles of their own, kept with this one). */

@@ -222,6 +222,12 @@ int sem_setup(const sem_mesh* mesh, int N, int geom_flags, void* stream, sem_han
 
   h->dev_err = &h->scal->err;
   if ((rc = launch_gll(*h))) return fail(rc);
+  if ((ce = cudaMemcpyAsync(h->D32_host, h->D32, sizeof(float) * n * n, cudaMemcpyDeviceToHost,
+                            h->stream)) != cudaSuccess ||
+      (ce = cudaMemcpyAsync(h->D64_host, h->D64, sizeof(double) * n * n, cudaMemcpyDeviceToHost,
+                            h->stream)) != cudaSuccess ||
+      (ce = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+    return fail(cuda_fail(ce, "sem_setup: D to host"));
   double* ucoords = nullptr;
   if (mesh->gid) {
     h->gid_user = true;
@@ -536,8 +542,12 @@ int sem_get_option(sem_handle h, const char* key, double* value) {
   else if (k == "upd_tma") *value = h->upd_tma ? 1 : 0;
   else if (k == "mg_hcoarsen") *value = h->mg_hcoarsen ? 1 : 0;
   else if (k == "mg_levels") *value = mg_levels(*h);
-  else if (k.rfind("mg_omega_", 0) == 0 && k.size() == 10 && k[9] >= '0' && k[9] <= '9')
-    *value = mg_omega(*h, k[9] - '0');
+  else if (k.rfind("mg_omega_", 0) == 0 && k.size() > 9 && k.size() <= 12 &&
+           k.find_first_not_of("0123456789", 9) == std::string::npos) {
+    // level index: any number of decimal digits (the level count grows with
+    // log2 of the mesh size once h-levels are built)
+    *value = mg_omega(*h, std::stoi(k.substr(9)));   // -1 for a level that does not exist
+  }
   else if (k == "l2_window_bytes") *value = (double)h->l2_window_bytes;
   else if (k == "l2_max_persist") *value = (double)h->l2_max_persist;
   else if (k == "l2_max_window") *value = (double)h->l2_max_window;

@@ -23,6 +23,14 @@
 
 namespace sem {
 
+// D by value (row-major D[i][l] at d[i * n + l]).  As a kernel parameter it
+// lives in the constant bank; indexed only by unrolled loop counters, its
+// entries are immediate operands of the FMAs (no shared-memory load).
+template <int n, typename T = float>
+struct DMat {
+  T d[n * n];
+};
+
 template <int n>
 struct AxShape {
   static constexpr int n2 = n * n;
@@ -39,7 +47,8 @@ __device__ __forceinline__ bool on_dirichlet(uint8_t f, int i, int j, int k, int
 template <int n, typename T, bool PCG, int DM>
 __global__ void __launch_bounds__(AxShape<n>::NT)
     ax_kernel(const T* __restrict__ uin, T* __restrict__ wout, const T* __restrict__ G,
-              const T* __restrict__ Dg, const uint8_t* __restrict__ faces, int64_t E,
+              const T* __restrict__ Dg, const __grid_constant__ DMat<n, T> Dc,
+              const uint8_t* __restrict__ faces, int64_t E,
               const T* __restrict__ rr, const T* __restrict__ minv, T* __restrict__ pp,
               PcgScalars* __restrict__ scal, double* __restrict__ partials) {
   using S = AxShape<n>;
@@ -118,7 +127,9 @@ __global__ void __launch_bounds__(AxShape<n>::NT)
       for (int l = 0; l < n; ++l) {
         ur += d_i(l) * su_e[k * n2 + jr * n + l];
         us += d_j(l) * su_e[k * n2 + l * n + ir];
-        ut += sD[k][l] * ureg[l];
+        // FP32: D from the constant bank; FP64 (DFMA-bound) measured faster from shared memory
+        if constexpr (sizeof(T) == 4) ut += Dc.d[k * n + l] * ureg[l];
+        else ut += sD[k][l] * ureg[l];
       }
       T g0 = T(0), g1 = T(0), g2 = T(0), g3 = T(0), g4 = T(0), g5 = T(0);
       if (act) {
@@ -137,7 +148,10 @@ __global__ void __launch_bounds__(AxShape<n>::NT)
         ss_e[k * n2 + ij] = vs;
       }
 #pragma unroll
-      for (int kk = 0; kk < n; ++kk) wreg[kk] += sD[k][kk] * vt;
+      for (int kk = 0; kk < n; ++kk) {
+        if constexpr (sizeof(T) == 4) wreg[kk] += Dc.d[k * n + kk] * vt;
+        else wreg[kk] += sD[k][kk] * vt;
+      }
     }
     __syncthreads();
 
@@ -203,7 +217,11 @@ int ax_launch(Handle& h, const T* u, T* w, const T* G, const T* D, const AxProlo
   PcgScalars* scal = PCG ? const_cast<PcgScalars*>(pro->scal) : nullptr;
   double* partials = PCG ? pro->pap_partials : nullptr;
   T* pp = PCG ? const_cast<T*>(u) : nullptr;
-  kern<<<grid, S::NT, smem, h.stream>>>(u, w, G, D, h.bfaces, h.E, r, minv, pp, scal, partials);
+  DMat<n, T> Dc;
+  for (int q = 0; q < n * n; ++q)
+    Dc.d[q] = sizeof(T) == sizeof(double) ? (T)h.D64_host[q] : (T)h.D32_host[q];
+  kern<<<grid, S::NT, smem, h.stream>>>(u, w, G, D, Dc, h.bfaces, h.E, r, minv, pp, scal,
+                                        partials);
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
   return 0;

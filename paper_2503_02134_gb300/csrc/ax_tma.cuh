@@ -10,6 +10,15 @@
 // never issue a global load: the memory pipe is kept busy by the copy engine
 // instead of by occupancy.  Requires 16-byte aligned element blocks, i.e. an
 // even number of GLL points per direction (n^3 * 4 bytes % 16 == 0).
+//
+// The t-direction contractions (u_t = D u along k and the accumulation of
+// D^T v_t) index D with the two unrolled loop counters only, so D is passed
+// by value as a kernel parameter: the entries are constant-bank operands of
+// the FMAs and cost no shared-memory access.  Shared-memory wavefronts are
+// what bounds this kernel at n >= 8 (per k-plane and warp: n/4 vector row
+// loads for u_r, n loads for u_s, 6 for G, the same again for the transposed
+// pass), so the 2n broadcast loads of D per plane that this removes are
+// about a third of them.
 #pragma once
 
 #include "ax_kernel.cuh"
@@ -18,17 +27,24 @@
 namespace sem {
 
 // Launch variants (elements per block, pipeline stages); the set-up
-// autotuner times them on the actual mesh and keeps the fastest.
+// autotuner times them on the actual mesh and keeps the fastest.  For
+// n >= 12 one element already fills 144..256 threads: variants 0..2 are one
+// element per stage with two, three and one stage, variant 3 two elements
+// per stage (two stages).  A variant whose stages do not fit in shared
+// memory (tma_fits) is never launched.
 template <int n, int V>
 struct TmaShape {
   static constexpr int n2 = n * n;
   static constexpr int n3 = n * n * n;
   static constexpr int EPB_BIG = (128 / n2) > 0 ? (128 / n2) : 1;
   static constexpr int EPB_SMALL = (64 / n2) > 0 ? (64 / n2) : 1;
-  static constexpr int EPB = V == 0 ? EPB_BIG : EPB_SMALL;
-  // bulk-copy stages: variant 0 two (two elements each), 1 three, 2 four,
-  // 3 two (one element each: more resident blocks, shallower prefetch)
-  static constexpr int NS = V == 0 ? 2 : (V == 1 ? 3 : (V == 2 ? 4 : 2));
+  static constexpr int EPB = n >= 12 ? (V == 3 ? 2 : 1) : (V == 0 ? EPB_BIG : EPB_SMALL);
+  // bulk-copy stages: for n < 12 variant 0 two (two elements each), 1 three,
+  // 2 four, 3 two (one element each: more resident blocks, shallower
+  // prefetch); for n >= 12 variant 2 has a single stage, so that two blocks
+  // (one computing while the other waits for its copy) fit on an SM where
+  // two stages of one block would not leave room for a second block
+  static constexpr int NS = V == 0 ? 2 : (V == 1 ? 3 : (V == 2 ? (n >= 12 ? 1 : 4) : 2));
   static constexpr int NT = ((n2 * EPB + 31) / 32) * 32;
   static constexpr uint32_t VEC = EPB * n3 * 4;                 // bytes of one vector per stage
 };
@@ -38,6 +54,16 @@ constexpr size_t tma_smem_bytes() {
   using S = TmaShape<n, V>;
   constexpr int NV = PCG ? 3 : 1;
   return S::NS * (size_t)(NV + 6) * S::VEC + S::NS * sizeof(uint64_t);
+}
+
+// Shared memory per block on sm_100/sm_103 (227 KB) and the static part of
+// ax_tma_kernel (D with a padded row, one double per warp, alignment slack).
+constexpr size_t kMaxSmemPerBlock = 232448;
+template <int n, bool PCG, int V>
+constexpr bool tma_fits() {
+  return tma_smem_bytes<n, PCG, V>() + sizeof(float) * n * (n + 1) +
+             sizeof(double) * (TmaShape<n, V>::NT / 32) + 256 <=
+         kMaxSmemPerBlock;
 }
 
 // Dot product of a row of n contiguous shared-memory floats (16- or 8-byte
@@ -73,6 +99,7 @@ template <int n, bool PCG, int DM, int V>
 __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     ax_tma_kernel(const float* __restrict__ uin, float* __restrict__ wout,
                   const float* __restrict__ G, const float* __restrict__ Dg,
+                  const __grid_constant__ DMat<n> Dc,
                   const uint8_t* __restrict__ faces, int64_t E, const float* __restrict__ rr,
                   const float* __restrict__ minv, float* pp, PcgScalars* __restrict__ scal,
                   double* __restrict__ partials, int* __restrict__ err, int l2h) {
@@ -201,7 +228,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
 #pragma unroll
       for (int l = 0; l < n; ++l) {
         us += Dj[l] * su_e[k * n2 + l * n + ir];
-        ut += sD[k][l] * ureg[l];
+        ut += Dc.d[k * n + l] * ureg[l];
       }
       const float g0 = Gs[0 * n3 + k * n2], g1 = Gs[1 * n3 + k * n2], g2 = Gs[2 * n3 + k * n2];
       const float g3 = Gs[3 * n3 + k * n2], g4 = Gs[4 * n3 + k * n2], g5 = Gs[5 * n3 + k * n2];
@@ -213,7 +240,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         ss_e[k * n2 + ij] = vs;
       }
 #pragma unroll
-      for (int kk = 0; kk < n; ++kk) wreg[kk] += sD[k][kk] * vt;
+      for (int kk = 0; kk < n; ++kk) wreg[kk] += Dc.d[k * n + kk] * vt;
     }
     __syncthreads();
 
@@ -299,8 +326,10 @@ int ax_tma_launch(Handle& h, const float* u, float* w, const AxPrologue* pro) {
   double* partials = PCG ? pro->pap_partials : nullptr;
   float* pp = PCG ? const_cast<float*>(u) : nullptr;
   const int l2h = PCG && h.l2_hints ? 1 : 0;
-  kern<<<grid, S::NT, smem, h.stream>>>(u, w, h.G32, h.D32, h.bfaces, h.E, r, minv, pp, scal,
-                                        partials, h.dev_err, l2h);
+  DMat<n> Dc;
+  for (int q = 0; q < n * n; ++q) Dc.d[q] = h.D32_host[q];
+  kern<<<grid, S::NT, smem, h.stream>>>(u, w, h.G32, h.D32, Dc, h.bfaces, h.E, r, minv, pp,
+                                        scal, partials, h.dev_err, l2h);
   ++h.launches;
   SEM_CUDA(cudaGetLastError());
   return 0;

@@ -48,7 +48,9 @@ __global__ void __launch_bounds__(kNoAllocTileThreads)
   }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device and kept
+// for the life of the process (valid for the context current at the lookup:
+// a cudaDeviceReset afterwards invalidates it, which the header states).
 static std::mutex g_noalloc_mutex;
 static void* g_noalloc_ptr[64] = {};
 

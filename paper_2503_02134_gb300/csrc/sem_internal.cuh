@@ -62,6 +62,8 @@ struct Handle {
   double* wq = nullptr;     // n
   double* D64 = nullptr;    // n*n, D[i][j] row-major
   float* D32 = nullptr;
+  float D32_host[kMaxn * kMaxn] = {};   // host copies of D32, D64 (kernel parameters by value)
+  double D64_host[kMaxn * kMaxn] = {};
 
   // geometry
   double* coords = nullptr;  // 3*L
@@ -193,6 +195,7 @@ struct AxPrologue {
 int launch_ax_local(Handle& h, sem_precision p, const void* u, void* w, const AxPrologue* pro);
 
 int autotune_ax32(Handle& h);
+bool ax32_variant_fits(int n, bool pcg, int v);   // staged FP32 operator variant fits in smem
 
 // gs_kernels.cu
 int launch_gs(Handle& h, sem_precision p, void* v);

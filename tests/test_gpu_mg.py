@@ -51,9 +51,15 @@ def test_vcycle_matches_oracle(sem, dims, N, deform):
     S.close()
 
 
-def test_vcycle_symmetric_on_device(sem):
-    S = sem.Solver(4, 3, 3, 7, deform=True)
-    P = so.Problem(4, 3, 3, 7, deform=True)
+@pytest.mark.parametrize("dims,N", [((4, 3, 3), 7), ((8, 4, 4), 5)])
+def test_vcycle_symmetric_on_device(sem, dims, N):
+    """<M^-1 a, b> = <a, M^-1 b> on the device.  (8, 4, 4) at N = 5 has an
+    h-level (N = 1 on 4x2x2), so the trilinear prolongation and its adjoint
+    are part of the cycle; (4, 3, 3) has p-levels only.  FP64 to rounding;
+    FP32 cycles to a few FP32 ulps of the Cauchy-Schwarz scale
+    sqrt(<M^-1 a, a> <M^-1 b, b>)."""
+    S = sem.Solver(*dims, N, deform=True)
+    P = so.Problem(*dims, N, deform=True)
     a = torch.tensor(_continuous(P, 1), device="cuda")
     b = torch.tensor(_continuous(P, 2), device="cuda")
     za, zb = torch.empty_like(a), torch.empty_like(b)
@@ -63,6 +69,18 @@ def test_vcycle_symmetric_on_device(sem):
     y = sem.sem_glsc3(S.h, a, zb, sem.SEM_FP64)
     assert abs(x - y) <= 1e-12 * abs(x)
     assert sem.sem_glsc3(S.h, za, a, sem.SEM_FP64) > 0
+    if N == 5:
+        assert sem.sem_get_option(S.h, "mg_levels") >= 4   # 5 -> 2 -> 1, then N = 1 on 4x2x2
+    a32, b32 = a.float(), b.float()
+    za32 = torch.empty_like(a32)
+    zb32 = torch.empty_like(b32)
+    sem.sem_mg_apply(S.h, a32, za32, sem.SEM_MIXED_FP32)
+    sem.sem_mg_apply(S.h, b32, zb32, sem.SEM_MIXED_FP32)
+    x32 = sem.sem_glsc3(S.h, za32.double(), b32.double(), sem.SEM_FP64)
+    y32 = sem.sem_glsc3(S.h, a32.double(), zb32.double(), sem.SEM_FP64)
+    scale = np.sqrt(sem.sem_glsc3(S.h, za32.double(), a32.double(), sem.SEM_FP64) *
+                    sem.sem_glsc3(S.h, zb32.double(), b32.double(), sem.SEM_FP64))
+    assert abs(x32 - y32) <= 1e-5 * scale
     S.close()
 
 
