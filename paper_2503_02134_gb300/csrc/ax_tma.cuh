@@ -49,11 +49,19 @@ struct TmaShape {
   static constexpr uint32_t VEC = EPB * n3 * 4;                 // bytes of one vector per stage
 };
 
+// Orders whose s-direction contractions run as whole lines through a
+// shared-memory buffer of one element (see ax_tma_kernel).
+template <int n>
+constexpr bool tma_sline() {
+  return n >= 10 && n <= 14;
+}
+
 template <int n, bool PCG, int V>
 constexpr size_t tma_smem_bytes() {
   using S = TmaShape<n, V>;
   constexpr int NV = PCG ? 3 : 1;
-  return S::NS * (size_t)(NV + 6) * S::VEC + S::NS * sizeof(uint64_t);
+  return S::NS * (size_t)(NV + 6) * S::VEC + (tma_sline<n>() ? S::VEC : 0) +
+         S::NS * sizeof(uint64_t);
 }
 
 // Shared memory per block on sm_100/sm_103 (227 KB) and the static part of
@@ -95,6 +103,42 @@ __device__ __forceinline__ float row_dot(const float* __restrict__ row, const fl
   return s;
 }
 
+// Dot products with two independent accumulator chains (even and odd l,
+// added at the end): twice the instruction-level parallelism of one FMA
+// chain, for the orders where a block holds only a few warps.
+template <int n>
+__device__ __forceinline__ float row_dot_2acc(const float* __restrict__ row, const float* coef) {
+  float s0 = 0.f, s1 = 0.f;
+  if constexpr (n % 4 == 0) {
+#pragma unroll
+    for (int l = 0; l < n; l += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(row + l);
+      s0 += coef[l] * v.x;
+      s1 += coef[l + 1] * v.y;
+      s0 += coef[l + 2] * v.z;
+      s1 += coef[l + 3] * v.w;
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < n; l += 2) {
+      const float2 v = *reinterpret_cast<const float2*>(row + l);
+      s0 += coef[l] * v.x;
+      s1 += coef[l + 1] * v.y;
+    }
+  }
+  return s0 + s1;
+}
+template <int n, int stride>
+__device__ __forceinline__ float col_dot_2acc(const float* __restrict__ p, const float* coef) {
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int l = 0; l < n; l += 2) {
+    s0 += coef[l] * p[l * stride];
+    s1 += coef[l + 1] * p[(l + 1) * stride];
+  }
+  return s0 + s1;
+}
+
 template <int n, bool PCG, int DM, int V>
 __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     ax_tma_kernel(const float* __restrict__ uin, float* __restrict__ wout,
@@ -108,9 +152,13 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   constexpr int NV = PCG ? 3 : 1;
   constexpr int SV = EPB * n3;                 // floats of one vector per stage
   constexpr int STAGE = (NV + 6) * SV;         // floats per stage
+  // n >= 10: split accumulator chains (one or two blocks of few warps per SM)
+  constexpr bool kSplit = n >= 10;
+  constexpr bool kSLine = tma_sline<n>();
   extern __shared__ __align__(128) float smem_f[];
   float* const stage0 = smem_f;
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + NS * STAGE);
+  float* const sS = smem_f + NS * STAGE;   // s-line buffer (kSLine): u_s, v_s, then w_s
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + NS * STAGE + (kSLine ? SV : 0));
   __shared__ float sD[n][n + 1];
   __shared__ double sh_red[S::NT / 32];
 
@@ -216,20 +264,50 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       }
       ureg[k] = v;
     }
-    if (PCG) __syncthreads();
+    float* const sS_e = sS + ler * n3;
+    if constexpr (kSLine) {
+      // s-lines: this thread also owns the line (i, k = j) along s; u_s of
+      // the whole line is D times the line, every D entry indexed by the
+      // two unrolled counters (constant bank), written to the s-line buffer
+      if (PCG) __syncthreads();   // p complete in shared memory
+      float a[n];
+#pragma unroll
+      for (int l = 0; l < n; ++l) a[l] = su_e[jr * n2 + l * n + ir];
+#pragma unroll
+      for (int jj = 0; jj < n; ++jj) {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int l = 0; l < n; l += 2) {
+          s0 += Dc.d[jj * n + l] * a[l];
+          s1 += Dc.d[jj * n + l + 1] * a[l + 1];
+        }
+        if (lane_ok) sS_e[jr * n2 + jj * n + ir] = s0 + s1;
+      }
+      __syncthreads();
+    } else {
+      if (PCG) __syncthreads();
+    }
 
     float wreg[n];
 #pragma unroll
     for (int k = 0; k < n; ++k) wreg[k] = 0.f;
 #pragma unroll
     for (int k = 0; k < n; ++k) {
-      const float ur = row_dot<n>(su_e + k * n2 + jr * n, Di);
-      float us = 0.f, ut = 0.f;
+      float ur, us, ut = 0.f;
+      if constexpr (kSLine) {
+        ur = row_dot_2acc<n>(su_e + k * n2 + jr * n, Di);
+        us = sS_e[k * n2 + ij];
+      } else if constexpr (kSplit) {
+        ur = row_dot_2acc<n>(su_e + k * n2 + jr * n, Di);
+        us = col_dot_2acc<n, n>(su_e + k * n2 + ir, Dj);
+      } else {
+        ur = row_dot<n>(su_e + k * n2 + jr * n, Di);
+        us = 0.f;
 #pragma unroll
-      for (int l = 0; l < n; ++l) {
-        us += Dj[l] * su_e[k * n2 + l * n + ir];
-        ut += Dc.d[k * n + l] * ureg[l];
+        for (int l = 0; l < n; ++l) us += Dj[l] * su_e[k * n2 + l * n + ir];
       }
+#pragma unroll
+      for (int l = 0; l < n; ++l) ut += Dc.d[k * n + l] * ureg[l];
       const float g0 = Gs[0 * n3 + k * n2], g1 = Gs[1 * n3 + k * n2], g2 = Gs[2 * n3 + k * n2];
       const float g3 = Gs[3 * n3 + k * n2], g4 = Gs[4 * n3 + k * n2], g5 = Gs[5 * n3 + k * n2];
       const float vr = g0 * ur + g3 * us + g4 * ut;
@@ -237,18 +315,46 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       const float vt = g4 * ur + g5 * us + g2 * ut;
       if (lane_ok) {
         sr_e[k * n2 + ij] = vr;
-        ss_e[k * n2 + ij] = vs;
+        if constexpr (kSLine) sS_e[k * n2 + ij] = vs;   // over this thread's own u_s
+        else ss_e[k * n2 + ij] = vs;
       }
 #pragma unroll
       for (int kk = 0; kk < n; ++kk) wreg[kk] += Dc.d[k * n + kk] * vt;
     }
     __syncthreads();
+    if constexpr (kSLine) {
+      // transposed s-lines: w_s of line (i, k = j) = D^T times the line of
+      // v_s, written back over the same line (this thread reads all of it
+      // first; no other thread touches it)
+      float b[n];
+#pragma unroll
+      for (int l = 0; l < n; ++l) b[l] = sS_e[jr * n2 + l * n + ir];
+#pragma unroll
+      for (int jj = 0; jj < n; ++jj) {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int l = 0; l < n; l += 2) {
+          s0 += Dc.d[l * n + jj] * b[l];
+          s1 += Dc.d[(l + 1) * n + jj] * b[l + 1];
+        }
+        if (lane_ok) sS_e[jr * n2 + jj * n + ir] = s0 + s1;
+      }
+      __syncthreads();
+    }
 
 #pragma unroll
     for (int k = 0; k < n; ++k) {
-      float wv = wreg[k] + row_dot<n>(sr_e + k * n2 + jr * n, DiT);
+      float wv;
+      if constexpr (kSLine) {
+        wv = wreg[k] + (row_dot_2acc<n>(sr_e + k * n2 + jr * n, DiT) + sS_e[k * n2 + ij]);
+      } else if constexpr (kSplit) {
+        wv = wreg[k] + (row_dot_2acc<n>(sr_e + k * n2 + jr * n, DiT) +
+                        col_dot_2acc<n, n>(ss_e + k * n2 + ir, DjT));
+      } else {
+        wv = wreg[k] + row_dot<n>(sr_e + k * n2 + jr * n, DiT);
 #pragma unroll
-      for (int l = 0; l < n; ++l) wv += DjT[l] * ss_e[k * n2 + l * n + ir];
+        for (int l = 0; l < n; ++l) wv += DjT[l] * ss_e[k * n2 + l * n + ir];
+      }
       if (on_dirichlet(f, i, j, k, n - 1)) wv = 0.f;
       if (act) {
         if (l2h) st_hint(wout + e * n3 + k * n2 + ij, wv, pol_last);
