@@ -103,6 +103,45 @@ __device__ __forceinline__ float row_dot(const float* __restrict__ row, const fl
   return s;
 }
 
+// D by value for the staged kernel: the full matrix (row-major) and, for the
+// whole-line contractions, its even-odd halves.  GLL D is centro-antisymmetric
+// (D[N-i][N-l] = -D[i][l], nodes symmetric about 0), and so is D^T; for such
+// an M, with x_e[l] = x[l] + x[N-l] and x_o[l] = x[l] - x[N-l] (l < n/2),
+//   (M x)[i] = e_i + o_i,  (M x)[N-i] = o_i - e_i,
+//   e_i = sum_l E[i][l] x_e[l],  o_i = sum_l O[i][l] x_o[l],
+//   E[i][l] = (M[i][l] + M[i][N-l]) / 2,  O[i][l] = (M[i][l] - M[i][N-l]) / 2,
+// i.e. n^2/2 FMAs and 2n additions instead of n^2 FMAs per line.
+template <int n>
+struct DMatEO {
+  float d[n * n];
+  float E[(n / 2) * (n / 2)], O[(n / 2) * (n / 2)];     // M = D
+  float ET[(n / 2) * (n / 2)], OT[(n / 2) * (n / 2)];   // M = D^T
+};
+
+template <int n>
+__device__ __forceinline__ void eo_line(const float (&E)[(n / 2) * (n / 2)],
+                                        const float (&O)[(n / 2) * (n / 2)], const float (&x)[n],
+                                        float (&y)[n]) {
+  constexpr int h = n / 2;
+  float xe[h], xo[h];
+#pragma unroll
+  for (int l = 0; l < h; ++l) {
+    xe[l] = x[l] + x[n - 1 - l];
+    xo[l] = x[l] - x[n - 1 - l];
+  }
+#pragma unroll
+  for (int i = 0; i < h; ++i) {
+    float e = 0.f, o = 0.f;
+#pragma unroll
+    for (int l = 0; l < h; ++l) {
+      e += E[i * h + l] * xe[l];
+      o += O[i * h + l] * xo[l];
+    }
+    y[i] = e + o;
+    y[n - 1 - i] = o - e;
+  }
+}
+
 // Dot products with two independent accumulator chains (even and odd l,
 // added at the end): twice the instruction-level parallelism of one FMA
 // chain, for the orders where a block holds only a few warps.
@@ -143,7 +182,7 @@ template <int n, bool PCG, int DM, int V>
 __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     ax_tma_kernel(const float* __restrict__ uin, float* __restrict__ wout,
                   const float* __restrict__ G, const float* __restrict__ Dg,
-                  const __grid_constant__ DMat<n> Dc,
+                  const __grid_constant__ DMatEO<n> Dc,
                   const uint8_t* __restrict__ faces, int64_t E, const float* __restrict__ rr,
                   const float* __restrict__ minv, float* pp, PcgScalars* __restrict__ scal,
                   double* __restrict__ partials, int* __restrict__ err, int l2h) {
@@ -270,18 +309,13 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       // the whole line is D times the line, every D entry indexed by the
       // two unrolled counters (constant bank), written to the s-line buffer
       if (PCG) __syncthreads();   // p complete in shared memory
-      float a[n];
+      float a[n], y[n];
 #pragma unroll
       for (int l = 0; l < n; ++l) a[l] = su_e[jr * n2 + l * n + ir];
+      eo_line<n>(Dc.E, Dc.O, a, y);
+      if (lane_ok) {
 #pragma unroll
-      for (int jj = 0; jj < n; ++jj) {
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int l = 0; l < n; l += 2) {
-          s0 += Dc.d[jj * n + l] * a[l];
-          s1 += Dc.d[jj * n + l + 1] * a[l + 1];
-        }
-        if (lane_ok) sS_e[jr * n2 + jj * n + ir] = s0 + s1;
+        for (int jj = 0; jj < n; ++jj) sS_e[jr * n2 + jj * n + ir] = y[jj];
       }
       __syncthreads();
     } else {
@@ -326,18 +360,13 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       // transposed s-lines: w_s of line (i, k = j) = D^T times the line of
       // v_s, written back over the same line (this thread reads all of it
       // first; no other thread touches it)
-      float b[n];
+      float b[n], y[n];
 #pragma unroll
       for (int l = 0; l < n; ++l) b[l] = sS_e[jr * n2 + l * n + ir];
+      eo_line<n>(Dc.ET, Dc.OT, b, y);
+      if (lane_ok) {
 #pragma unroll
-      for (int jj = 0; jj < n; ++jj) {
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int l = 0; l < n; l += 2) {
-          s0 += Dc.d[l * n + jj] * b[l];
-          s1 += Dc.d[(l + 1) * n + jj] * b[l + 1];
-        }
-        if (lane_ok) sS_e[jr * n2 + jj * n + ir] = s0 + s1;
+        for (int jj = 0; jj < n; ++jj) sS_e[jr * n2 + jj * n + ir] = y[jj];
       }
       __syncthreads();
     }
@@ -432,8 +461,17 @@ int ax_tma_launch(Handle& h, const float* u, float* w, const AxPrologue* pro) {
   double* partials = PCG ? pro->pap_partials : nullptr;
   float* pp = PCG ? const_cast<float*>(u) : nullptr;
   const int l2h = PCG && h.l2_hints ? 1 : 0;
-  DMat<n> Dc;
+  DMatEO<n> Dc;
   for (int q = 0; q < n * n; ++q) Dc.d[q] = h.D32_host[q];
+  constexpr int hh = n / 2;
+  for (int a = 0; a < hh; ++a)
+    for (int l = 0; l < hh; ++l) {
+      const double* D = h.D64_host;   // halves formed in FP64, rounded once
+      Dc.E[a * hh + l] = (float)(0.5 * (D[a * n + l] + D[a * n + (n - 1 - l)]));
+      Dc.O[a * hh + l] = (float)(0.5 * (D[a * n + l] - D[a * n + (n - 1 - l)]));
+      Dc.ET[a * hh + l] = (float)(0.5 * (D[l * n + a] + D[(n - 1 - l) * n + a]));
+      Dc.OT[a * hh + l] = (float)(0.5 * (D[l * n + a] - D[(n - 1 - l) * n + a]));
+    }
   kern<<<grid, S::NT, smem, h.stream>>>(u, w, h.G32, h.D32, Dc, h.bfaces, h.E, r, minv, pp,
                                         scal, partials, h.dev_err, l2h);
   ++h.launches;
