@@ -142,6 +142,41 @@ __device__ __forceinline__ void eo_line(const float (&E)[(n / 2) * (n / 2)],
   }
 }
 
+// A row of n contiguous shared-memory floats (16- or 8-byte aligned) to and
+// from registers with the widest vector accesses the alignment allows.
+template <int n>
+__device__ __forceinline__ void load_row(const float* __restrict__ row, float (&x)[n]) {
+  if constexpr (n % 4 == 0) {
+#pragma unroll
+    for (int l = 0; l < n; l += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(row + l);
+      x[l] = v.x;
+      x[l + 1] = v.y;
+      x[l + 2] = v.z;
+      x[l + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < n; l += 2) {
+      const float2 v = *reinterpret_cast<const float2*>(row + l);
+      x[l] = v.x;
+      x[l + 1] = v.y;
+    }
+  }
+}
+template <int n>
+__device__ __forceinline__ void store_row(float* __restrict__ row, const float (&x)[n]) {
+  if constexpr (n % 4 == 0) {
+#pragma unroll
+    for (int l = 0; l < n; l += 4)
+      *reinterpret_cast<float4*>(row + l) = make_float4(x[l], x[l + 1], x[l + 2], x[l + 3]);
+  } else {
+#pragma unroll
+    for (int l = 0; l < n; l += 2)
+      *reinterpret_cast<float2*>(row + l) = make_float2(x[l], x[l + 1]);
+  }
+}
+
 // Dot products with two independent accumulator chains (even and odd l,
 // added at the end): twice the instruction-level parallelism of one FMA
 // chain, for the orders where a block holds only a few warps.
@@ -305,11 +340,13 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     }
     float* const sS_e = sS + ler * n3;
     if constexpr (kSLine) {
-      // s-lines: this thread also owns the line (i, k = j) along s; u_s of
-      // the whole line is D times the line, every D entry indexed by the
-      // two unrolled counters (constant bank), written to the s-line buffer
+      // line contractions: besides its t-column (i, j) this thread owns the
+      // s-line (i, k = j) and the r-line (j = i, k = j) of the element.  u_s
+      // and u_r of a whole line are D times the line by the even-odd halves
+      // (constant bank); u_s goes to the s-line buffer at once, u_r over the
+      // same row of u once every thread has read u
       if (PCG) __syncthreads();   // p complete in shared memory
-      float a[n], y[n];
+      float a[n], y[n], yr[n];
 #pragma unroll
       for (int l = 0; l < n; ++l) a[l] = su_e[jr * n2 + l * n + ir];
       eo_line<n>(Dc.E, Dc.O, a, y);
@@ -317,11 +354,19 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
 #pragma unroll
         for (int jj = 0; jj < n; ++jj) sS_e[jr * n2 + jj * n + ir] = y[jj];
       }
+      load_row<n>(su_e + jr * n2 + ir * n, a);
+      eo_line<n>(Dc.E, Dc.O, a, yr);
+      __syncthreads();
+      if (lane_ok) store_row<n>(su_e + jr * n2 + ir * n, yr);
       __syncthreads();
     } else {
       if (PCG) __syncthreads();
     }
 
+    // line orders: u_t of the whole t-column by the even-odd halves, and the
+    // t-column of v_t kept for the transposed product after the plane loop
+    float utk[kSLine ? n : 1], vtk[kSLine ? n : 1];
+    if constexpr (kSLine) eo_line<n>(Dc.E, Dc.O, ureg, utk);
     float wreg[n];
 #pragma unroll
     for (int k = 0; k < n; ++k) wreg[k] = 0.f;
@@ -329,8 +374,9 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     for (int k = 0; k < n; ++k) {
       float ur, us, ut = 0.f;
       if constexpr (kSLine) {
-        ur = row_dot_2acc<n>(su_e + k * n2 + jr * n, Di);
+        ur = su_e[k * n2 + ij];
         us = sS_e[k * n2 + ij];
+        ut = utk[k];
       } else if constexpr (kSplit) {
         ur = row_dot_2acc<n>(su_e + k * n2 + jr * n, Di);
         us = col_dot_2acc<n, n>(su_e + k * n2 + ir, Dj);
@@ -340,8 +386,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
 #pragma unroll
         for (int l = 0; l < n; ++l) us += Dj[l] * su_e[k * n2 + l * n + ir];
       }
+      if constexpr (!kSLine) {
 #pragma unroll
-      for (int l = 0; l < n; ++l) ut += Dc.d[k * n + l] * ureg[l];
+        for (int l = 0; l < n; ++l) ut += Dc.d[k * n + l] * ureg[l];
+      }
       const float g0 = Gs[0 * n3 + k * n2], g1 = Gs[1 * n3 + k * n2], g2 = Gs[2 * n3 + k * n2];
       const float g3 = Gs[3 * n3 + k * n2], g4 = Gs[4 * n3 + k * n2], g5 = Gs[5 * n3 + k * n2];
       const float vr = g0 * ur + g3 * us + g4 * ut;
@@ -352,14 +400,21 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         if constexpr (kSLine) sS_e[k * n2 + ij] = vs;   // over this thread's own u_s
         else ss_e[k * n2 + ij] = vs;
       }
+      if constexpr (kSLine) {
+        vtk[k] = vt;
+      } else {
 #pragma unroll
-      for (int kk = 0; kk < n; ++kk) wreg[kk] += Dc.d[k * n + kk] * vt;
+        for (int kk = 0; kk < n; ++kk) wreg[kk] += Dc.d[k * n + kk] * vt;
+      }
     }
+    if constexpr (kSLine) eo_line<n>(Dc.ET, Dc.OT, vtk, wreg);
     __syncthreads();
     if constexpr (kSLine) {
       // transposed s-lines: w_s of line (i, k = j) = D^T times the line of
       // v_s, written back over the same line (this thread reads all of it
       // first; no other thread touches it)
+      // and w_r of the r-line (j = i, k = j) = D^T times the row of v_r, in
+      // place as well
       float b[n], y[n];
 #pragma unroll
       for (int l = 0; l < n; ++l) b[l] = sS_e[jr * n2 + l * n + ir];
@@ -368,6 +423,9 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
 #pragma unroll
         for (int jj = 0; jj < n; ++jj) sS_e[jr * n2 + jj * n + ir] = y[jj];
       }
+      load_row<n>(sr_e + jr * n2 + ir * n, b);
+      eo_line<n>(Dc.ET, Dc.OT, b, y);
+      if (lane_ok) store_row<n>(sr_e + jr * n2 + ir * n, y);
       __syncthreads();
     }
 
@@ -375,7 +433,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     for (int k = 0; k < n; ++k) {
       float wv;
       if constexpr (kSLine) {
-        wv = wreg[k] + (row_dot_2acc<n>(sr_e + k * n2 + jr * n, DiT) + sS_e[k * n2 + ij]);
+        wv = wreg[k] + (sr_e[k * n2 + ij] + sS_e[k * n2 + ij]);
       } else if constexpr (kSplit) {
         wv = wreg[k] + (row_dot_2acc<n>(sr_e + k * n2 + jr * n, DiT) +
                         col_dot_2acc<n, n>(ss_e + k * n2 + ir, DjT));
