@@ -53,15 +53,24 @@ struct TmaShape {
 // shared-memory buffer of one element (see ax_tma_kernel).
 template <int n>
 constexpr bool tma_sline() {
-  return n >= 10 && n <= 14;
+  return n >= 10;
+}
+// Orders whose stages hold G only: u (PCG mode: r, J^{-1}, p_old) is read
+// by the threads themselves, one group ahead into registers, and stored to
+// a single shared buffer; at n = 16 two stages of u and G plus the line
+// buffer would exceed shared memory, two stages of G plus u and the line
+// buffer fit.
+template <int n>
+constexpr bool tma_gonly() {
+  return n == 16;
 }
 
 template <int n, bool PCG, int V>
 constexpr size_t tma_smem_bytes() {
   using S = TmaShape<n, V>;
-  constexpr int NV = PCG ? 3 : 1;
-  return S::NS * (size_t)(NV + 6) * S::VEC + (tma_sline<n>() ? S::VEC : 0) +
-         S::NS * sizeof(uint64_t);
+  constexpr int NV = tma_gonly<n>() ? 0 : (PCG ? 3 : 1);   // vectors in a stage
+  constexpr int NB = tma_gonly<n>() ? 2 : (tma_sline<n>() ? 1 : 0);   // single buffers
+  return S::NS * (size_t)(NV + 6) * S::VEC + NB * S::VEC + S::NS * sizeof(uint64_t);
 }
 
 // Shared memory per block on sm_100/sm_103 (227 KB) and the static part of
@@ -223,7 +232,8 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
                   double* __restrict__ partials, int* __restrict__ err, int l2h) {
   using S = TmaShape<n, V>;
   constexpr int n2 = S::n2, n3 = S::n3, EPB = S::EPB, NS = S::NS;
-  constexpr int NV = PCG ? 3 : 1;
+  constexpr bool kGOnly = tma_gonly<n>();
+  constexpr int NV = kGOnly ? 0 : (PCG ? 3 : 1);   // vectors staged with G
   constexpr int SV = EPB * n3;                 // floats of one vector per stage
   constexpr int STAGE = (NV + 6) * SV;         // floats per stage
   // n >= 10: split accumulator chains (one or two blocks of few warps per SM)
@@ -231,8 +241,12 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   constexpr bool kSLine = tma_sline<n>();
   extern __shared__ __align__(128) float smem_f[];
   float* const stage0 = smem_f;
-  float* const sS = smem_f + NS * STAGE;   // s-line buffer (kSLine): u_s, v_s, then w_s
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + NS * STAGE + (kSLine ? SV : 0));
+  // kGOnly: u (or p) of the group, then u_r; kSLine: the s-line buffer
+  // (u_s, v_s, then w_s)
+  float* const sU = smem_f + NS * STAGE;
+  float* const sS = smem_f + NS * STAGE + (kGOnly ? SV : 0);
+  uint64_t* const bar =
+      reinterpret_cast<uint64_t*>(smem_f + NS * STAGE + (kGOnly ? 2 * SV : (kSLine ? SV : 0)));
   __shared__ float sD[n][n + 1];
   __shared__ double sh_red[S::NT / 32];
 
@@ -257,6 +271,11 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     const uint32_t vb = (uint32_t)(cnt * n3 * 4);
     float* dst = stage0 + st * STAGE;
     mbar_arrive_expect_tx(&bar[st], (NV + 6) * vb);
+    if (kGOnly) {
+      if (l2h) bulk_load_hint(dst, G + e0 * 6 * n3, 6 * vb, &bar[st], pol_first);
+      else bulk_load(dst, G + e0 * 6 * n3, 6 * vb, &bar[st]);
+      return;
+    }
     if (l2h) {
       if (PCG) {
         bulk_load_hint(dst, rr + e0 * n3, vb, &bar[st], pol_first);
@@ -299,6 +318,29 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     DjT[l] = sD[l][jr];
   }
 
+  // kGOnly: the next group's vectors, read one group ahead (u; PCG mode r,
+  // J^{-1}, p_old of this thread's column)
+  float pa[kGOnly ? n : 1], pb[kGOnly && PCG ? n : 1], pc[kGOnly && PCG ? n : 1];
+  auto prefetch = [&](int64_t gq) {
+    if constexpr (kGOnly) {
+      const int64_t eq = gq * EPB + le;
+      if (lane_ok && gq < ngroups && eq < E) {
+        const int64_t b0 = eq * n3 + ij;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          if (PCG) {
+            pa[k] = __ldg(rr + b0 + k * n2);
+            pb[k] = __ldg(minv + b0 + k * n2);
+            pc[k] = pp[b0 + k * n2];   // written by this kernel (other elements)
+          } else {
+            pa[k] = __ldg(uin + b0 + k * n2);
+          }
+        }
+      }
+    }
+  };
+  prefetch(blockIdx.x);
+
   DotAcc<float, DM> acc;
   bool aborted = false;
   int t = 0;
@@ -312,7 +354,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       break;
     }
     float* const sb = stage0 + st * STAGE;
-    float* const su = PCG ? sb + 2 * SV : sb;   // p (formed in place) or u
+    float* const su = kGOnly ? sU : (PCG ? sb + 2 * SV : sb);   // p (formed in place) or u
     const float* const Gs = sb + NV * SV + ler * 6 * n3 + ij;
     float* const su_e = su + ler * n3;
     // the two transposed-contraction inputs overwrite G1 and G2 of the
@@ -326,17 +368,27 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     const uint8_t f = act ? faces[e] : uint8_t(0);   // issued early, used in the epilogue
 
     float ureg[n];
+    if constexpr (kGOnly) {
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-      const int si = k * n2 + ij;
-      float v;
-      if (PCG) {
-        v = sb[SV + ler * n3 + si] * sb[ler * n3 + si] + beta * su_e[si];
-        if (lane_ok) su_e[si] = v;   // p goes to memory with w in the epilogue
-      } else {
-        v = su_e[si];
+      for (int k = 0; k < n; ++k) {
+        const float v = PCG ? pb[k] * pa[k] + beta * pc[k] : pa[k];
+        ureg[k] = v;
+        if (lane_ok) su_e[k * n2 + ij] = v;
       }
-      ureg[k] = v;
+      prefetch(g + gridDim.x);
+    } else {
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        const int si = k * n2 + ij;
+        float v;
+        if (PCG) {
+          v = sb[SV + ler * n3 + si] * sb[ler * n3 + si] + beta * su_e[si];
+          if (lane_ok) su_e[si] = v;   // p goes to memory with w in the epilogue
+        } else {
+          v = su_e[si];
+        }
+        ureg[k] = v;
+      }
     }
     float* const sS_e = sS + ler * n3;
     if constexpr (kSLine) {
@@ -345,7 +397,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       // and u_r of a whole line are D times the line by the even-odd halves
       // (constant bank); u_s goes to the s-line buffer at once, u_r over the
       // same row of u once every thread has read u
-      if (PCG) __syncthreads();   // p complete in shared memory
+      if (PCG || kGOnly) __syncthreads();   // u or p complete in shared memory
       float a[n], y[n], yr[n];
 #pragma unroll
       for (int l = 0; l < n; ++l) a[l] = su_e[jr * n2 + l * n + ir];
