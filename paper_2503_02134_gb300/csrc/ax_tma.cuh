@@ -186,6 +186,54 @@ __device__ __forceinline__ void store_row(float* __restrict__ row, const float (
   }
 }
 
+// Layout of the line buffers.  Node (i, j, k) of an element sits at
+// k n^2 + j n + i (the bulk-copied layout) except in the thread-written
+// buffers at n = 16, where 64-byte rows and 1 KB planes put the accesses of
+// the s-lines (the same row in two planes) and of the r-lines (eight rows
+// of a plane, 16 bytes each) on the same banks.  There the row index is
+// flipped in odd planes and the 16-byte chunks of a row are permuted by the
+// row pair: (i, j, k) -> k 256 + r 16 + (i ^ 4 ((r >> 1) & 3)), r = j ^ (k & 1),
+// which makes the column, s-line and r-line accesses conflict-free.
+template <int n, bool kSwz>
+__device__ __forceinline__ int lb_at(int i, int j, int k) {
+  if constexpr (kSwz) {
+    static_assert(n == 16, "the swizzled layout is for n = 16");
+    const int r = j ^ (k & 1);
+    return k * 256 + r * 16 + (i ^ (((r >> 1) & 3) << 2));
+  } else {
+    return (k * n + j) * n + i;
+  }
+}
+// Row (j, k) to and from registers in either layout.
+template <int n, bool kSwz>
+__device__ __forceinline__ void load_row_lb(const float* __restrict__ buf, int j, int k,
+                                            float (&x)[n]) {
+  if constexpr (kSwz) {
+#pragma unroll
+    for (int c = 0; c < n / 4; ++c) {
+      const float4 v = *reinterpret_cast<const float4*>(buf + lb_at<n, true>(4 * c, j, k));
+      x[4 * c] = v.x;
+      x[4 * c + 1] = v.y;
+      x[4 * c + 2] = v.z;
+      x[4 * c + 3] = v.w;
+    }
+  } else {
+    load_row<n>(buf + (k * n + j) * n, x);
+  }
+}
+template <int n, bool kSwz>
+__device__ __forceinline__ void store_row_lb(float* __restrict__ buf, int j, int k,
+                                             const float (&x)[n]) {
+  if constexpr (kSwz) {
+#pragma unroll
+    for (int c = 0; c < n / 4; ++c)
+      *reinterpret_cast<float4*>(buf + lb_at<n, true>(4 * c, j, k)) =
+          make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+  } else {
+    store_row<n>(buf + (k * n + j) * n, x);
+  }
+}
+
 // Dot products with two independent accumulator chains (even and odd l,
 // added at the end): twice the instruction-level parallelism of one FMA
 // chain, for the orders where a block holds only a few warps.
@@ -239,6 +287,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   // n >= 10: split accumulator chains (one or two blocks of few warps per SM)
   constexpr bool kSplit = n >= 10;
   constexpr bool kSLine = tma_sline<n>();
+  constexpr bool kSwz = kGOnly && n == 16;   // swizzled thread-written line buffers
   extern __shared__ __align__(128) float smem_f[];
   float* const stage0 = smem_f;
   // kGOnly: u (or p) of the group, then u_r; kSLine: the s-line buffer
@@ -373,7 +422,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       for (int k = 0; k < n; ++k) {
         const float v = PCG ? pb[k] * pa[k] + beta * pc[k] : pa[k];
         ureg[k] = v;
-        if (lane_ok) su_e[k * n2 + ij] = v;
+        if (lane_ok) su_e[lb_at<n, kSwz>(i, j, k)] = v;
       }
       prefetch(g + gridDim.x);
     } else {
@@ -400,16 +449,16 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       if (PCG || kGOnly) __syncthreads();   // u or p complete in shared memory
       float a[n], y[n], yr[n];
 #pragma unroll
-      for (int l = 0; l < n; ++l) a[l] = su_e[jr * n2 + l * n + ir];
+      for (int l = 0; l < n; ++l) a[l] = su_e[lb_at<n, kSwz>(ir, l, jr)];
       eo_line<n>(Dc.E, Dc.O, a, y);
       if (lane_ok) {
 #pragma unroll
-        for (int jj = 0; jj < n; ++jj) sS_e[jr * n2 + jj * n + ir] = y[jj];
+        for (int jj = 0; jj < n; ++jj) sS_e[lb_at<n, kSwz>(ir, jj, jr)] = y[jj];
       }
-      load_row<n>(su_e + jr * n2 + ir * n, a);
+      load_row_lb<n, kSwz>(su_e, ir, jr, a);
       eo_line<n>(Dc.E, Dc.O, a, yr);
       __syncthreads();
-      if (lane_ok) store_row<n>(su_e + jr * n2 + ir * n, yr);
+      if (lane_ok) store_row_lb<n, kSwz>(su_e, ir, jr, yr);
       __syncthreads();
     } else {
       if (PCG) __syncthreads();
@@ -426,8 +475,8 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     for (int k = 0; k < n; ++k) {
       float ur, us, ut = 0.f;
       if constexpr (kSLine) {
-        ur = su_e[k * n2 + ij];
-        us = sS_e[k * n2 + ij];
+        ur = su_e[lb_at<n, kSwz>(i, j, k)];
+        us = sS_e[lb_at<n, kSwz>(i, j, k)];
         ut = utk[k];
       } else if constexpr (kSplit) {
         ur = row_dot_2acc<n>(su_e + k * n2 + jr * n, Di);
@@ -448,8 +497,11 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       const float vs = g3 * ur + g1 * us + g5 * ut;
       const float vt = g4 * ur + g5 * us + g2 * ut;
       if (lane_ok) {
-        sr_e[k * n2 + ij] = vr;
-        if constexpr (kSLine) sS_e[k * n2 + ij] = vs;   // over this thread's own u_s
+        // v_r over G1 of the stage, or with the stages holding G only over
+        // this thread's own u_r; v_s over its own u_s
+        if constexpr (kGOnly) su_e[lb_at<n, kSwz>(i, j, k)] = vr;
+        else sr_e[k * n2 + ij] = vr;
+        if constexpr (kSLine) sS_e[lb_at<n, kSwz>(i, j, k)] = vs;
         else ss_e[k * n2 + ij] = vs;
       }
       if constexpr (kSLine) {
@@ -469,15 +521,16 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       // place as well
       float b[n], y[n];
 #pragma unroll
-      for (int l = 0; l < n; ++l) b[l] = sS_e[jr * n2 + l * n + ir];
+      for (int l = 0; l < n; ++l) b[l] = sS_e[lb_at<n, kSwz>(ir, l, jr)];
       eo_line<n>(Dc.ET, Dc.OT, b, y);
       if (lane_ok) {
 #pragma unroll
-        for (int jj = 0; jj < n; ++jj) sS_e[jr * n2 + jj * n + ir] = y[jj];
+        for (int jj = 0; jj < n; ++jj) sS_e[lb_at<n, kSwz>(ir, jj, jr)] = y[jj];
       }
-      load_row<n>(sr_e + jr * n2 + ir * n, b);
+      float* const vr_e = kGOnly ? su_e : sr_e;
+      load_row_lb<n, kSwz>(vr_e, ir, jr, b);
       eo_line<n>(Dc.ET, Dc.OT, b, y);
-      if (lane_ok) store_row<n>(sr_e + jr * n2 + ir * n, y);
+      if (lane_ok) store_row_lb<n, kSwz>(vr_e, ir, jr, y);
       __syncthreads();
     }
 
@@ -485,7 +538,8 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     for (int k = 0; k < n; ++k) {
       float wv;
       if constexpr (kSLine) {
-        wv = wreg[k] + (sr_e[k * n2 + ij] + sS_e[k * n2 + ij]);
+        const float wr = kGOnly ? su_e[lb_at<n, kSwz>(i, j, k)] : sr_e[k * n2 + ij];
+        wv = wreg[k] + (wr + sS_e[lb_at<n, kSwz>(i, j, k)]);
       } else if constexpr (kSplit) {
         wv = wreg[k] + (row_dot_2acc<n>(sr_e + k * n2 + jr * n, DiT) +
                         col_dot_2acc<n, n>(ss_e + k * n2 + ir, DjT));
