@@ -65,12 +65,24 @@ constexpr bool tma_gonly() {
   return n == 16;
 }
 
+// Plane stride of the s-line buffer: the smallest P >= n^2 with P = n
+// (mod 32), so that the n-thread runs of a warp in consecutive planes fall
+// on consecutive banks (n = 16 keeps 256 and uses the swizzled layout).
+template <int n>
+constexpr int tma_ps() {
+  if (n == 16) return 256;
+  int P = n * n;
+  while (P % 32 != n % 32) ++P;
+  return P;
+}
+
 template <int n, bool PCG, int V>
 constexpr size_t tma_smem_bytes() {
   using S = TmaShape<n, V>;
   constexpr int NV = tma_gonly<n>() ? 0 : (PCG ? 3 : 1);   // vectors in a stage
-  constexpr int NB = tma_gonly<n>() ? 2 : (tma_sline<n>() ? 1 : 0);   // single buffers
-  return S::NS * (size_t)(NV + 6) * S::VEC + NB * S::VEC + S::NS * sizeof(uint64_t);
+  constexpr size_t ubuf = tma_gonly<n>() ? S::VEC : 0;      // thread-written u
+  constexpr size_t sbuf = tma_sline<n>() ? (size_t)S::EPB * n * tma_ps<n>() * 4 : 0;
+  return S::NS * (size_t)(NV + 6) * S::VEC + ubuf + sbuf + S::NS * sizeof(uint64_t);
 }
 
 // Shared memory per block on sm_100/sm_103 (227 KB) and the static part of
@@ -204,6 +216,12 @@ __device__ __forceinline__ int lb_at(int i, int j, int k) {
     return (k * n + j) * n + i;
   }
 }
+// The s-line buffer: swizzled at n = 16, otherwise planes of tma_ps<n>().
+template <int n, bool kSwz>
+__device__ __forceinline__ int sb_at(int i, int j, int k) {
+  if constexpr (kSwz) return lb_at<n, true>(i, j, k);
+  else return k * tma_ps<n>() + j * n + i;
+}
 // Row (j, k) to and from registers in either layout.
 template <int n, bool kSwz>
 __device__ __forceinline__ void load_row_lb(const float* __restrict__ buf, int j, int k,
@@ -292,10 +310,11 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   float* const stage0 = smem_f;
   // kGOnly: u (or p) of the group, then u_r; kSLine: the s-line buffer
   // (u_s, v_s, then w_s)
+  constexpr int SSE = n * tma_ps<n>();                 // floats of one element's s-lines
   float* const sU = smem_f + NS * STAGE;
   float* const sS = smem_f + NS * STAGE + (kGOnly ? SV : 0);
-  uint64_t* const bar =
-      reinterpret_cast<uint64_t*>(smem_f + NS * STAGE + (kGOnly ? 2 * SV : (kSLine ? SV : 0)));
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + NS * STAGE + (kGOnly ? SV : 0) +
+                                                    (kSLine ? EPB * SSE : 0));
   __shared__ float sD[n][n + 1];
   __shared__ double sh_red[S::NT / 32];
 
@@ -439,7 +458,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         ureg[k] = v;
       }
     }
-    float* const sS_e = sS + ler * n3;
+    float* const sS_e = sS + ler * SSE;
     if constexpr (kSLine) {
       // line contractions: besides its t-column (i, j) this thread owns the
       // s-line (i, k = j) and the r-line (j = i, k = j) of the element.  u_s
@@ -453,7 +472,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       eo_line<n>(Dc.E, Dc.O, a, y);
       if (lane_ok) {
 #pragma unroll
-        for (int jj = 0; jj < n; ++jj) sS_e[lb_at<n, kSwz>(ir, jj, jr)] = y[jj];
+        for (int jj = 0; jj < n; ++jj) sS_e[sb_at<n, kSwz>(ir, jj, jr)] = y[jj];
       }
       load_row_lb<n, kSwz>(su_e, ir, jr, a);
       eo_line<n>(Dc.E, Dc.O, a, yr);
@@ -476,7 +495,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       float ur, us, ut = 0.f;
       if constexpr (kSLine) {
         ur = su_e[lb_at<n, kSwz>(i, j, k)];
-        us = sS_e[lb_at<n, kSwz>(i, j, k)];
+        us = sS_e[sb_at<n, kSwz>(i, j, k)];
         ut = utk[k];
       } else if constexpr (kSplit) {
         ur = row_dot_2acc<n>(su_e + k * n2 + jr * n, Di);
@@ -501,7 +520,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         // this thread's own u_r; v_s over its own u_s
         if constexpr (kGOnly) su_e[lb_at<n, kSwz>(i, j, k)] = vr;
         else sr_e[k * n2 + ij] = vr;
-        if constexpr (kSLine) sS_e[lb_at<n, kSwz>(i, j, k)] = vs;
+        if constexpr (kSLine) sS_e[sb_at<n, kSwz>(i, j, k)] = vs;
         else ss_e[k * n2 + ij] = vs;
       }
       if constexpr (kSLine) {
@@ -521,11 +540,11 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       // place as well
       float b[n], y[n];
 #pragma unroll
-      for (int l = 0; l < n; ++l) b[l] = sS_e[lb_at<n, kSwz>(ir, l, jr)];
+      for (int l = 0; l < n; ++l) b[l] = sS_e[sb_at<n, kSwz>(ir, l, jr)];
       eo_line<n>(Dc.ET, Dc.OT, b, y);
       if (lane_ok) {
 #pragma unroll
-        for (int jj = 0; jj < n; ++jj) sS_e[lb_at<n, kSwz>(ir, jj, jr)] = y[jj];
+        for (int jj = 0; jj < n; ++jj) sS_e[sb_at<n, kSwz>(ir, jj, jr)] = y[jj];
       }
       float* const vr_e = kGOnly ? su_e : sr_e;
       load_row_lb<n, kSwz>(vr_e, ir, jr, b);
@@ -539,7 +558,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       float wv;
       if constexpr (kSLine) {
         const float wr = kGOnly ? su_e[lb_at<n, kSwz>(i, j, k)] : sr_e[k * n2 + ij];
-        wv = wreg[k] + (wr + sS_e[lb_at<n, kSwz>(i, j, k)]);
+        wv = wreg[k] + (wr + sS_e[sb_at<n, kSwz>(i, j, k)]);
       } else if constexpr (kSplit) {
         wv = wreg[k] + (row_dot_2acc<n>(sr_e + k * n2 + jr * n, DiT) +
                         col_dot_2acc<n, n>(ss_e + k * n2 + ir, DjT));
