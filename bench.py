@@ -79,14 +79,25 @@ def peaks():
 
 
 def fp64_peak(num_sms):
-    """FP64 FMA peak of the GPU in TFLOP/s: SMs x 4 flop per clock (two FP64
-    FMAs per SM and clock, the rate behind GB300's nominal 1.25 TFLOP/s) x
-    the maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+    """Nominal FP64 FMA rate in TFLOP/s, for context beside the measured one:
+    SMs x 4 flop per clock (two FP64 FMAs per SM and clock, the rate behind
+    GB300's nominal 1.25 TFLOP/s) x the maximum SM clock
+    (MEASURED_PEAKS.json, else 2070 MHz)."""
     mhz = 2070.0
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
     return num_sms * 4 * mhz * 1e6 / 1e12, f"derived: {num_sms} SMs x 4 FP64 flop/clock x {mhz:.0f} MHz"
+
+
+def fma_peaks(sem):
+    """Measured FMA throughput of the CUDA cores (sem_fma_peak: 8 independent
+    FMA chains per thread, 4 blocks of 256 threads per SM, CUDA events), in
+    TFLOP/s: the roofline denominator of the compute-bound FP64 operator."""
+    return {"fp64_tflops": sem.sem_fma_peak(True, 4096),
+            "fp32_tflops": sem.sem_fma_peak(False, 262144),
+            "method": "sem_fma_peak: 8 FMA chains per thread, 4 x 256 threads per SM, "
+                      "one warm-up and one timed launch (CUDA events); no clock or power change"}
 
 
 class Clocks:
@@ -143,6 +154,66 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _single_thread_env():
+    """Pool initializer: one BLAS/OpenMP thread per oracle process (set before
+    the worker imports numpy)."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
+def _oracle_ax_worker(args):
+    """One oracle process: builds a deformed k^3 box at order N (untimed),
+    waits for the common start time, then times `reps` calls of the oracle's
+    ax_local as it stands.  Returns (local DOFs, reps, seconds)."""
+    N, k, reps, start_at = args
+    import numpy as np
+    from oracle import sem_oracle as so
+    P = so.Problem(k, k, k, N, deform=True)
+    u = np.random.default_rng(N).uniform(-1.0, 1.0, P.L)
+    P.ax_local(u)   # first touch
+    while time.time() < start_at:
+        time.sleep(0.01)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        P.ax_local(u)
+    return P.L, reps, time.perf_counter() - t0
+
+
+def cpu_legs(orders=(5, 7, 9, 11, 13, 15), k=8, reps=3):
+    """The oracle (unchanged) on the host cores, beside the GPU numbers:
+    config 1's full FP64 Jacobi PCG solve to 1e-10 (one core), and config 3's
+    element operator per order on one core and on every core (one spawned
+    process per core, each applying the oracle's ax_local to its own
+    deformed k^3-element box, all started together; throughput = all local
+    DOFs / the slowest process's time).  The oracle is single-threaded numpy
+    (einsum contractions), so one process is one core."""
+    import multiprocessing as mp
+    from oracle import sem_oracle as so
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    out = {"cores_available": cores, "kind": "oracle"}
+    P1 = so.Problem(4, 4, 4, 7)
+    b1 = P1.rhs_sine()
+    t0 = time.perf_counter()
+    _, it1, hist1 = P1.pcg(b1, tol=1e-10, maxit=500)
+    dt1 = time.perf_counter() - t0
+    out["config1_fp64_pcg_to_1e-10"] = {"time_s": dt1, "iterations": it1, "relres": hist1[-1],
+                                        "cores": 1, "local_dofs": P1.L}
+    sweep = []
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_single_thread_env) as pool:
+        for N in orders:
+            L1, r1, t1 = _oracle_ax_worker((N, k, reps, 0.0))
+            start = time.time() + 4.0 + 0.02 * N * N   # after every worker's (untimed) build
+            res = pool.map(_oracle_ax_worker, [(N, k, reps, start)] * cores)
+            tmax = max(r[2] for r in res)
+            sweep.append({"N": N, "elements_per_process": k ** 3, "local_dofs_per_process": L1,
+                          "gdofs_1core": L1 * r1 / t1 / 1e9,
+                          "gdofs_all_cores": sum(r[0] * r[1] for r in res) / tmax / 1e9,
+                          "cores": cores})
+    out["config3_ax"] = sweep
+    return out
 
 
 def cpu_baseline(sample=CPU_SAMPLE):
@@ -224,7 +295,7 @@ def batched_leg(sem, torch):
     return out
 
 
-def order_sweep_leg(sem, torch, hbm_gbs):
+def order_sweep_leg(sem, torch, hbm_gbs, fp64_peak_tflops):
     """Deformed cubes of about 2^24 local DOFs at N = 5, 7, ..., 15: FP32 and
     FP64 operator (sem_ax_local) throughput with CUDA events, fraction of
     the HBM roofline (FP32: 32 B per DOF), FP64 flop rate (12 n^4 + 15 n^3
@@ -272,6 +343,7 @@ def order_sweep_leg(sem, torch, hbm_gbs):
                     "fp32_gdofs": L / ms32 / 1e6, "fp32_hbm_frac": L * 32 / (ms32 * 1e-3) / 1e9 / hbm_gbs,
                     "fp32_tflops": flops / (ms32 * 1e-3) / 1e12,
                     "fp64_gdofs": L / ms64 / 1e6, "fp64_tflops": flops / (ms64 * 1e-3) / 1e12,
+                    "fp64_frac_of_measured_fma_peak": flops / (ms64 * 1e-3) / 1e12 / fp64_peak_tflops,
                     "fp32_rel_err_vs_fp64": err, "tensor_cores": tc,
                     "fp32_kernel": "bulk-copy staged" if n % 2 == 0 else "register/shared (unstaged)",
                     "fp32_variant": int(sem.sem_get_option(S.h, "ax_variant")),
@@ -681,13 +753,16 @@ def main():
     n_gll = W["N"] + 1
     flops64 = S.E * (12 * n_gll ** 4 + 15 * n_gll ** 3)
     ach64 = flops64 / (ax64_ms * 1e-3) / 1e12
-    peak64, peak64_source = fp64_peak(torch.cuda.get_device_properties(0).multi_processor_count)
+    fma = fma_peaks(sem)
+    peak64 = fma["fp64_tflops"]
+    nominal64, nominal64_how = fp64_peak(torch.cuda.get_device_properties(0).multi_processor_count)
     traffic64 = TRAFFIC.get("operator_fp64")
     roofline_fp64 = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
                      "frac": ach64 / peak64, "traffic": traffic64 * L if traffic64 else None,
                      "kernel": f"ax_kernel<{n_gll},double> (sem_ax_local, FP64 operator)",
                      "algorithmic_flops_per_launch": flops64, "launch_ms": ax64_ms,
-                     "peak_source": peak64_source}
+                     "peak_source": "measured: " + fma["method"],
+                     "nominal_peak": nominal64, "nominal_peak_source": nominal64_how}
 
     # end to end through the C-ABI with host (pinned) buffers
     fh = torch.empty(L, dtype=torch.float64, pin_memory=True)
@@ -727,7 +802,7 @@ def main():
             "ax_gdofs_fp32_with_gs": L / (ax32_full_ms * 1e-3) / 1e9,
             "ax_gdofs_fp64": L / (ax64_ms * 1e-3) / 1e9,
             "roofline": roofline, "roofline_operator_plain": roofline_plain,
-            "roofline_operator_fp64": roofline_fp64,
+            "roofline_operator_fp64": roofline_fp64, "fma_peaks_measured": fma,
             "kernel_ms": {"operator_pcg": kt["kt_ms_ax"], "gather_scatter": kt["kt_ms_gs"],
                           "update": kt["kt_ms_update"]},
             "kernel_share_of_step": shares,
@@ -745,9 +820,12 @@ def main():
         if not args.no_learned:
             line["learned_x0"] = learned_leg(sem, torch)
         if not args.no_sweep:
-            line["order_sweep"] = order_sweep_leg(sem, torch, hbm)
+            line["order_sweep"] = order_sweep_leg(sem, torch, hbm, peak64)
         if not args.no_cpu and world >= 1:
             line["cpu_baseline"] = cpu_baseline()
+            cb = line["cpu_baseline"]
+            line["cpu_oracle_legs"] = cpu_legs()
+            line["cpu_oracle_legs"]["config2_per_iteration_ms_1core"] = L / (cb["value"] * 1e9) * 1e3
         print(json.dumps(line))
     S.close()
     if world > 1:

@@ -281,6 +281,17 @@ void sem_batch_destroy(sem_batch b);
 int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t n,
                       double* result, void* stream);
 
+/* Measured FMA throughput of the CUDA cores (the paper has no counterpart:
+ * it is the roofline denominator of the compute-bound FP64 operator).
+ * Launches, on the current device and the legacy default stream, 4 blocks
+ * of 256 threads per SM, each thread running 8 independent FMA chains for
+ * `iters` steps (a multiple of 4 is used), once to warm up and once timed
+ * with CUDA events; *tflops = 2 * 8 * steps * threads / time.  fp64: 1 for
+ * FP64 (DFMA), 0 for FP32 (FFMA).  Changes no clock or power setting.
+ * Returns SEM_EINVAL for iters < 4 or a null result, SEM_ECUDA on a CUDA
+ * error. */
+int sem_fma_peak(int fp64, int iters, double* tflops);
+
 /* Tuning knobs and diagnostics of the implementation (the paper has no
  * counterpart; they never change results beyond rounding).  Keys:
  *   "ax_variant", "ax_variant_pcg"  launch variant (0..3) of the bulk-copy

@@ -87,6 +87,7 @@ def _load():
                                  ctypes.POINTER(sem_info)]),
         "sem_set_option": (i, [h, ctypes.c_char_p, ctypes.c_int64]),
         "sem_glsc3_noalloc": (i, [vp, vp, vp, ctypes.c_int64, vp, vp]),
+        "sem_fma_peak": (i, [i, i, ctypes.POINTER(d)]),
         "sem_batch_setup": (i, [ctypes.POINTER(sem_mesh), ctypes.POINTER(i), i, vp,
                                 ctypes.POINTER(h)]),
         "sem_batch_problem": (i, [h, i, ctypes.POINTER(h)]),
@@ -121,7 +122,7 @@ EXPORTED = ("sem_setup", "sem_destroy", "sem_last_error", "sem_get_sizes", "sem_
             "sem_batch_setup", "sem_batch_problem", "sem_batch_pcg_solve", "sem_batch_get_option",
             "sem_batch_destroy", "sem_rhs_fourier", "sem_x0_create", "sem_x0_param_count",
             "sem_x0_params", "sem_x0_features", "sem_x0_gradients", "sem_x0_add_pair",
-            "sem_x0_train", "sem_x0_predict", "sem_x0_destroy", "sem_mg_apply")
+            "sem_x0_train", "sem_x0_predict", "sem_x0_destroy", "sem_mg_apply", "sem_fma_peak")
 
 
 class SemError(RuntimeError):
@@ -221,6 +222,13 @@ def sem_glsc3_noalloc(a, b, c, n, result, stream=None):
     """Allocation-free sum_i a_i c_i b_i into the device double `result`."""
     return _check(_lib.sem_glsc3_noalloc(_ptr(a), _ptr(b), _ptr(c), int(n), _ptr(result), stream),
                   "sem_glsc3_noalloc")
+
+
+def sem_fma_peak(fp64: bool, iters: int) -> float:
+    """Measured FMA throughput of the CUDA cores in TFLOP/s (FP64 or FP32)."""
+    out = ctypes.c_double()
+    _check(_lib.sem_fma_peak(1 if fp64 else 0, int(iters), ctypes.byref(out)), "sem_fma_peak")
+    return out.value
 
 
 def sem_batch_setup(meshes, Ns, stream=None):

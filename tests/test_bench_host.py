@@ -53,3 +53,16 @@ def test_fp64_peak_derivation(monkeypatch, tmp_path):
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"sm_max_mhz": 1980.0}')
     assert bench.fp64_peak(152)[0] == pytest.approx(152 * 4 * 1980e6 / 1e12)
     assert os.path.exists(tmp_path / "MEASURED_PEAKS.json")
+
+
+def test_cpu_oracle_legs_small():
+    """The host-core legs of the benchmark on a tiny case: config 1's full
+    oracle solve converges to 1e-10, and the one-core and all-core operator
+    rates are positive with the core count stated."""
+    out = bench.cpu_legs(orders=(3,), k=2, reps=1)
+    c1 = out["config1_fp64_pcg_to_1e-10"]
+    assert c1["relres"] <= 1e-10 and 0 < c1["iterations"] < 500
+    (leg,) = out["config3_ax"]
+    assert leg["N"] == 3 and leg["local_dofs_per_process"] == 8 * 64
+    assert leg["gdofs_1core"] > 0 and leg["gdofs_all_cores"] > 0
+    assert leg["cores"] == out["cores_available"] >= 1
