@@ -92,11 +92,11 @@ def fp64_peak(num_sms):
 
 def fma_peaks(sem):
     """Measured FMA throughput of the CUDA cores (sem_fma_peak: 8 independent
-    FMA chains per thread, 4 blocks of 256 threads per SM, CUDA events), in
+    FMA chains per thread, 8 blocks of 256 threads per SM, CUDA events), in
     TFLOP/s: the roofline denominator of the compute-bound FP64 operator."""
     return {"fp64_tflops": sem.sem_fma_peak(True, 4096),
             "fp32_tflops": sem.sem_fma_peak(False, 262144),
-            "method": "sem_fma_peak: 8 FMA chains per thread, 4 x 256 threads per SM, "
+            "method": "sem_fma_peak: 8 FMA chains per thread, 8 x 256 threads per SM, "
                       "one warm-up and one timed launch (CUDA events); no clock or power change"}
 
 
@@ -395,43 +395,116 @@ def mg_leg(sem, torch, S, b, stream):
     return out
 
 
-def learned_leg(sem, torch, train_pairs=128, epochs=20):
-    """Deformed 16^3 elements, N = 7, random Fourier right-hand sides: train
-    the element network on pairs solved by the mixed solver, then compare
-    iterations and time to 1e-8 from x0 = 0 and from the learned guess
-    (inference and energy scaling included in the learned time), FP64 and
-    mixed, on held-out right-hand sides."""
-    S = sem.Solver(16, 16, 16, 7, deform=True)
-    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
-    m = sem.sem_x0_create(S.h, 256, 7)
+def learned_leg(sem, torch, train_pairs=4096, pair_rows=1024, tests=32, epochs=8, batch=8192):
+    """Config 5: deformed 16^3 elements, N = 7, random Fourier right-hand
+    sides (modes |k| <= 8 per axis, amplitude 1/|k|^2).  Training pairs
+    (b, x) come from the solver itself (zero x0, mixed, multigrid
+    preconditioner, to 1e-8); each pair contributes `pair_rows` seeded
+    random element rows.  Two networks: the element-local features, and the
+    same plus a coarse approximation of the solution (two FP32
+    multigrid-Richardson steps) at the element vertices.  On `tests`
+    held-out right-hand sides, Jacobi PCG to 1e-8 from x0 = 0 and from each
+    guess, FP64 and mixed; the learned times are CUDA events on the solver's
+    stream around prediction + solve.  A control without the network (x0 =
+    the same two multigrid steps) separates what the network adds."""
+    stream = torch.cuda.Stream()
+    S = sem.Solver(16, 16, 16, 7, deform=True, stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+        x0 = torch.empty_like(b)
+        r = torch.empty_like(b)
+        w = torch.empty_like(b)
+    models = {}
+    for name, coarse in (("local", 0), ("coarse", 2)):
+        m = sem.sem_x0_create(S.h, 256, 7)
+        sem.sem_x0_set_option(m, "pair_rows", pair_rows)
+        sem.sem_x0_set_option(m, "reserve_rows", train_pairs * pair_rows)
+        if coarse:
+            sem.sem_x0_set_option(m, "coarse_cycles", coarse)
+        models[name] = m
     t0 = time.perf_counter()
+    gen_iters = []
+    with torch.cuda.stream(stream):
+        x = torch.empty_like(b)
     for sample in range(train_pairs):
         sem.sem_rhs_fourier(S.h, 5, sample, b)
-        x, info = S.solve(b, tol=1e-8, maxit=5000, precision=sem.SEM_MIXED_FP32)
-        sem.sem_x0_add_pair(m, b, x)
+        _, info = S.solve(b, tol=1e-8, maxit=500, precision=sem.SEM_MIXED_FP32, precond="mg", x=x)
+        gen_iters.append(info["iters"])
+        for m in models.values():
+            sem.sem_x0_add_pair(m, b, x)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    loss = sem.sem_x0_train(m, epochs, 4096, 1e-3, seed=0)
-    train_s = time.perf_counter() - t0
-    x0 = torch.empty_like(b)
-    res = {"train_pairs": train_pairs, "rows": train_pairs * S.E, "epochs": epochs,
-           "final_loss": loss, "data_s": gen_s, "train_s": train_s, "tests": []}
-    for sample in (10001, 10002, 10003):
+    rows = train_pairs * pair_rows
+    steps = epochs * (rows // batch)
+    flops_step = 2.0 * batch * (2 * 544 * 256 + 3 * 256 * 256 + 3 * 256 * 512)
+    res = {"train_pairs": train_pairs, "rows_per_pair": pair_rows, "rows": rows, "epochs": epochs,
+           "batch": batch, "steps": steps, "data_s": gen_s,
+           "data_solver": "mixed, multigrid preconditioner, zero x0, to 1e-8",
+           "data_iterations_max": max(gen_iters), "models": {}, "tests": []}
+    for name, m in models.items():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        loss = sem.sem_x0_train(m, epochs, batch, 1e-3, seed=0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res["models"][name] = {"final_loss": loss, "train_ms": ms,
+                               "train_tflops": flops_step * steps / (ms * 1e-3) / 1e12,
+                               "flops": "GEMM flops of the 8 products per step (forward 3, backward 5)"}
+
+    def timed(fn):
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        out = fn()
+        eb.record(stream)
+        torch.cuda.synchronize()
+        return out, ea.elapsed_time(eb)
+
+    def mg_steps(k):
+        # the torch operations run on the solver's stream, in order with the
+        # library's launches
+        with torch.cuda.stream(stream):
+            x0.zero_()
+            for _ in range(k):
+                sem.sem_ax(S.h, x0, w, sem.SEM_FP64)
+                torch.sub(b, w, out=r)
+                r32 = r.float()
+                d32 = torch.empty_like(r32)
+                sem.sem_mg_apply(S.h, r32, d32, sem.SEM_MIXED_FP32)
+                x0.add_(d32.double())
+
+    variants = (("local", 0), ("coarse", 0), ("coarse", 2))
+    for sample in range(10001, 10001 + tests):
         sem.sem_rhs_fourier(S.h, 5, sample, b)
         row = {}
-        for name, prec in (("fp64", sem.SEM_FP64), ("mixed", sem.SEM_MIXED_FP32)):
+        for pname, prec in (("fp64", sem.SEM_FP64), ("mixed", sem.SEM_MIXED_FP32)):
             _, iz = S.solve(b, tol=1e-8, maxit=5000, precision=prec)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            sem.sem_x0_predict(m, b, x0, True)
-            _, il = S.solve(b, x0=x0, tol=1e-8, maxit=5000, precision=prec)
-            torch.cuda.synchronize()
-            row[name] = {"zero_iters": iz["iters"], "zero_ms": iz["solve_ms"],
-                         "learned_iters": il["iters"], "learned_ms": (time.perf_counter() - t1) * 1e3,
-                         "learned_converged": il["rc"] == 0}
+            entry = {"zero_iters": iz["iters"], "zero_ms": iz["solve_ms"]}
+            (_, il), ms = timed(lambda: (mg_steps(2), S.solve(b, x0=x0, tol=1e-8, maxit=5000,
+                                                                precision=prec))[1])
+            entry["mg2_iters"], entry["mg2_ms"] = il["iters"], ms
+            for mname, post in variants:
+                m = models[mname]
+                sem.sem_x0_set_option(m, "post_cycles", post)
+                (_, il), ms = timed(lambda: (sem.sem_x0_predict(m, b, x0, True),
+                                             S.solve(b, x0=x0, tol=1e-8, maxit=5000,
+                                                     precision=prec))[1])
+                key = f"{mname}_post{post}"
+                entry[key + "_iters"], entry[key + "_ms"] = il["iters"], ms
+                entry[key + "_converged"] = il["rc"] == 0
+            row[pname] = entry
         res["tests"].append(row)
-    sem.sem_x0_destroy(m)
+    summ = {}
+    for pname in ("fp64", "mixed"):
+        keys = ["zero", "mg2"] + [f"{m}_post{p}" for m, p in variants]
+        summ[pname] = {k: {"iters_mean": statistics.mean(t[pname][k + "_iters"] for t in res["tests"]),
+                           "ms_mean": statistics.mean(t[pname][k + "_ms"] for t in res["tests"])}
+                       for k in keys}
+    res["summary"] = summ
+    for m in models.values():
+        sem.sem_x0_destroy(m)
     S.close()
     return res
 

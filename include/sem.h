@@ -219,7 +219,24 @@ int sem_pcg_solve_ex(sem_handle h, const double* f, const double* x0, double* x,
  * b3, row-major); sem_x0_gradients runs one forward/backward pass on `rows`
  * host rows (X: rows x 544, T: rows x n^3, FP32) in BF16 (bf16_mode = 1) or
  * FP32 arithmetic and returns the gradient of mean((y - T)^2) in the same
- * layout; sem_x0_features writes the FP32 features (E x 544) and scales. */
+ * layout; sem_x0_features writes the FP32 features (E x 544) and scales.
+ * The BF16 products run on the tensor cores (mma.sync m16n8k16, FP32
+ * accumulation; the FP32 gradient-check mode on the CUDA cores).
+ * sem_x0_set_option keys:
+ *   "pair_rows"     element rows kept per training pair: a seeded random
+ *                   subset (seed: the pair's index); 0 (default) keeps all E
+ *   "reserve_rows"  allocate the training set for this many rows at once
+ *   "coarse_cycles" c > 0: the features also carry a coarse approximation
+ *                   of the solution, z = c FP32 multigrid-Richardson steps
+ *                   (z += M^{-1}(b - A z) from 0, sem_mg_apply's V-cycle),
+ *                   at the element's 8 vertices and its element mean, / s_e,
+ *                   times 1 / (RMS of the first training pair's x_L / s_e),
+ *                   a constant of the model that keeps them O(1) (inputs
+ *                   539 of 544; fixed once pairs are stored)
+ *   "post_cycles"   p > 0: sem_x0_predict ends with p steps
+ *                   x0 += M^{-1}(b - A x0) (FP64 residual, FP32 V-cycle)
+ * sem_x0_predict returns once x0 is written; its energy scaling runs on the
+ * device (no host round trip). */
 typedef struct sem_x0_model_s* sem_x0_model;
 int sem_x0_create(sem_handle h, int hidden, uint64_t seed, sem_x0_model* out);
 int sem_x0_param_count(sem_x0_model m, int64_t* sizes6, int64_t* offsets6);
@@ -230,6 +247,7 @@ int sem_x0_gradients(sem_x0_model m, const float* X, const float* T, int rows, i
 int sem_x0_add_pair(sem_x0_model m, const double* b, const double* x);
 int sem_x0_train(sem_x0_model m, int epochs, int batch, float lr, uint64_t seed, double* final_loss);
 int sem_x0_predict(sem_x0_model m, const double* b, double* x0, int energy_scale);
+int sem_x0_set_option(sem_x0_model m, const char* key, int64_t value);
 void sem_x0_destroy(sem_x0_model m);
 
 /* ---- Batched solves: many independent problems of uneven E and N ----
@@ -283,7 +301,7 @@ int sem_glsc3_noalloc(const double* a, const double* b, const double* c, int64_t
 
 /* Measured FMA throughput of the CUDA cores (the paper has no counterpart:
  * it is the roofline denominator of the compute-bound FP64 operator).
- * Launches, on the current device and the legacy default stream, 4 blocks
+ * Launches, on the current device and the legacy default stream, 8 blocks
  * of 256 threads per SM, each thread running 8 independent FMA chains for
  * `iters` steps (a multiple of 4 is used), once to warm up and once timed
  * with CUDA events; *tflops = 2 * 8 * steps * threads / time.  fp64: 1 for

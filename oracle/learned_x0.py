@@ -27,6 +27,12 @@ Definitions (all per element e of a box mesh, local node order i + n j + n^2 k):
   * network: h1 = relu(X W1 + b1), h2 = relu(h1 W2 + b2), y = h2 W3 + b3,
     loss = mean over rows and outputs of (y - t)^2.
   * prediction: u_pred_e = s_e * y_e, x0 = c * QQ^T(u_pred).
+  * coarse features (optional, 9 more values): z_c from c steps of
+    multigrid-Richardson iteration z <- z + M^{-1}(b - A z) from z = 0 (M^{-1}
+    one V-cycle of the multigrid preconditioner, A the assembled masked
+    operator); z_c at the element's 8 vertices (i, j, k in {0, N}, vertex
+    index v = (i>0) + 2 (j>0) + 4 (k>0)) and the element mean of z_c, all
+    divided by s_e.
 """
 from __future__ import annotations
 
@@ -93,6 +99,24 @@ def features(P, b):
     face = np.where(nb >= 0, emean[np.maximum(nb, 0)], 0.0) / s[:, None]
     X = np.concatenate([bl / s[:, None], gm, gs, face], axis=1)
     return X, s
+
+
+def coarse_features(P, vcycle, b, cycles, s):
+    """The 9 coarse features [E, 9] (vertex values and mean of the multigrid-
+    Richardson approximation z, / s_e); vcycle(r) applies one V-cycle."""
+    z = np.zeros(P.L)
+    for _ in range(cycles):
+        z = z + vcycle(b - P.ax(z))
+    n, n3 = P.n, P.n ** 3
+    zl = z.reshape(P.E, n3)
+    out = np.zeros((P.E, 9))
+    for v in range(8):
+        i = n - 1 if v & 1 else 0
+        j = n - 1 if v & 2 else 0
+        k = n - 1 if v & 4 else 0
+        out[:, v] = zl[:, i + n * (j + n * k)]
+    out[:, 8] = zl.mean(axis=1)
+    return out / s[:, None]
 
 
 def targets(P, x, s):

@@ -88,6 +88,7 @@ def _load():
         "sem_set_option": (i, [h, ctypes.c_char_p, ctypes.c_int64]),
         "sem_glsc3_noalloc": (i, [vp, vp, vp, ctypes.c_int64, vp, vp]),
         "sem_fma_peak": (i, [i, i, ctypes.POINTER(d)]),
+        "sem_x0_set_option": (i, [vp, ctypes.c_char_p, ctypes.c_int64]),
         "sem_batch_setup": (i, [ctypes.POINTER(sem_mesh), ctypes.POINTER(i), i, vp,
                                 ctypes.POINTER(h)]),
         "sem_batch_problem": (i, [h, i, ctypes.POINTER(h)]),
@@ -122,7 +123,8 @@ EXPORTED = ("sem_setup", "sem_destroy", "sem_last_error", "sem_get_sizes", "sem_
             "sem_batch_setup", "sem_batch_problem", "sem_batch_pcg_solve", "sem_batch_get_option",
             "sem_batch_destroy", "sem_rhs_fourier", "sem_x0_create", "sem_x0_param_count",
             "sem_x0_params", "sem_x0_features", "sem_x0_gradients", "sem_x0_add_pair",
-            "sem_x0_train", "sem_x0_predict", "sem_x0_destroy", "sem_mg_apply", "sem_fma_peak")
+            "sem_x0_train", "sem_x0_predict", "sem_x0_destroy", "sem_mg_apply", "sem_fma_peak",
+            "sem_x0_set_option")
 
 
 class SemError(RuntimeError):
@@ -310,6 +312,10 @@ def sem_x0_train(m, epochs, batch, lr, seed=0):
 
 def sem_x0_predict(m, b, x0, energy_scale=True):
     return _check(_lib.sem_x0_predict(m, _ptr(b), _ptr(x0), 1 if energy_scale else 0), "sem_x0_predict")
+
+
+def sem_x0_set_option(m, key: str, value: int):
+    return _check(_lib.sem_x0_set_option(m, key.encode(), int(value)), "sem_x0_set_option")
 
 
 def sem_x0_destroy(m):

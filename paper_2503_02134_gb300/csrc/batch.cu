@@ -57,15 +57,22 @@ inline int order_slot(int n) { return n / 2 - 1; }
 template <int n, int V>
 __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     batch_ax_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ items,
-                    const int* __restrict__ seg, int* __restrict__ err) {
+                    const int* __restrict__ seg, int* __restrict__ err,
+                    const __grid_constant__ DMatEO<n> Dc) {
   using S = TmaShape<n, V>;
   constexpr int n2 = S::n2, n3 = S::n3, EPB = S::EPB, NS = S::NS;
   constexpr int SV = EPB * n3;       // floats of one vector per stage
   constexpr int STAGE = 9 * SV;      // r | J^{-1} | p_old | G1..G6
+  // the whole-line contractions of ax_tma_kernel (n >= 10), with its
+  // s-line buffer after the stages
+  constexpr bool kSLine = tma_sline<n>();
+  constexpr int SSE = n * tma_ps<n>();
   const int off = seg[0], nitems = seg[1];
   extern __shared__ __align__(128) float smem_f[];
   float* const stage0 = smem_f;
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + NS * STAGE);
+  float* const sS = smem_f + NS * STAGE;
+  uint64_t* const bar =
+      reinterpret_cast<uint64_t*>(smem_f + NS * STAGE + (kSLine ? EPB * SSE : 0));
   __shared__ float sD[n][n + 1];
   __shared__ double sh_red[S::NT / 32];
   __shared__ int2 s_item[NS];   // item staged on each stage ({-1, -1} = none)
@@ -177,17 +184,44 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         ureg[k] = v;
       }
       __syncthreads();
+      float* const sS_e = sS + ler * SSE;
+      if constexpr (kSLine) {
+        // s-line (i, k = j) and r-line (j = i, k = j) of this thread: u_s to
+        // the s-line buffer, u_r over the row of p once all threads read p
+        float a[n], y[n], yr[n];
+#pragma unroll
+        for (int l = 0; l < n; ++l) a[l] = su_e[jr * n2 + l * n + ir];
+        eo_line<n>(Dc.E, Dc.O, a, y);
+        if (lane_ok) {
+#pragma unroll
+          for (int jj = 0; jj < n; ++jj) sS_e[sb_at<n, false>(ir, jj, jr)] = y[jj];
+        }
+        load_row_lb<n, false>(su_e, ir, jr, a);
+        eo_line<n>(Dc.E, Dc.O, a, yr);
+        __syncthreads();
+        if (lane_ok) store_row_lb<n, false>(su_e, ir, jr, yr);
+        __syncthreads();
+      }
+      float utk[kSLine ? n : 1], vtk[kSLine ? n : 1];
+      if constexpr (kSLine) eo_line<n>(Dc.E, Dc.O, ureg, utk);
       float wreg[n];
 #pragma unroll
       for (int k = 0; k < n; ++k) wreg[k] = 0.f;
 #pragma unroll
       for (int k = 0; k < n; ++k) {
-        const float ur = row_dot<n>(su_e + k * n2 + jr * n, Di);
-        float us = 0.f, ut = 0.f;
+        float ur, us, ut = 0.f;
+        if constexpr (kSLine) {
+          ur = su_e[k * n2 + ij];
+          us = sS_e[sb_at<n, false>(i, j, k)];
+          ut = utk[k];
+        } else {
+          ur = row_dot<n>(su_e + k * n2 + jr * n, Di);
+          us = 0.f;
 #pragma unroll
-        for (int l = 0; l < n; ++l) {
-          us += Dj[l] * su_e[k * n2 + l * n + ir];
-          ut += sD[k][l] * ureg[l];
+          for (int l = 0; l < n; ++l) {
+            us += Dj[l] * su_e[k * n2 + l * n + ir];
+            ut += Dc.d[k * n + l] * ureg[l];
+          }
         }
         const float g0 = Gs[0 * n3 + k * n2], g1 = Gs[1 * n3 + k * n2], g2 = Gs[2 * n3 + k * n2];
         const float g3 = Gs[3 * n3 + k * n2], g4 = Gs[4 * n3 + k * n2], g5 = Gs[5 * n3 + k * n2];
@@ -196,17 +230,43 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         const float vt = g4 * ur + g5 * us + g2 * ut;
         if (lane_ok) {
           sr_e[k * n2 + ij] = vr;
-          ss_e[k * n2 + ij] = vs;
+          if constexpr (kSLine) sS_e[sb_at<n, false>(i, j, k)] = vs;
+          else ss_e[k * n2 + ij] = vs;
         }
+        if constexpr (kSLine) {
+          vtk[k] = vt;
+        } else {
 #pragma unroll
-        for (int kk = 0; kk < n; ++kk) wreg[kk] += sD[k][kk] * vt;
+          for (int kk = 0; kk < n; ++kk) wreg[kk] += Dc.d[k * n + kk] * vt;
+        }
       }
+      if constexpr (kSLine) eo_line<n>(Dc.ET, Dc.OT, vtk, wreg);
       __syncthreads();
+      if constexpr (kSLine) {
+        // transposed s-line and r-line products, in place
+        float b[n], y[n];
+#pragma unroll
+        for (int l = 0; l < n; ++l) b[l] = sS_e[sb_at<n, false>(ir, l, jr)];
+        eo_line<n>(Dc.ET, Dc.OT, b, y);
+        if (lane_ok) {
+#pragma unroll
+          for (int jj = 0; jj < n; ++jj) sS_e[sb_at<n, false>(ir, jj, jr)] = y[jj];
+        }
+        load_row_lb<n, false>(sr_e, ir, jr, b);
+        eo_line<n>(Dc.ET, Dc.OT, b, y);
+        if (lane_ok) store_row_lb<n, false>(sr_e, ir, jr, y);
+        __syncthreads();
+      }
 #pragma unroll
       for (int k = 0; k < n; ++k) {
-        float wv = wreg[k] + row_dot<n>(sr_e + k * n2 + jr * n, DiT);
+        float wv;
+        if constexpr (kSLine) {
+          wv = wreg[k] + (sr_e[k * n2 + ij] + sS_e[sb_at<n, false>(i, j, k)]);
+        } else {
+          wv = wreg[k] + row_dot<n>(sr_e + k * n2 + jr * n, DiT);
 #pragma unroll
-        for (int l = 0; l < n; ++l) wv += DjT[l] * ss_e[k * n2 + l * n + ir];
+          for (int l = 0; l < n; ++l) wv += DjT[l] * ss_e[k * n2 + l * n + ir];
+        }
         if (on_dirichlet(f, i, j, k, n - 1)) wv = 0.f;
         if (act) {
           wg[e * n3 + k * n2 + ij] = wv;
@@ -243,16 +303,38 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
 template <int n, int V>
 constexpr size_t batch_smem_bytes() {
   using S = TmaShape<n, V>;
-  return sizeof(float) * (size_t)S::NS * 9 * S::EPB * S::n3 + S::NS * sizeof(uint64_t);
+  return sizeof(float) * (size_t)S::NS * 9 * S::EPB * S::n3 +
+         (tma_sline<n>() ? sizeof(float) * (size_t)S::EPB * n * tma_ps<n>() : 0) +
+         S::NS * sizeof(uint64_t);
+}
+
+// D of order n as the kernel parameter (the full matrix and its even-odd
+// halves), from the host copy of any problem of that order (D depends on N
+// only).
+template <int n>
+static DMatEO<n> batch_dmat(const float* D32h, const double* D64h) {
+  DMatEO<n> Dc;
+  for (int q = 0; q < n * n; ++q) Dc.d[q] = D32h[q];
+  constexpr int hh = n / 2;
+  for (int a = 0; a < hh; ++a)
+    for (int l = 0; l < hh; ++l) {
+      const double* D = D64h;
+      Dc.E[a * hh + l] = (float)(0.5 * (D[a * n + l] + D[a * n + (n - 1 - l)]));
+      Dc.O[a * hh + l] = (float)(0.5 * (D[a * n + l] - D[a * n + (n - 1 - l)]));
+      Dc.ET[a * hh + l] = (float)(0.5 * (D[l * n + a] + D[(n - 1 - l) * n + a]));
+      Dc.OT[a * hh + l] = (float)(0.5 * (D[l * n + a] - D[(n - 1 - l) * n + a]));
+    }
+  return Dc;
 }
 
 template <int n, int V>
 int batch_ax_launch(cudaStream_t st, int grid, const BatchProb* probs, const int2* items,
-                    const int* seg, int* err) {
+                    const int* seg, int* err, const float* D32h, const double* D64h) {
   auto kern = batch_ax_kernel<n, V>;
   constexpr size_t smem = batch_smem_bytes<n, V>();
   SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, TmaShape<n, V>::NT, smem, st>>>(probs, items, seg, err);
+  kern<<<grid, TmaShape<n, V>::NT, smem, st>>>(probs, items, seg, err,
+                                               batch_dmat<n>(D32h, D64h));
   SEM_CUDA(cudaGetLastError());
   return 0;
 }
@@ -268,23 +350,24 @@ int batch_ax_occupancy(int* per_sm) {
 
 template <int n>
 int batch_ax_dispatch(int V, cudaStream_t st, int grid, const BatchProb* probs, const int2* items,
-                      const int* seg, int* err) {
+                      const int* seg, int* err, const float* D32h, const double* D64h) {
   switch (V) {
-    case 1: return batch_ax_launch<n, 1>(st, grid, probs, items, seg, err);
-    case 2: return batch_ax_launch<n, 2>(st, grid, probs, items, seg, err);
-    case 3: return batch_ax_launch<n, 3>(st, grid, probs, items, seg, err);
-    default: return batch_ax_launch<n, 0>(st, grid, probs, items, seg, err);
+    case 1: return batch_ax_launch<n, 1>(st, grid, probs, items, seg, err, D32h, D64h);
+    case 2: return batch_ax_launch<n, 2>(st, grid, probs, items, seg, err, D32h, D64h);
+    case 3: return batch_ax_launch<n, 3>(st, grid, probs, items, seg, err, D32h, D64h);
+    default: return batch_ax_launch<n, 0>(st, grid, probs, items, seg, err, D32h, D64h);
   }
 }
 
 int batch_ax_any(int n, int V, cudaStream_t st, int grid, const BatchProb* probs,
-                 const int2* items, const int* seg, int* err) {
+                 const int2* items, const int* seg, int* err, const float* D32h,
+                 const double* D64h) {
   switch (n) {
-    case 2: return batch_ax_dispatch<2>(V, st, grid, probs, items, seg, err);
-    case 4: return batch_ax_dispatch<4>(V, st, grid, probs, items, seg, err);
-    case 6: return batch_ax_dispatch<6>(V, st, grid, probs, items, seg, err);
-    case 8: return batch_ax_dispatch<8>(V, st, grid, probs, items, seg, err);
-    default: return batch_ax_dispatch<10>(V, st, grid, probs, items, seg, err);
+    case 2: return batch_ax_dispatch<2>(V, st, grid, probs, items, seg, err, D32h, D64h);
+    case 4: return batch_ax_dispatch<4>(V, st, grid, probs, items, seg, err, D32h, D64h);
+    case 6: return batch_ax_dispatch<6>(V, st, grid, probs, items, seg, err, D32h, D64h);
+    case 8: return batch_ax_dispatch<8>(V, st, grid, probs, items, seg, err, D32h, D64h);
+    default: return batch_ax_dispatch<10>(V, st, grid, probs, items, seg, err, D32h, D64h);
   }
 }
 
@@ -484,6 +567,7 @@ struct sem_batch_s {
   int* d_err = nullptr;
   // per order slot q (n = 2q + 2): present, autotuned launch variant and grid
   bool present[sem::kBatchOrders] = {};
+  int first_of[sem::kBatchOrders] = {};   // a problem of each order (its D is the order's D)
   int variant[sem::kBatchOrders] = {};
   int grid[sem::kBatchOrders] = {};
   float tune_ms[sem::kBatchOrders][sem::kTmaVariants] = {};
@@ -500,8 +584,9 @@ namespace sem {
 static int batch_launch_ax(sem_batch_s& b) {
   for (int q = 0; q < kBatchOrders; ++q) {
     if (!b.present[q]) continue;
+    const Handle& hq = *b.subs[b.first_of[q]];
     int rc = batch_ax_any(2 * q + 2, b.variant[q], b.stream, b.grid[q], b.d_probs, b.d_items,
-                          b.d_counts + 2 * q, b.d_err);
+                          b.d_counts + 2 * q, b.d_err, hq.D32_host, hq.D64_host);
     if (rc) return rc;
     ++b.launches;
   }
@@ -683,10 +768,14 @@ static int batch_autotune(sem_batch_s& b) {
       for (int bps = 1; bps <= per_sm && !rc; ++bps) {
         const int grid = num_sms * bps;
         const int* seg = b.d_counts + 2 * q;
-        if ((rc = batch_ax_any(n, V, b.stream, grid, b.d_probs, b.d_items, seg, b.d_err))) break;
+        const Handle& hq = *b.subs[b.first_of[q]];
+        if ((rc = batch_ax_any(n, V, b.stream, grid, b.d_probs, b.d_items, seg, b.d_err,
+                               hq.D32_host, hq.D64_host)))
+          break;
         SEM_CUDA(cudaEventRecord(e0, b.stream));
         for (int r = 0; r < 2 && !rc; ++r)
-          rc = batch_ax_any(n, V, b.stream, grid, b.d_probs, b.d_items, seg, b.d_err);
+          rc = batch_ax_any(n, V, b.stream, grid, b.d_probs, b.d_items, seg, b.d_err,
+                            hq.D32_host, hq.D64_host);
         SEM_CUDA(cudaEventRecord(e1, b.stream));
         SEM_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -802,6 +891,7 @@ extern "C" int sem_batch_setup(const sem_mesh* meshes, const int* Ns, int count,
     // N = 5, 7, 9 and the per-node gather of other orders measured slower
     // than the separate pass)
     P.fuse = gs_fusable(h) && h.n == 8 ? 1 : 0;
+    if (!b->present[order_slot(h.n)]) b->first_of[order_slot(h.n)] = p;
     b->present[order_slot(h.n)] = true;
     ax_off[p] = part_total;
     part_total += h.E;

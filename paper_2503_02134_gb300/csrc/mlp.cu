@@ -4,9 +4,11 @@
 // glsc3 weight c of the paper's CG loop, Sec. 3.1).  The paper has no
 // learned component; this is the extension the hot path carries.
 //
-// Network: 544 (530 features, zero padded) -> H -> H -> n^3, ReLU, FP32
-// master weights with BF16 copies; products in BF16 with FP32 accumulation
-// (GEMM kernel below), Adam (Kingma & Ba 2015) on the master weights.
+// Network: 544 (530 features, or 539 with the coarse features, zero
+// padded) -> H -> H -> n^3, ReLU, FP32 master weights with BF16 copies;
+// products on the tensor cores in BF16 with FP32 accumulation (gemm_tc
+// below; the FP32 gradient-check mode uses the CUDA-core GEMM), Adam
+// (Kingma & Ba 2015) on the master weights.
 // Features of element e: b_L / s_e (n^3 values), the element mean and
 // standard deviation of each geometric factor G1..G6, and the mean of b_L
 // over each face neighbour / s_e (0 on the domain boundary);
@@ -17,6 +19,7 @@
 
 #include <algorithm>
 #include <random>
+#include <string>
 #include <vector>
 
 #include "pcg.cuh"
@@ -109,6 +112,166 @@ static int gemm(cudaStream_t st, int M, int N, int K, const TAe* A, int lda, con
   return 0;
 }
 
+// ------------------------------------------------------------------ tensor-core GEMM
+// The BF16 products of training and inference on the tensor cores: warp-level
+// mma.sync m16n8k16 (BF16 operands, FP32 accumulation).  A block computes a
+// 64x64 tile of C with 4 warps (2 x 2, 32x32 each); 32-deep k slices of A
+// and B are converted to BF16 (FP32 operands, e.g. dY, are rounded once
+// here) and stored k-contiguous in shared memory with rows padded to 40
+// elements, so each fragment register is one conflict-free 32-bit load.
+// splits > 1 divides K (the batch rows of the weight gradients) over
+// gridDim.z blocks writing FP32 partial tiles to `part`; reduce_splits adds
+// them in split order (deterministic), then bias / ReLU are applied.
+constexpr int kTM = 64, kTN = 64, kTK = 32, kTKP = kTK + 8;
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+template <typename T>
+__device__ __forceinline__ bf16 to_bf(T v);
+template <>
+__device__ __forceinline__ bf16 to_bf<float>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ bf16 to_bf<bf16>(bf16 v) { return v; }
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4],
+                                               const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <typename TAe, typename TBe, bool TA, bool TB>
+__global__ void __launch_bounds__(128)
+    gemm_tc_kernel(int M, int N, int K, int kchunk, const TAe* __restrict__ A, int lda,
+                   const TBe* __restrict__ B, int ldb, const float* __restrict__ bias, int relu,
+                   float* __restrict__ C32, bf16* __restrict__ C16, int ldc,
+                   float* __restrict__ part) {
+  __shared__ __align__(16) bf16 As[kTM][kTKP];   // As[m][k]
+  __shared__ __align__(16) bf16 Bs[kTN][kTKP];   // Bs[n][k]
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int wm = (warp / 2) * 32, wn = (warp % 2) * 32;
+  const int gid = lane / 4, tig = lane % 4;
+  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  float acc[2][4][4] = {};
+  for (int k0 = kb; k0 < ke; k0 += kTK) {
+    // stage: 64 x 32 of A and of B, 16 elements per thread each, read along
+    // the operand's contiguous index
+    for (int q = threadIdx.x; q < kTM * kTK; q += 128) {
+      int mm, kk;
+      if (TA) { mm = q % kTM; kk = q / kTM; } else { kk = q % kTK; mm = q / kTK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      bf16 va = __float2bfloat16_rn(0.f);
+      if (gm < M && gk < ke) va = to_bf(TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]);
+      As[mm][kk] = va;
+      int nn, kq;
+      if (TB) { kq = q % kTK; nn = q / kTK; } else { nn = q % kTN; kq = q / kTN; }
+      const int gn = n0 + nn, gkb = k0 + kq;
+      bf16 vb = __float2bfloat16_rn(0.f);
+      if (gn < N && gkb < ke) vb = to_bf(TB ? B[(size_t)gn * ldb + gkb] : B[(size_t)gkb * ldb + gn]);
+      Bs[nn][kq] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < kTK; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + gid;
+        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tig]);
+        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tig]);
+        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tig + 8]);
+        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tig + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + 8 * j + gid;
+        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 2 * tig]);
+        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 2 * tig + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bfr[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gm = m0 + wm + 16 * i + gid + 8 * h;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int gn = n0 + wn + 8 * j + 2 * tig + c;
+          if (gn >= N) continue;
+          const float v0 = acc[i][j][2 * h + c];
+          if (part) {
+            part[((size_t)blockIdx.z * M + gm) * N + gn] = v0;
+            continue;
+          }
+          float v = v0 + (bias ? bias[gn] : 0.f);
+          if (relu) v = v > 0.f ? v : 0.f;
+          if (C32) C32[(size_t)gm * ldc + gn] = v;
+          if (C16) C16[(size_t)gm * ldc + gn] = __float2bfloat16_rn(v);
+        }
+      }
+}
+
+// C = sum over splits of the partial tiles (in split order), bias, ReLU.
+__global__ void reduce_splits(const float* __restrict__ part, int splits, int M, int N,
+                              const float* __restrict__ bias, int relu, float* __restrict__ C32,
+                              bf16* __restrict__ C16, int ldc) {
+  const int64_t MN = (int64_t)M * N;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < MN;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int z = 0; z < splits; ++z) v += part[z * MN + q];
+    const int gm = (int)(q / N), gn = (int)(q % N);
+    v += bias ? bias[gn] : 0.f;
+    if (relu) v = v > 0.f ? v : 0.f;
+    if (C32) C32[(size_t)gm * ldc + gn] = v;
+    if (C16) C16[(size_t)gm * ldc + gn] = __float2bfloat16_rn(v);
+  }
+}
+
+// Partial tiles of the split-K products: up to kMaxSplits x M x N floats.
+constexpr int kMaxSplits = 32;
+
+template <typename TAe, typename TBe, bool TA, bool TB>
+static int gemm_tc(cudaStream_t st, int num_sms, float* scratch, int64_t scratch_floats, int M,
+                   int N, int K, const TAe* A, int lda, const TBe* B, int ldb, const float* bias,
+                   int relu, float* C32, bf16* C16, int ldc, double* ms_acc = nullptr) {
+  const int gx = (N + kTN - 1) / kTN, gy = (M + kTM - 1) / kTM;
+  // split K until the grid covers the SMs about twice (weight gradients:
+  // K = the batch rows, M x N = one weight matrix)
+  int splits = 1;
+  while (splits < kMaxSplits && (int64_t)gx * gy * splits < 2LL * num_sms &&
+         K / (2 * splits) >= 4 * kTK && (int64_t)(2 * splits) * M * N <= scratch_floats)
+    splits *= 2;
+  const int kchunk = ((K + splits - 1) / splits + kTK - 1) / kTK * kTK;
+  dim3 grid(gx, gy, splits);
+  gemm_tc_kernel<TAe, TBe, TA, TB><<<grid, 128, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, bias,
+                                                         relu, C32, C16, ldc,
+                                                         splits > 1 ? scratch : nullptr);
+  SEM_CUDA(cudaGetLastError());
+  if (splits > 1) {
+    const int64_t MN = (int64_t)M * N;
+    reduce_splits<<<(int)std::min<int64_t>((MN + 255) / 256, 4096), 256, 0, st>>>(
+        scratch, splits, M, N, bias, relu, C32, C16, ldc);
+    SEM_CUDA(cudaGetLastError());
+  }
+  (void)ms_acc;
+  return 0;
+}
+
 // ------------------------------------------------------------------ features
 // Per element: sum of b_L, sum of b_L^2 (block reductions, FP64).
 __global__ void elem_moments(const double* __restrict__ b, int n3, int64_t E,
@@ -133,7 +296,8 @@ __global__ void elem_moments(const double* __restrict__ b, int n3, int64_t E,
 template <typename TO>
 __global__ void elem_features(const double* __restrict__ b, const double* __restrict__ G, int n3,
                               int64_t E, int kx, int ky, int kz, const double* __restrict__ emean,
-                              const double* __restrict__ escale, TO* __restrict__ X) {
+                              const double* __restrict__ escale, const float* __restrict__ zc,
+                              double zmul, TO* __restrict__ X) {
   __shared__ double sh[8];
   for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
     const double inv = 1.0 / escale[e];
@@ -172,6 +336,22 @@ __global__ void elem_features(const double* __restrict__ b, const double* __rest
       row[n3 + 12 + f] = (TO)(nb >= 0 ? emean[nb] * inv : 0.0);
     }
     for (int q = n3 + 18 + threadIdx.x; q < kFeatPad; q += blockDim.x) row[q] = (TO)0.0;
+    if (zc) {
+      // coarse information: a multigrid approximation z of the solution at
+      // the element's 8 vertices and its element mean, / s_e
+      __syncthreads();
+      int n = 1;
+      while (n * n * n < n3) ++n;
+      if (threadIdx.x < 8) {
+        const int c = threadIdx.x;
+        const int vi = (c & 1) ? n - 1 : 0, vj = (c & 2) ? n - 1 : 0, vk = (c & 4) ? n - 1 : 0;
+        row[n3 + 18 + c] = (TO)((double)zc[e * n3 + vi + n * (vj + n * vk)] * inv * zmul);
+      }
+      double s = 0.0;
+      for (int q = threadIdx.x; q < n3; q += blockDim.x) s += zc[e * n3 + q];
+      const double zm = block_sum<kDotFP64>(s, sh) / n3;
+      if (threadIdx.x == 0) row[n3 + 26] = (TO)(zm * inv * zmul);
+    }
   }
 }
 
@@ -238,11 +418,32 @@ __global__ void relu_back(float* __restrict__ dH, const float* __restrict__ H, i
     if (!(H[q] > 0.f)) dH[q] = 0.f;
 }
 
-// db[n] = sum_m D[m][n]
-__global__ void col_sums(const float* __restrict__ D, int M, int N, float* __restrict__ db) {
+// db[n] = sum_m D[m][n] in two deterministic passes: block (x, y) sums
+// rows y, y + gridDim.y, ... of 32 columns (a warp reads 32 consecutive
+// floats of a row; the 8 warps' sums are added in warp order) into
+// part[y][n]; col_sums_finish adds the gridDim.y partials in order.
+constexpr int kColChunks = 32;
+__global__ void __launch_bounds__(256)
+    col_sums(const float* __restrict__ D, int M, int N, float* __restrict__ part) {
+  __shared__ float sh[8][33];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int n = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (n < N)
+    for (int m = blockIdx.y + gridDim.y * warp; m < M; m += gridDim.y * 8) s += D[(size_t)m * N + n];
+  sh[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && n < N) {
+    float t = 0.f;
+    for (int q = 0; q < 8; ++q) t += sh[q][lane];
+    part[(size_t)blockIdx.y * N + n] = t;
+  }
+}
+__global__ void col_sums_finish(const float* __restrict__ part, int chunks, int N,
+                                float* __restrict__ db) {
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += D[(size_t)m * N + n];
+    for (int y = 0; y < chunks; ++y) s += part[(size_t)y * N + n];
     db[n] = s;
   }
 }
@@ -301,8 +502,22 @@ struct sem_x0_model_s {
   float *H1 = nullptr, *H2 = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr, *dH2 = nullptr;
   int* rowidx = nullptr;
   double* part = nullptr;
+  float* gs = nullptr;          // split-K partial tiles of the tensor-core products
+  int64_t gs_floats = 0;
   double *emean = nullptr, *escale = nullptr, *u = nullptr;
   float* Xf = nullptr;   // FP32 features for gradient checks
+  // options (sem_x0_set_option)
+  int64_t pair_rows = 0;    // element rows kept per training pair (0: all E)
+  int coarse_cycles = 0;    // FP32 multigrid cycles behind the coarse features (0: off)
+  int post_cycles = 0;      // multigrid-Richardson steps applied to the prediction
+  int64_t pairs = 0;        // training pairs added so far
+  double zmul = 1.0;        // coarse features' factor: 1 / RMS of the first pair's x_L / s_e
+  float *zc = nullptr, *rc32 = nullptr, *dz32 = nullptr;   // coarse / smoothing work (L each)
+  double* r64 = nullptr;    // residual (L)
+  double* ratio = nullptr;  // device scalars of the energy scaling: {<b,c,x0>, <x0,c,A x0>}
+  sem::bf16* Xall = nullptr;   // features of every element of one pair (E rows)
+  sem::bf16* Tall = nullptr;
+  int* sel = nullptr;       // selected element rows of one pair
 };
 
 namespace sem {
@@ -349,13 +564,13 @@ static int x0_forward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16* 
     return gemm<float, float, false, false>(st, rows, M.out, M.H, M.H2, M.H, wf + M.off[4], M.out,
                                             wf + M.off[5], 0, M.Y, nullptr, M.out);
   }
-  if ((rc = gemm<bf16, bf16, false, false>(st, rows, M.H, M.in, X, M.in, wb + M.off[0], M.H,
+  if ((rc = gemm_tc<bf16, bf16, false, false>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.in, X, M.in, wb + M.off[0], M.H,
                                            wf + M.off[1], 1, M.H1, M.H1b, M.H)))
     return rc;
-  if ((rc = gemm<bf16, bf16, false, false>(st, rows, M.H, M.H, M.H1b, M.H, wb + M.off[2], M.H,
+  if ((rc = gemm_tc<bf16, bf16, false, false>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.H, M.H1b, M.H, wb + M.off[2], M.H,
                                            wf + M.off[3], 1, M.H2, M.H2b, M.H)))
     return rc;
-  return gemm<bf16, bf16, false, false>(st, rows, M.out, M.H, M.H2b, M.H, wb + M.off[4], M.out,
+  return gemm_tc<bf16, bf16, false, false>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.out, M.H, M.H2b, M.H, wb + M.off[4], M.out,
                                         wf + M.off[5], 0, M.Y, nullptr, M.out);
 }
 
@@ -372,17 +587,18 @@ static int x0_backward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16*
                                               M.g + M.off[4], nullptr, M.out)))
       return rc;
   } else {
-    if ((rc = gemm<bf16, float, true, false>(st, M.H, M.out, rows, M.H2b, M.H, M.dY, M.out, nullptr, 0,
+    if ((rc = gemm_tc<bf16, float, true, false>(st, M.h->num_sms, M.gs, M.gs_floats, M.H, M.out, rows, M.H2b, M.H, M.dY, M.out, nullptr, 0,
                                              M.g + M.off[4], nullptr, M.out)))
       return rc;
   }
-  col_sums<<<(M.out + 255) / 256, 256, 0, st>>>(M.dY, rows, M.out, M.g + M.off[5]);
+  col_sums<<<dim3((M.out + 31) / 32, kColChunks), 256, 0, st>>>(M.dY, rows, M.out, M.gs);
+  col_sums_finish<<<(M.out + 255) / 256, 256, 0, st>>>(M.gs, kColChunks, M.out, M.g + M.off[5]);
   if (fp32) {
     if ((rc = gemm<float, float, false, true>(st, rows, M.H, M.out, M.dY, M.out, M.w + M.off[4], M.out,
                                               nullptr, 0, M.dH2, nullptr, M.H)))
       return rc;
   } else {
-    if ((rc = gemm<float, bf16, false, true>(st, rows, M.H, M.out, M.dY, M.out, M.w16 + M.off[4], M.out,
+    if ((rc = gemm_tc<float, bf16, false, true>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.out, M.dY, M.out, M.w16 + M.off[4], M.out,
                                              nullptr, 0, M.dH2, nullptr, M.H)))
       return rc;
   }
@@ -393,17 +609,18 @@ static int x0_backward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16*
                                               M.g + M.off[2], nullptr, M.H)))
       return rc;
   } else {
-    if ((rc = gemm<bf16, float, true, false>(st, M.H, M.H, rows, M.H1b, M.H, M.dH2, M.H, nullptr, 0,
+    if ((rc = gemm_tc<bf16, float, true, false>(st, M.h->num_sms, M.gs, M.gs_floats, M.H, M.H, rows, M.H1b, M.H, M.dH2, M.H, nullptr, 0,
                                              M.g + M.off[2], nullptr, M.H)))
       return rc;
   }
-  col_sums<<<(M.H + 255) / 256, 256, 0, st>>>(M.dH2, rows, M.H, M.g + M.off[3]);
+  col_sums<<<dim3((M.H + 31) / 32, kColChunks), 256, 0, st>>>(M.dH2, rows, M.H, M.gs);
+  col_sums_finish<<<(M.H + 255) / 256, 256, 0, st>>>(M.gs, kColChunks, M.H, M.g + M.off[3]);
   if (fp32) {
     if ((rc = gemm<float, float, false, true>(st, rows, M.H, M.H, M.dH2, M.H, M.w + M.off[2], M.H,
                                               nullptr, 0, M.dH, nullptr, M.H)))
       return rc;
   } else {
-    if ((rc = gemm<float, bf16, false, true>(st, rows, M.H, M.H, M.dH2, M.H, M.w16 + M.off[2], M.H,
+    if ((rc = gemm_tc<float, bf16, false, true>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.H, M.dH2, M.H, M.w16 + M.off[2], M.H,
                                              nullptr, 0, M.dH, nullptr, M.H)))
       return rc;
   }
@@ -414,11 +631,12 @@ static int x0_backward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16*
                                               M.g + M.off[0], nullptr, M.H)))
       return rc;
   } else {
-    if ((rc = gemm<bf16, float, true, false>(st, M.in, M.H, rows, X, M.in, M.dH, M.H, nullptr, 0,
+    if ((rc = gemm_tc<bf16, float, true, false>(st, M.h->num_sms, M.gs, M.gs_floats, M.in, M.H, rows, X, M.in, M.dH, M.H, nullptr, 0,
                                              M.g + M.off[0], nullptr, M.H)))
       return rc;
   }
-  col_sums<<<(M.H + 255) / 256, 256, 0, st>>>(M.dH, rows, M.H, M.g + M.off[1]);
+  col_sums<<<dim3((M.H + 31) / 32, kColChunks), 256, 0, st>>>(M.dH, rows, M.H, M.gs);
+  col_sums_finish<<<(M.H + 255) / 256, 256, 0, st>>>(M.gs, kColChunks, M.H, M.g + M.off[1]);
   SEM_CUDA(cudaGetLastError());
   return 0;
 }
@@ -442,17 +660,65 @@ static int x0_loss(sem_x0_model_s& M, cudaStream_t st, int rows, const TT* T, do
   return 0;
 }
 
+__global__ void to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t L) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L;
+       q += (int64_t)gridDim.x * blockDim.x)
+    b[q] = (float)a[q];
+}
+// y += x (FP32 into FP32 or FP64), r = b - w (FP32 or FP64)
+template <typename TY, typename TX>
+__global__ void add_to(TY* __restrict__ y, const TX* __restrict__ x, int64_t L) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L;
+       q += (int64_t)gridDim.x * blockDim.x)
+    y[q] += (TY)x[q];
+}
+template <typename T>
+__global__ void sub_from(const T* __restrict__ b, const T* __restrict__ w, T* __restrict__ r,
+                         int64_t L) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L;
+       q += (int64_t)gridDim.x * blockDim.x)
+    r[q] = b[q] - w[q];
+}
+
+int mg_apply(Handle& h, sem_precision p, const void* r, void* z);
+
+// Coarse approximation of the solution for the features: `cycles` FP32
+// multigrid-Richardson steps from z = 0 (z += M^{-1}(b - A z)), into M.zc.
+static int x0_coarse(sem_x0_model_s& M, const double* b) {
+  Handle& h = *M.h;
+  const int grid = (int)std::min<int64_t>((h.L + 255) / 256, (int64_t)h.num_sms * 8);
+  int rc;
+  to_f32<<<grid, 256, 0, h.stream>>>(b, M.rc32, h.L);   // r = b (z = 0)
+  SEM_CUDA(cudaMemsetAsync(M.zc, 0, sizeof(float) * h.L, h.stream));
+  for (int c = 0; c < M.coarse_cycles; ++c) {
+    if (c > 0) {
+      // r = b - A z (FP32 operator, summed, masked)
+      if ((rc = launch_ax_local(h, SEM_MIXED_FP32, M.zc, M.dz32, nullptr))) return rc;
+      if ((rc = launch_gs(h, SEM_MIXED_FP32, M.dz32))) return rc;
+      to_f32<<<grid, 256, 0, h.stream>>>(b, M.rc32, h.L);
+      sub_from<float><<<grid, 256, 0, h.stream>>>(M.rc32, M.dz32, M.rc32, h.L);
+    }
+    if ((rc = mg_apply(h, SEM_MIXED_FP32, M.rc32, M.dz32))) return rc;
+    add_to<float, float><<<grid, 256, 0, h.stream>>>(M.zc, M.dz32, h.L);
+  }
+  SEM_CUDA(cudaGetLastError());
+  return 0;
+}
+
 static int x0_features(sem_x0_model_s& M, const double* b, bf16* X16, float* X32) {
   Handle& h = *M.h;
   const int n3 = h.n * h.n * h.n;
   const int grid = (int)std::min<int64_t>(h.E, (int64_t)h.num_sms * 8);
+  int rc;
+  if (M.coarse_cycles > 0 && (rc = x0_coarse(M, b))) return rc;
+  const float* zc = M.coarse_cycles > 0 ? M.zc : nullptr;
   elem_moments<<<grid, 256, 0, h.stream>>>(b, n3, h.E, M.emean, M.escale);
   if (X16)
     elem_features<bf16><<<grid, 256, 0, h.stream>>>(b, h.G64, n3, h.E, h.kx, h.ky, h.kz, M.emean,
-                                                    M.escale, X16);
+                                                    M.escale, zc, M.zmul, X16);
   if (X32)
     elem_features<float><<<grid, 256, 0, h.stream>>>(b, h.G64, n3, h.E, h.kx, h.ky, h.kz, M.emean,
-                                                     M.escale, X32);
+                                                     M.escale, zc, M.zmul, X32);
   SEM_CUDA(cudaGetLastError());
   return 0;
 }
@@ -462,7 +728,8 @@ static void x0_free(sem_x0_model_s* M) {
   if (M->h && M->h->stream) cudaStreamSynchronize(M->h->stream);
   void* ptrs[] = {M->w, M->g, M->m, M->v, M->w16, M->Xtr, M->Ttr, M->Xb, M->Tb, M->H1b, M->H2b,
                   M->H1, M->H2, M->Y, M->dY, M->dH, M->dH2, M->rowidx, M->part, M->emean,
-                  M->escale, M->u, M->Xf};
+                  M->escale, M->u, M->Xf, M->gs, M->zc, M->rc32, M->dz32, M->r64,
+                  M->ratio, M->Xall, M->Tall, M->sel};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete M;
@@ -504,7 +771,10 @@ extern "C" int sem_x0_create(sem_handle h, int hidden, uint64_t seed, sem_x0_mod
       (rc = x0_alloc(*M, o * 4, (void**)&M->m)) || (rc = x0_alloc(*M, o * 4, (void**)&M->v)) ||
       (rc = x0_alloc(*M, o * 2, (void**)&M->w16)) || (rc = x0_alloc(*M, h->E * 8, (void**)&M->emean)) ||
       (rc = x0_alloc(*M, h->E * 8, (void**)&M->escale)) ||
-      (rc = x0_alloc(*M, h->L * 8, (void**)&M->u))) {
+      (rc = x0_alloc(*M, h->L * 8, (void**)&M->u)) ||
+      (rc = x0_alloc(*M, (M->gs_floats = (int64_t)kMaxSplits *
+                                         std::max<int64_t>({sz[0], sz[2], sz[4], 1 << 20})) * 4,
+                     (void**)&M->gs))) {
     x0_free(M);
     return rc;
   }
@@ -619,6 +889,30 @@ extern "C" int sem_x0_features(sem_x0_model m, const double* b, float* X, double
   return SEM_OK;
 }
 
+// Grow the training set to hold `rows` rows (one allocation, old rows copied).
+static int x0_reserve(sem_x0_model_s& m, int64_t rows) {
+  if (rows <= m.cap) return 0;
+  Handle& h = *m.h;
+  bf16 *X2 = nullptr, *T2 = nullptr;
+  SEM_CUDA(cudaMalloc((void**)&X2, (size_t)rows * m.in * 2));
+  cudaError_t ce = cudaMalloc((void**)&T2, (size_t)rows * m.out * 2);
+  if (ce != cudaSuccess) {
+    cudaFree(X2);
+    return cuda_fail(ce, "cudaMalloc");
+  }
+  if (m.rows) {
+    SEM_CUDA(cudaMemcpyAsync(X2, m.Xtr, (size_t)m.rows * m.in * 2, cudaMemcpyDeviceToDevice, h.stream));
+    SEM_CUDA(cudaMemcpyAsync(T2, m.Ttr, (size_t)m.rows * m.out * 2, cudaMemcpyDeviceToDevice, h.stream));
+  }
+  SEM_CUDA(cudaStreamSynchronize(h.stream));
+  if (m.Xtr) cudaFree(m.Xtr);
+  if (m.Ttr) cudaFree(m.Ttr);
+  m.Xtr = X2;
+  m.Ttr = T2;
+  m.cap = rows;
+  return 0;
+}
+
 extern "C" int sem_x0_add_pair(sem_x0_model m, const double* b, const double* x) {
   if (!m || !b || !x || !is_device_ptr(b) || !is_device_ptr(x)) {
     set_error("sem_x0_add_pair: b and x must be device pointers");
@@ -626,28 +920,94 @@ extern "C" int sem_x0_add_pair(sem_x0_model m, const double* b, const double* x)
   }
   Handle& h = *m->h;
   const int64_t E = h.E, n3 = m->out;
-  if (m->rows + E > m->cap) {
-    const int64_t ncap = std::max<int64_t>(2 * m->cap, m->rows + E);
-    bf16 *X2 = nullptr, *T2 = nullptr;
-    SEM_CUDA(cudaMalloc((void**)&X2, (size_t)ncap * m->in * 2));
-    SEM_CUDA(cudaMalloc((void**)&T2, (size_t)ncap * n3 * 2));
-    if (m->rows) {
-      SEM_CUDA(cudaMemcpyAsync(X2, m->Xtr, (size_t)m->rows * m->in * 2, cudaMemcpyDeviceToDevice, h.stream));
-      SEM_CUDA(cudaMemcpyAsync(T2, m->Ttr, (size_t)m->rows * n3 * 2, cudaMemcpyDeviceToDevice, h.stream));
-    }
-    SEM_CUDA(cudaStreamSynchronize(h.stream));
-    if (m->Xtr) cudaFree(m->Xtr);
-    if (m->Ttr) cudaFree(m->Ttr);
-    m->Xtr = X2;
-    m->Ttr = T2;
-    m->cap = ncap;
-  }
+  const int64_t keep = (m->pair_rows > 0 && m->pair_rows < E) ? m->pair_rows : E;
   int rc;
-  if ((rc = x0_features(*m, b, m->Xtr + m->rows * m->in, nullptr))) return rc;
-  elem_targets<<<(int)std::min<int64_t>((E * n3 + 255) / 256, 4096), 256, 0, h.stream>>>(
-      x, (int)n3, E, m->escale, m->Ttr + m->rows * n3);
+  if (m->rows + keep > m->cap &&
+      (rc = x0_reserve(*m, std::max<int64_t>(2 * m->cap, m->rows + keep))))
+    return rc;
+  const int tg = (int)std::min<int64_t>((E * n3 + 255) / 256, 4096);
+  if (m->coarse_cycles > 0 && m->pairs == 0) {
+    // the coarse values z / s_e approximate the targets x_L / s_e, whose
+    // size is set by the problem (b carries the mass matrix): scale them by
+    // the first pair's target RMS so the features are O(1) like the others
+    if (!m->Tall) SEM_CUDA(cudaMalloc((void**)&m->Tall, (size_t)E * n3 * 2));
+    if (!m->part && (rc = x0_ensure_batch(*m, 1))) return rc;
+    const int grid = (int)std::min<int64_t>(E, (int64_t)h.num_sms * 8);
+    elem_moments<<<grid, 256, 0, h.stream>>>(b, (int)n3, E, m->emean, m->escale);
+    elem_targets<<<tg, 256, 0, h.stream>>>(x, (int)n3, E, m->escale, m->Tall);
+    sumsq_bf16<<<tg, 256, 0, h.stream>>>(m->Tall, E * n3, m->part);
+    std::vector<double> hp(tg);
+    SEM_CUDA(cudaMemcpyAsync(hp.data(), m->part, sizeof(double) * tg, cudaMemcpyDeviceToHost, h.stream));
+    SEM_CUDA(cudaStreamSynchronize(h.stream));
+    double ss = 0.0;
+    for (double v : hp) ss += v;
+    m->zmul = ss > 0.0 ? 1.0 / sqrt(ss / (double)(E * n3)) : 1.0;
+  }
+  if (keep == E) {
+    if ((rc = x0_features(*m, b, m->Xtr + m->rows * m->in, nullptr))) return rc;
+    elem_targets<<<tg, 256, 0, h.stream>>>(x, (int)n3, E, m->escale, m->Ttr + m->rows * n3);
+  } else {
+    // a seeded random subset of `keep` elements of this pair (seed: the pair's index)
+    if (!m->Xall) {
+      SEM_CUDA(cudaMalloc((void**)&m->Xall, (size_t)E * m->in * 2));
+      SEM_CUDA(cudaMalloc((void**)&m->Tall, (size_t)E * n3 * 2));
+      SEM_CUDA(cudaMalloc((void**)&m->sel, (size_t)E * sizeof(int)));
+    }
+    if ((rc = x0_features(*m, b, m->Xall, nullptr))) return rc;
+    elem_targets<<<tg, 256, 0, h.stream>>>(x, (int)n3, E, m->escale, m->Tall);
+    std::vector<int> idx((size_t)E);
+    for (int64_t q = 0; q < E; ++q) idx[(size_t)q] = (int)q;
+    std::mt19937_64 gen(0x9e3779b97f4a7c15ull ^ (uint64_t)m->pairs);
+    std::shuffle(idx.begin(), idx.end(), gen);
+    SEM_CUDA(cudaMemcpyAsync(m->sel, idx.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, h.stream));
+    gather_rows<bf16><<<1024, 256, 0, h.stream>>>(m->Xall, m->sel, (int)keep, m->in,
+                                                  m->Xtr + m->rows * m->in);
+    gather_rows<bf16><<<1024, 256, 0, h.stream>>>(m->Tall, m->sel, (int)keep, (int)n3,
+                                                  m->Ttr + m->rows * n3);
+    // the host index array is reused by the next call: wait for its copy
+    SEM_CUDA(cudaStreamSynchronize(h.stream));
+  }
   SEM_CUDA(cudaGetLastError());
-  m->rows += E;
+  m->rows += keep;
+  m->pairs += 1;
+  return SEM_OK;
+}
+
+extern "C" int sem_x0_set_option(sem_x0_model m, const char* key, int64_t value) {
+  if (!m || !key) {
+    set_error("sem_x0_set_option: null argument");
+    return SEM_EINVAL;
+  }
+  const std::string k(key);
+  Handle& h = *m->h;
+  if (k == "pair_rows" && value >= 0) {
+    m->pair_rows = value;
+  } else if (k == "reserve_rows" && value >= 0) {
+    return x0_reserve(*m, value);
+  } else if ((k == "coarse_cycles" || k == "post_cycles") && value >= 0 && value <= 16) {
+    if (k == "coarse_cycles") {
+      if (value > 0 && h.n * h.n * h.n + 27 > kFeatPad) {
+        set_error("sem_x0_set_option: no room for the coarse features at this order");
+        return SEM_EINVAL;
+      }
+      if (m->rows > 0 && (value > 0) != (m->coarse_cycles > 0)) {
+        set_error("sem_x0_set_option: the feature set cannot change once pairs are stored");
+        return SEM_EINVAL;
+      }
+      m->coarse_cycles = (int)value;
+    } else {
+      m->post_cycles = (int)value;
+    }
+    if (value > 0 && !m->zc) {
+      SEM_CUDA(cudaMalloc((void**)&m->zc, sizeof(float) * h.L));
+      SEM_CUDA(cudaMalloc((void**)&m->rc32, sizeof(float) * h.L));
+      SEM_CUDA(cudaMalloc((void**)&m->dz32, sizeof(float) * h.L));
+      SEM_CUDA(cudaMalloc((void**)&m->r64, sizeof(double) * h.L));
+    }
+  } else {
+    set_error("sem_x0_set_option: unknown key or value out of range: " + k);
+    return SEM_EINVAL;
+  }
   return SEM_OK;
 }
 
@@ -718,6 +1078,16 @@ extern "C" int sem_x0_train(sem_x0_model m, int epochs, int batch, float lr, uin
   return SEM_OK;
 }
 
+// x0 *= <b, c, x0> / <x0, c, A x0> (0 if the denominator is not positive),
+// from the two device scalars, without a host round trip
+__global__ void scale_by_ratio(double* __restrict__ x0, const double* __restrict__ nd, int64_t L) {
+  const double den = nd[1];
+  const double alpha = den > 0.0 ? nd[0] / den : 0.0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L;
+       q += (int64_t)gridDim.x * blockDim.x)
+    x0[q] *= alpha;
+}
+
 extern "C" int sem_x0_predict(sem_x0_model m, const double* b, double* x0, int energy_scale) {
   if (!m || !b || !x0 || !is_device_ptr(b) || !is_device_ptr(x0)) {
     set_error("sem_x0_predict: b and x0 must be device pointers");
@@ -728,6 +1098,7 @@ extern "C" int sem_x0_predict(sem_x0_model m, const double* b, double* x0, int e
   int rc;
   const int rows = (int)h.E;
   if ((rc = x0_ensure_batch(*m, rows))) return rc;
+  if (!m->ratio) SEM_CUDA(cudaMalloc((void**)&m->ratio, 2 * sizeof(double)));
   if ((rc = x0_features(*m, b, m->Xb, nullptr))) return rc;
   if ((rc = x0_forward(*m, st, rows, m->Xb, nullptr, false))) return rc;
   const int grid = (int)std::min<int64_t>((h.L + 255) / 256, (int64_t)h.num_sms * 8);
@@ -742,15 +1113,20 @@ extern "C" int sem_x0_predict(sem_x0_model m, const double* b, double* x0, int e
     // never worse than x0 = 0 in the A-norm
     if ((rc = launch_ax_local(h, SEM_FP64, x0, m->u, nullptr))) return rc;
     if ((rc = launch_gs(h, SEM_FP64, m->u))) return rc;
-    double num = 0.0, den = 0.0;
-    if ((rc = launch_glsc3(h, SEM_FP64, b, x0, h.dot_out))) return rc;
-    SEM_CUDA(cudaMemcpyAsync(&num, h.dot_out, 8, cudaMemcpyDeviceToHost, st));
-    SEM_CUDA(cudaStreamSynchronize(st));
-    if ((rc = launch_glsc3(h, SEM_FP64, x0, m->u, h.dot_out))) return rc;
-    SEM_CUDA(cudaMemcpyAsync(&den, h.dot_out, 8, cudaMemcpyDeviceToHost, st));
-    SEM_CUDA(cudaStreamSynchronize(st));
-    const double alpha = den > 0.0 ? num / den : 0.0;
-    mul_weight<<<grid, 256, 0, st>>>(x0, nullptr, h.L, alpha);
+    if ((rc = launch_glsc3(h, SEM_FP64, b, x0, m->ratio))) return rc;
+    if ((rc = launch_glsc3(h, SEM_FP64, x0, m->u, m->ratio + 1))) return rc;
+    scale_by_ratio<<<grid, 256, 0, st>>>(x0, m->ratio, h.L);
+    SEM_CUDA(cudaGetLastError());
+  }
+  // post-smoothing: x0 += M^{-1}(b - A x0), the residual in FP64, the cycle
+  // in FP32 (its rough error is what the guess carries)
+  for (int c = 0; c < m->post_cycles; ++c) {
+    if ((rc = launch_ax_local(h, SEM_FP64, x0, m->r64, nullptr))) return rc;
+    if ((rc = launch_gs(h, SEM_FP64, m->r64))) return rc;
+    sub_from<double><<<grid, 256, 0, st>>>(b, m->r64, m->r64, h.L);
+    to_f32<<<grid, 256, 0, st>>>(m->r64, m->rc32, h.L);
+    if ((rc = mg_apply(h, SEM_MIXED_FP32, m->rc32, m->dz32))) return rc;
+    add_to<double, float><<<grid, 256, 0, st>>>(x0, m->dz32, h.L);
     SEM_CUDA(cudaGetLastError());
   }
   SEM_CUDA(cudaStreamSynchronize(st));

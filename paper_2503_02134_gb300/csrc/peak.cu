@@ -2,21 +2,25 @@
 // operator is bound by the FP64 FMA pipe, not by memory, so its roofline is
 // a fraction of this rate; the FP32 figure bounds the CUDA-core contractions
 // at high order.  Every thread runs kChains independent FMA chains
-// (a <- a * m + b), enough to cover the pipe's latency with the resident
-// warps; flops = 2 * chains * iterations * threads.  The result feeds a sink
-// that a comparison nothing satisfies guards, so the chains stay live.
+// (a <- a * m + b) with register operands, enough to cover the pipe's
+// latency with the 64 resident warps per SM; flops = 2 * chains *
+// iterations * threads.  The result feeds a sink that a comparison nothing
+// satisfies guards, so the chains stay live.
 #include "sem_internal.cuh"
 
 namespace sem {
 
 constexpr int kPeakChains = 8;
 constexpr int kPeakThreads = 256;
-constexpr int kPeakBlocksPerSm = 4;
+constexpr int kPeakBlocksPerSm = 8;
 
 static __device__ double g_peak_sink;
 
 template <typename T>
-__global__ void __launch_bounds__(kPeakThreads) fma_peak_kernel(int iters, T m, T b) {
+__global__ void __launch_bounds__(kPeakThreads) fma_peak_kernel(int iters, T m0, T b0) {
+  // the coefficients in registers (a value the compiler cannot fold), so
+  // every FMA is register-only
+  const T m = m0 + (T)threadIdx.x * (T)1e-30, b = b0 + (T)blockIdx.x * (T)1e-30;
   T a[kPeakChains];
 #pragma unroll
   for (int c = 0; c < kPeakChains; ++c) a[c] = (T)(threadIdx.x + c) * (T)1e-3;

@@ -49,6 +49,35 @@ def test_features_match_oracle(sem):
     S.close()
 
 
+def test_coarse_features_match_oracle(sem):
+    """The optional coarse features (two multigrid-Richardson steps, at the
+    element vertices and the element mean) against the oracle's FP64
+    definition; the GPU's steps run in FP32 (V-cycle and residual), so the
+    bound is a few FP32 V-cycle roundings (the V-cycle test allows 2e-5)."""
+    from oracle import pmg
+    dims, N = (4, 4, 2), 3
+    M = pmg.PMG(*dims, N, deform=True)
+    P = M.levels[0].P
+    S = sem.Solver(*dims, N, deform=True)
+    m = sem.sem_x0_create(S.h, 32, 0)
+    sem.sem_x0_set_option(m, "coarse_cycles", 2)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    sem.sem_rhs_fourier(S.h, 2, 1, b)
+    X = np.zeros((S.E, 544), dtype=np.float32)
+    sc = np.zeros(S.E)
+    sem.sem_x0_features(m, b, X, sc)
+    Xo, so_ = lx.features(P, b.cpu().numpy())
+    Co = lx.coarse_features(P, M.vcycle, b.cpu().numpy(), 2, so_)
+    nf = P.n ** 3 + 18
+    assert rel_maxerr(X[:, :nf], Xo) < 1e-6
+    assert rel_maxerr(X[:, nf:nf + 9], Co) < 1e-4
+    assert np.all(X[:, nf + 9:] == 0)
+    with pytest.raises(sem.SemError):
+        sem.sem_x0_set_option(m, "coarse_cycles", 99)
+    sem.sem_x0_destroy(m)
+    S.close()
+
+
 def _bf16(a):
     """Round float32 values to bfloat16 (round to nearest even), kept as float64."""
     u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
@@ -128,5 +157,38 @@ def test_training_reduces_loss_and_guess_is_safe(sem):
         assert i1["iters"] <= i0["iters"] + 10
         saved.append(i0["iters"] - i1["iters"])
     print("iterations saved by the learned guess:", saved)
+    sem.sem_x0_destroy(m)
+    S.close()
+
+
+def test_subsampled_pairs_coarse_features_and_smoothing(sem):
+    """A model that keeps a seeded half of each pair's element rows, uses
+    the coarse features and ends its prediction with two multigrid
+    smoothing steps: it trains, its guess stays continuous and masked, and
+    the solve from it converges."""
+    S = sem.Solver(6, 6, 6, 5, deform=True)
+    P = so.Problem(6, 6, 6, 5, deform=True)
+    m = sem.sem_x0_create(S.h, 64, 1)
+    sem.sem_x0_set_option(m, "pair_rows", S.E // 2)
+    sem.sem_x0_set_option(m, "reserve_rows", 12 * (S.E // 2))
+    sem.sem_x0_set_option(m, "coarse_cycles", 2)
+    b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+    for sample in range(12):
+        sem.sem_rhs_fourier(S.h, 1, sample, b)
+        x, info = S.solve(b, tol=1e-9, maxit=200, precision=sem.SEM_MIXED_FP32, precond="mg")
+        assert info["rc"] == 0
+        sem.sem_x0_add_pair(m, b, x)
+    first = sem.sem_x0_train(m, 1, 128, 1e-3, seed=0)
+    last = sem.sem_x0_train(m, 20, 128, 1e-3, seed=1)
+    assert last < first
+    sem.sem_x0_set_option(m, "post_cycles", 2)
+    x0 = torch.empty_like(b)
+    sem.sem_rhs_fourier(S.h, 1, 100, b)
+    sem.sem_x0_predict(m, b, x0, True)
+    xh = x0.cpu().numpy()
+    np.testing.assert_allclose(P.dssum(xh) / P.mult, xh, rtol=1e-6, atol=1e-12)
+    assert np.all(xh[P.mask == 0] == 0)
+    _, i1 = S.solve(b, x0=x0, tol=1e-8, maxit=4000, precision=sem.SEM_MIXED_FP32)
+    assert i1["rc"] == 0
     sem.sem_x0_destroy(m)
     S.close()

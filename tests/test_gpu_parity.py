@@ -114,8 +114,10 @@ def test_ax_fp32(pair, sem):
     w = torch.empty(P.L, dtype=torch.float32, device="cuda")
     sem.sem_ax(S.h, cu(u, torch.float32), w, sem.SEM_MIXED_FP32)
     ref = P.ax(u.astype(np.float64))
-    # FP32 rounding of G, D and the contractions: bounded by ~ 2 n^2 eps32 relative
-    assert rel_maxerr(w.cpu(), ref) < 2.0 * P.n ** 2 * 2.0 ** -24 * 8
+    # FP32 rounding of G, D and the n-term contractions: every case of this
+    # table (N = 1..15, box and deformed) measured at most 0.46 n 2^-24
+    # relative (max norm); the bound 2 n 2^-24 keeps about 4x of headroom
+    assert rel_maxerr(w.cpu(), ref) < 2.0 * P.n * 2.0 ** -24
 
 
 def test_gs(pair, sem):
@@ -358,7 +360,9 @@ def test_fused_gather_scatter_is_bitwise(sem, dims, N):
 
 def test_fused_gather_scatter_large_mesh(sem):
     """Where the fused update runs its own (occupancy-sized) grid, the dot
-    products are summed in another order: the solves agree to rounding."""
+    products are summed in another order: the solves agree to rounding, and
+    the folded mixed solve to 1e-9 is within 1e-7 of the oracle's x solved
+    to 1e-12 (so the two tolerances are not conflated)."""
     P = so.Problem(12, 10, 9, 7, deform=True)
     S = sem.Solver(12, 10, 9, 7, deform=True)
     b = torch.empty(S.L, dtype=torch.float64, device="cuda")
@@ -370,6 +374,8 @@ def test_fused_gather_scatter_large_mesh(sem):
     assert abs(i1["iters"] - i0["iters"]) <= max(3, i0["iters"] // 50)
     assert rel_maxerr(x1.cpu(), x0.cpu()) < 1e-7
     assert P.true_relres(b.cpu().numpy(), x1.cpu().numpy()) <= 1.0000001e-9
+    xo, _, _ = P.pcg(b.cpu().numpy(), tol=1e-12, maxit=5000)
+    assert rel_maxerr(x1.cpu(), xo) < 1e-7
     S.close()
 
 
@@ -553,15 +559,18 @@ def test_reliable_updates_and_restarts_both_converge(sem):
 def test_ax_tensor_cores(sem, kx, ky, kz, N):
     """D-contractions on tensor cores: TF32 products and the three-product
     BF16 split, FP32 accumulation.  Error relative to the FP64 oracle: TF32
-    keeps 10 mantissa bits (unit roundoff 2^-11), the BF16 split ~16."""
+    keeps 10 mantissa bits (unit roundoff 2^-11; measured 0.6-1.65 x 2^-11
+    on these cases), the BF16 split about 16 (measured 0.36-0.8 x 2^-16).
+    Bounds of 3 x those units: a single-product BF16 contraction (unit
+    roundoff 2^-8, errors of several 2^-9) fails the TF32 bound."""
     P = so.Problem(kx, ky, kz, N, deform=True)
     S = sem.Solver(kx, ky, kz, N, deform=True)
     u = sem_inputs.uniform_local(P.L, seed=61, dtype=np.float32)
     ref = P.mask * P.ax_local(u.astype(np.float64))
     w = torch.empty(P.L, dtype=torch.float32, device="cuda")
     errs = {}
-    for name, prec, tol in (("tf32", sem.SEM_MIXED_TF32, 2.0 ** -11 * 8 * P.n),
-                            ("bf16x3", sem.SEM_MIXED_BF16X3, 2.0 ** -16 * 8 * P.n)):
+    for name, prec, tol in (("tf32", sem.SEM_MIXED_TF32, 3.0 * 2.0 ** -11),
+                            ("bf16x3", sem.SEM_MIXED_BF16X3, 3.0 * 2.0 ** -16)):
         sem.sem_ax_local(S.h, cu(u, torch.float32), w, prec)
         errs[name] = rel_maxerr(w.cpu(), ref)
         assert errs[name] < tol, (name, errs[name], tol)
@@ -570,6 +579,6 @@ def test_ax_tensor_cores(sem, kx, ky, kz, N):
     assert errs["bf16x3"] < errs["tf32"]
     # assembled operator through the same path
     sem.sem_ax(S.h, cu(u, torch.float32), w, sem.SEM_MIXED_TF32)
-    assert rel_maxerr(w.cpu(), P.ax(u.astype(np.float64))) < 2.0 ** -11 * 8 * P.n
+    assert rel_maxerr(w.cpu(), P.ax(u.astype(np.float64))) < 3.0 * 2.0 ** -11
     print(N, errs)
     S.close()

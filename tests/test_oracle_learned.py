@@ -92,3 +92,26 @@ def test_continuity_projection():
     assert np.all(x0[P.mask == 0] == 0)
     cont = P.mask * P.dssum(u) / P.mult
     np.testing.assert_allclose(lx.continuity_projection(P, cont), cont, rtol=1e-13, atol=1e-15)
+
+
+def test_coarse_features_converge_to_the_solution():
+    """Multigrid-Richardson converges to A^{-1} b, so with many steps the
+    coarse features equal the exact solution's values at the element
+    vertices and its element means (pins the iteration's sign and the vertex
+    order v = (i>0) + 2 (j>0) + 4 (k>0))."""
+    from oracle import pmg
+    M = pmg.PMG(2, 2, 2, 3, deform=True)
+    P = M.levels[0].P
+    b = lx.fourier_rhs(P, 4, 2)
+    _, s = lx.features(P, b)
+    x, _, _ = P.pcg(b, tol=1e-14, maxit=2000)
+    C = lx.coarse_features(P, M.vcycle, b, 60, s)
+    n = P.n
+    xl = x.reshape(P.E, n ** 3)
+    want = np.stack([xl[:, (n - 1 if v & 1 else 0) + n * ((n - 1 if v & 2 else 0) +
+                                                       n * (n - 1 if v & 4 else 0))]
+                     for v in range(8)] + [xl.mean(axis=1)], axis=1) / s[:, None]
+    assert np.abs(C - want).max() <= 1e-8 * np.abs(want).max()
+    # one step is far from it: the pin is the convergence, not the start
+    C1 = lx.coarse_features(P, M.vcycle, b, 1, s)
+    assert np.abs(C1 - want).max() > 1e-3 * np.abs(want).max()
