@@ -306,6 +306,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   constexpr bool kSplit = n >= 10;
   constexpr bool kSLine = tma_sline<n>();
   constexpr bool kSwz = kGOnly && n == 16;   // swizzled thread-written line buffers
+  // line orders with two or more stages refill a stage's G as soon as the
+  // geometric loop is done with it (measured: faster with two stages,
+  // slower with a single stage, where the block waits for its own copy)
+  constexpr bool kEarly = kSLine && NS >= 2;
   extern __shared__ __align__(128) float smem_f[];
   float* const stage0 = smem_f;
   // kGOnly: u (or p) of the group, then u_r; kSLine: the s-line buffer
@@ -333,36 +337,32 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   const uint64_t pol_first = l2h ? l2_policy_evict_first() : 0ull;
   const uint64_t pol_last = l2h ? l2_policy_evict_last() : 0ull;
 
-  auto issue = [&](int st, int64_t g) {
+  // Copies of group g into stage st.  part 0: everything; part 1 (issued as
+  // soon as the stage's G is no longer read): the transaction count of the
+  // whole stage, G and, in PCG mode, r and J^{-1}; part 2 (once the group
+  // is finished): u, or p_old in PCG mode.  The stage's barrier phase
+  // completes only when the bytes of both parts have landed.
+  auto issue = [&](int st, int64_t g, int part) {
     const int64_t e0 = g * EPB;
     const int64_t cnt = E - e0 < EPB ? E - e0 : EPB;
     const uint32_t vb = (uint32_t)(cnt * n3 * 4);
     float* dst = stage0 + st * STAGE;
-    mbar_arrive_expect_tx(&bar[st], (NV + 6) * vb);
-    if (kGOnly) {
-      if (l2h) bulk_load_hint(dst, G + e0 * 6 * n3, 6 * vb, &bar[st], pol_first);
-      else bulk_load(dst, G + e0 * 6 * n3, 6 * vb, &bar[st]);
-      return;
-    }
-    if (l2h) {
-      if (PCG) {
-        bulk_load_hint(dst, rr + e0 * n3, vb, &bar[st], pol_first);
-        bulk_load_hint(dst + SV, minv + e0 * n3, vb, &bar[st], pol_first);
-        bulk_load_hint(dst + 2 * SV, pp + e0 * n3, vb, &bar[st], pol_first);
-      } else {
-        bulk_load_hint(dst, uin + e0 * n3, vb, &bar[st], pol_first);
+    auto copy = [&](float* d, const float* src, uint32_t bytes) {
+      if (l2h) bulk_load_hint(d, src, bytes, &bar[st], pol_first);
+      else bulk_load(d, src, bytes, &bar[st]);
+    };
+    if (part != 2) {
+      mbar_arrive_expect_tx(&bar[st], (NV + 6) * vb);
+      copy(dst + NV * SV, G + e0 * 6 * n3, 6 * vb);
+      if (PCG && !kGOnly) {
+        copy(dst, rr + e0 * n3, vb);
+        copy(dst + SV, minv + e0 * n3, vb);
       }
-      bulk_load_hint(dst + NV * SV, G + e0 * 6 * n3, 6 * vb, &bar[st], pol_first);
-      return;
     }
-    if (PCG) {
-      bulk_load(dst, rr + e0 * n3, vb, &bar[st]);
-      bulk_load(dst + SV, minv + e0 * n3, vb, &bar[st]);
-      bulk_load(dst + 2 * SV, pp + e0 * n3, vb, &bar[st]);
-    } else {
-      bulk_load(dst, uin + e0 * n3, vb, &bar[st]);
+    if (part != 1 && !kGOnly) {
+      if (PCG) copy(dst + 2 * SV, pp + e0 * n3, vb);
+      else copy(dst, uin + e0 * n3, vb);
     }
-    bulk_load(dst + NV * SV, G + e0 * 6 * n3, 6 * vb, &bar[st]);
   };
 
   if (tid == 0) {
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   if (tid == 0) {
     for (int q = 0; q < NS; ++q) {
       const int64_t g0 = (int64_t)blockIdx.x + (int64_t)q * gridDim.x;
-      if (g0 < ngroups) issue(q, g0);
+      if (g0 < ngroups) issue(q, g0, 0);
     }
   }
   float Di[n], Dj[n], DiT[n], DjT[n];
@@ -516,9 +516,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       const float vs = g3 * ur + g1 * us + g5 * ut;
       const float vt = g4 * ur + g5 * us + g2 * ut;
       if (lane_ok) {
-        // v_r over G1 of the stage, or with the stages holding G only over
-        // this thread's own u_r; v_s over its own u_s
-        if constexpr (kGOnly) su_e[lb_at<n, kSwz>(i, j, k)] = vr;
+        // line orders: v_r over this thread's own u_r and v_s over its own
+        // u_s, so that G is dead after this loop; otherwise v_r, v_s over
+        // G1, G2 of the stage
+        if constexpr (kSLine) su_e[lb_at<n, kSwz>(i, j, k)] = vr;
         else sr_e[k * n2 + ij] = vr;
         if constexpr (kSLine) sS_e[sb_at<n, kSwz>(i, j, k)] = vs;
         else ss_e[k * n2 + ij] = vs;
@@ -532,6 +533,17 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     }
     if constexpr (kSLine) eo_line<n>(Dc.ET, Dc.OT, vtk, wreg);
     __syncthreads();
+    if constexpr (kEarly) {
+      // G (and r, J^{-1}) of this stage are no longer read: start the copies
+      // of the next group that uses this stage now, not after the group
+      if (tid == 0) {
+        const int64_t gn = g + NS * (int64_t)gridDim.x;
+        if (gn < ngroups) {
+          fence_proxy_async_smem();
+          issue(st, gn, 1);
+        }
+      }
+    }
     if constexpr (kSLine) {
       // transposed s-lines: w_s of line (i, k = j) = D^T times the line of
       // v_s, written back over the same line (this thread reads all of it
@@ -546,7 +558,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
 #pragma unroll
         for (int jj = 0; jj < n; ++jj) sS_e[sb_at<n, kSwz>(ir, jj, jr)] = y[jj];
       }
-      float* const vr_e = kGOnly ? su_e : sr_e;
+      float* const vr_e = su_e;
       load_row_lb<n, kSwz>(vr_e, ir, jr, b);
       eo_line<n>(Dc.ET, Dc.OT, b, y);
       if (lane_ok) store_row_lb<n, kSwz>(vr_e, ir, jr, y);
@@ -557,7 +569,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     for (int k = 0; k < n; ++k) {
       float wv;
       if constexpr (kSLine) {
-        const float wr = kGOnly ? su_e[lb_at<n, kSwz>(i, j, k)] : sr_e[k * n2 + ij];
+        const float wr = su_e[lb_at<n, kSwz>(i, j, k)];
         wv = wreg[k] + (wr + sS_e[sb_at<n, kSwz>(i, j, k)]);
       } else if constexpr (kSplit) {
         wv = wreg[k] + (row_dot_2acc<n>(sr_e + k * n2 + jr * n, DiT) +
@@ -583,7 +595,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       const int64_t gn = g + NS * (int64_t)gridDim.x;
       if (gn < ngroups) {
         fence_proxy_async_smem();
-        issue(st, gn);
+        issue(st, gn, kEarly ? 2 : 0);
       }
     }
   }
