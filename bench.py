@@ -278,15 +278,19 @@ def batched_leg(sem, torch):
         seq_ok = seq_ok and rci == 0
     torch.cuda.synchronize()
     seq_s = time.perf_counter() - t0
-    total_L = sum(sem.sem_get_sizes(h).L for h in hs)
+    Ls = [sem.sem_get_sizes(h).L for h in hs]
+    total_L = sum(Ls)
     it = [i["iters"] for i in infos]
+    dof_iters = sum(L_i * it_i for L_i, it_i in zip(Ls, it))
     out = {"problems": len(cases), "local_dofs": total_L, "orders": sorted(set(N for _, N in cases)),
            "k_range": [min(k for k, _ in cases), max(k for k, _ in cases)],
            "batched_ms": batched_s * 1e3, "sequential_ms": seq_s * 1e3,
            "speedup_vs_sequential": seq_s / batched_s, "setup_s": setup_s,
            "iterations_min_max": [min(it), max(it)], "all_converged": rc == 0 and seq_ok,
            "max_relres_true": max(i["relres_true"] for i in infos),
-           "gdofs": total_L * sum(it) / len(it) / batched_s / 1e9,
+           "gdofs": dof_iters / batched_s / 1e9,
+           "gdofs_sequential": dof_iters / seq_s / 1e9,
+           "gdofs_definition": "sum over problems of local DOFs x iterations / time",
            "autotune": {f"n{N + 1}": {"variant": sem.sem_batch_get_option(b, f"variant_n{N + 1}"),
                                       "grid": sem.sem_batch_get_option(b, f"grid_n{N + 1}")}
                         for N in sorted(set(N for _, N in cases))},

@@ -329,13 +329,14 @@ int sem_fma_peak(int fp64, int iters, double* tflops);
  *                 instead of the access-policy window of "l2_persist";
  *                 0 (default) off
  *   "fuse_gs"     1 (default): in FP32 and mixed PCG iterations on a box mesh
- *                 (sem_setup without gid) with n a multiple of 4 the
+ *                 (sem_setup without gid) with an even n the
  *                 direct-stiffness summation is folded into the vector update
  *                 -- each copy of a shared node gathers the others, found from
- *                 its position, in ascending local index with the
+ *                 its position (whole rows of float4, or float2 pairs where n
+ *                 is not a multiple of 4), in ascending local index with the
  *                 accumulation "gs_acc" selects, which gives the separate
- *                 pass's bits; 2: folded for every n (slower than the
- *                 separate pass where n is not a multiple of 4); 0: separate pass
+ *                 pass's bits; 2: folded for odd n as well (node by node,
+ *                 slower than the separate pass); 0: separate pass
  *   "upd_tma"     1: the folded update at N = 7 stages its streams in shared
  *                 memory by bulk copies (two stages, bounded waits) and reads
  *                 only the other copies of shared nodes directly; 0 (default) off

@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
       g.m = __ldg(reinterpret_cast<const float4*>(minv) + q);
       g.c = __ldg(reinterpret_cast<const uchar4*>(cw) + q);
     }
-    g.w = gs_gather_row4<n, ACC>(w, q, faces, kx, kxky);
+    if constexpr (n % 4 == 0) g.w = gs_gather_row4<n, ACC>(w, q, faces, kx, kxky);
+    else g.w = gs_gather_row2x2<n, ACC>(w, q, faces, kx, kxky);
     return g;
   };
   auto finish = [&](int64_t q, Grp g) {
@@ -527,9 +528,10 @@ int launch_cg_update32(Handle& h, int dm, float* x, float* r, const float* p, co
   return update_t<float>(h, dm, x, r, p, w, h.c32, minv, s, hist);
 }
 
-// Fold QQ^T into the update on box meshes; by default only where whole
-// float4 rows can be gathered (n a multiple of 4): the per-node gather of
-// other orders measured slower than the separate pass.
+// Fold QQ^T into the update on box meshes; by default for even n, where
+// whole float4 rows (n a multiple of 4) or float2 pairs (n = 2, 6, 10, 14)
+// can be gathered: the per-node gather of odd orders measured slower than
+// the separate pass.
 // ---------------------------------------------------------------------------
 // Staged folded update (n = 8): the streams x, r, p, J^{-1}, w and the
 // multiplicity code of a group of EPB elements are brought into shared
@@ -687,7 +689,7 @@ static int update_tma_launch(Handle& h, float* x, float* r, const float* p, cons
 
 bool gs_fusable(const Handle& h) {
   if (h.gid_user || h.n < 2 || h.fuse_gs == 0) return false;
-  return h.fuse_gs == 2 || h.n % 4 == 0;
+  return h.fuse_gs == 2 || h.n % 2 == 0;
 }
 
 // Grid of a fused update kernel: the v4 update's grid (one thread per DOF,
@@ -733,9 +735,13 @@ static void update_gs_dispatch(Handle& h, float* x, float* r, const float* p, co
     return;                                                                               \
   }
   switch (h.n) {
+    SEM_UPD_ROW4(2)
     SEM_UPD_ROW4(4)
+    SEM_UPD_ROW4(6)
     SEM_UPD_ROW4(8)
+    SEM_UPD_ROW4(10)
     SEM_UPD_ROW4(12)
+    SEM_UPD_ROW4(14)
     SEM_UPD_ROW4(16)
     default: break;
   }
