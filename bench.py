@@ -351,7 +351,7 @@ def order_sweep_leg(sem, torch, hbm_gbs, fp64_peak_tflops):
                     "fp32_rel_err_vs_fp64": err, "tensor_cores": tc,
                     "fp32_kernel": "bulk-copy staged" if n % 2 == 0 else "register/shared (unstaged)",
                     "fp32_variant": int(sem.sem_get_option(S.h, "ax_variant")),
-                    "fp32_tune_ms": [sem.sem_get_option(S.h, f"ax_tune_ms_plain_{v}") for v in range(4)]})
+                    "fp32_tune_ms": [sem.sem_get_option(S.h, f"ax_tune_ms_plain_{v}") for v in range(5)]})
         S.close()
         del u64, u32, w64, w32
     return out

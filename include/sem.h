@@ -312,9 +312,17 @@ int sem_fma_peak(int fp64, int iters, double* tflops);
 
 /* Tuning knobs and diagnostics of the implementation (the paper has no
  * counterpart; they never change results beyond rounding).  Keys:
- *   "ax_variant", "ax_variant_pcg"  launch variant (0..3) of the bulk-copy
+ *   "ax_variant", "ax_variant_pcg"  launch variant (0..4) of the bulk-copy
  *                                   staged FP32 operator, plain / PCG mode;
  *                                   sem_setup's autotuner picks the fastest
+ *                                   (4: G in one buffer refilled after the
+ *                                   geometric step, u in two; plain mode at
+ *                                   n = 10, 12, 14 only).  A variant whose
+ *                                   stages do not fit runs the unstaged kernel
+ *   "ax_grid_cap" largest grid of the staged FP32 operator (0, the default:
+ *                 resident blocks on every SM); a small cap makes every block
+ *                 walk many element groups, so that small meshes go through
+ *                 the stage reuse of the copy pipeline
  *   "use_tma"     1 (default) staged FP32 operator where it applies, 0 off
  *   "gs_acc"      mixed-path gather-scatter accumulation: 2 error-free
  *                 FP32 TwoSum (default), 0 FP64, 1 plain FP32

@@ -495,6 +495,8 @@ int sem_set_option(sem_handle h, const char* key, int64_t value) {
   const std::string k(key);
   if ((k == "ax_variant" || k == "ax_variant_pcg") && value >= 0 && value < kTmaVariants) {
     (k == "ax_variant" ? h->ax_variant : h->ax_variant_pcg) = (int)value;
+  } else if (k == "ax_grid_cap" && value >= 0 && value <= (1 << 30)) {
+    h->ax_grid_cap = (int)value;
   } else if (k == "use_tma" && (value == 0 || value == 1)) {
     h->use_tma = value != 0;
   } else if (k == "gs_acc" && value >= 0 && value <= 2) {
@@ -534,6 +536,7 @@ int sem_get_option(sem_handle h, const char* key, double* value) {
   if (k == "ax_variant") *value = h->ax_variant;
   else if (k == "ax_variant_pcg") *value = h->ax_variant_pcg;
   else if (k == "use_tma") *value = h->use_tma ? 1 : 0;
+  else if (k == "ax_grid_cap") *value = h->ax_grid_cap;
   else if (k == "gs_acc") *value = h->gs_acc;
   else if (k == "l2_persist") *value = h->l2_persist ? 1 : 0;
   else if (k == "fuse_gs") *value = h->fuse_gs;

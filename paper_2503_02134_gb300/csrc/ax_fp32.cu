@@ -30,6 +30,7 @@ static bool tma_fits_rt(bool pcg, int v) {
     case 0: return pcg ? tma_fits<n, true, 0>() : tma_fits<n, false, 0>();
     case 1: return pcg ? tma_fits<n, true, 1>() : tma_fits<n, false, 1>();
     case 2: return pcg ? tma_fits<n, true, 2>() : tma_fits<n, false, 2>();
+    case 4: return pcg ? tma_fits<n, true, 4>() : tma_fits<n, false, 4>();
     default: return pcg ? tma_fits<n, true, 3>() : tma_fits<n, false, 3>();
   }
 }
@@ -48,6 +49,7 @@ static int run32(Handle& h, const float* u, float* w, const AxPrologue* pro, int
         case 1: rc = tma_variant<n, 1>(h, u, w, pro, dm, &fit); break;
         case 2: rc = tma_variant<n, 2>(h, u, w, pro, dm, &fit); break;
         case 3: rc = tma_variant<n, 3>(h, u, w, pro, dm, &fit); break;
+        case 4: rc = tma_variant<n, 4>(h, u, w, pro, dm, &fit); break;
         default: rc = tma_variant<n, 0>(h, u, w, pro, dm, &fit); break;
       }
       if (fit) return rc;

@@ -31,7 +31,9 @@ namespace sem {
 // n >= 12 one element already fills 144..256 threads: variants 0..2 are one
 // element per stage with two, three and one stage, variant 3 two elements
 // per stage (two stages).  A variant whose stages do not fit in shared
-// memory (tma_fits) is never launched.
+// memory (tma_fits) is never launched.  Variant 4 (plain mode, line orders
+// below 16 only, see tma_split) splits the stage: G alone single-staged and
+// refilled as soon as the geometric loop is done with it, u double-staged.
 template <int n, int V>
 struct TmaShape {
   static constexpr int n2 = n * n;
@@ -76,12 +78,26 @@ constexpr int tma_ps() {
   return P;
 }
 
+// Variant 4, the split stage: one buffer of G with its own barrier, two
+// buffers of u with theirs.  G of the next element is copied while the
+// block is still on the transposed lines and the epilogue of this one, u of
+// the element after next while it computes this one; with 8 element
+// vectors per block (one more than two blocks of the single-stage variant)
+// two blocks still fit on an SM at n = 14.  Plain mode only: in PCG mode
+// r and J^{-1} are read with p_old at the start of the element.
+template <int n, bool PCG, int V>
+constexpr bool tma_split() {
+  return V == 4 && !PCG && tma_sline<n>() && !tma_gonly<n>();
+}
+
 template <int n, bool PCG, int V>
 constexpr size_t tma_smem_bytes() {
   using S = TmaShape<n, V>;
   constexpr int NV = tma_gonly<n>() ? 0 : (PCG ? 3 : 1);   // vectors in a stage
   constexpr size_t ubuf = tma_gonly<n>() ? S::VEC : 0;      // thread-written u
   constexpr size_t sbuf = tma_sline<n>() ? (size_t)S::EPB * n * tma_ps<n>() * 4 : 0;
+  if constexpr (tma_split<n, PCG, V>())
+    return (size_t)(6 + S::NS) * S::VEC + sbuf + (S::NS + 1) * sizeof(uint64_t);
   return S::NS * (size_t)(NV + 6) * S::VEC + ubuf + sbuf + S::NS * sizeof(uint64_t);
 }
 
@@ -90,6 +106,7 @@ constexpr size_t tma_smem_bytes() {
 constexpr size_t kMaxSmemPerBlock = 232448;
 template <int n, bool PCG, int V>
 constexpr bool tma_fits() {
+  if constexpr (V == 4 && !tma_split<n, PCG, V>()) return false;   // no split stage here
   return tma_smem_bytes<n, PCG, V>() + sizeof(float) * n * (n + 1) +
              sizeof(double) * (TmaShape<n, V>::NT / 32) + 256 <=
          kMaxSmemPerBlock;
@@ -301,7 +318,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   constexpr bool kGOnly = tma_gonly<n>();
   constexpr int NV = kGOnly ? 0 : (PCG ? 3 : 1);   // vectors staged with G
   constexpr int SV = EPB * n3;                 // floats of one vector per stage
-  constexpr int STAGE = (NV + 6) * SV;         // floats per stage
+  // variant 4: G in one buffer (barrier NS), u in NS stages (barriers 0..NS-1)
+  constexpr bool kSplitSt = tma_split<n, PCG, V>();
+  constexpr int STAGE = kSplitSt ? SV : (NV + 6) * SV;   // floats per stage
+  constexpr int STAGED = kSplitSt ? (6 + NS) * SV : NS * STAGE;   // floats of all stages
   // n >= 10: split accumulator chains (one or two blocks of few warps per SM)
   constexpr bool kSplit = n >= 10;
   constexpr bool kSLine = tma_sline<n>();
@@ -309,16 +329,17 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   // line orders with two or more stages refill a stage's G as soon as the
   // geometric loop is done with it (measured: faster with two stages,
   // slower with a single stage, where the block waits for its own copy)
-  constexpr bool kEarly = kSLine && NS >= 2;
+  constexpr bool kEarly = kSLine && NS >= 2 && !kSplitSt;
   extern __shared__ __align__(128) float smem_f[];
-  float* const stage0 = smem_f;
+  float* const stage0 = kSplitSt ? smem_f + 6 * SV : smem_f;
   // kGOnly: u (or p) of the group, then u_r; kSLine: the s-line buffer
   // (u_s, v_s, then w_s)
   constexpr int SSE = n * tma_ps<n>();                 // floats of one element's s-lines
-  float* const sU = smem_f + NS * STAGE;
-  float* const sS = smem_f + NS * STAGE + (kGOnly ? SV : 0);
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + NS * STAGE + (kGOnly ? SV : 0) +
+  float* const sU = smem_f + STAGED;
+  float* const sS = smem_f + STAGED + (kGOnly ? SV : 0);
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + STAGED + (kGOnly ? SV : 0) +
                                                     (kSLine ? EPB * SSE : 0));
+  constexpr int NBAR = NS + (kSplitSt ? 1 : 0);
   __shared__ float sD[n][n + 1];
   __shared__ double sh_red[S::NT / 32];
 
@@ -341,16 +362,30 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   // soon as the stage's G is no longer read): the transaction count of the
   // whole stage, G and, in PCG mode, r and J^{-1}; part 2 (once the group
   // is finished): u, or p_old in PCG mode.  The stage's barrier phase
-  // completes only when the bytes of both parts have landed.
+  // completes only when the bytes of both parts have landed.  Split stage:
+  // part 1 is G into its own buffer (barrier NS), part 2 u into stage st,
+  // each with its own transaction count.
   auto issue = [&](int st, int64_t g, int part) {
     const int64_t e0 = g * EPB;
     const int64_t cnt = E - e0 < EPB ? E - e0 : EPB;
     const uint32_t vb = (uint32_t)(cnt * n3 * 4);
     float* dst = stage0 + st * STAGE;
-    auto copy = [&](float* d, const float* src, uint32_t bytes) {
-      if (l2h) bulk_load_hint(d, src, bytes, &bar[st], pol_first);
-      else bulk_load(d, src, bytes, &bar[st]);
+    auto copy_on = [&](float* d, const float* src, uint32_t bytes, uint64_t* b) {
+      if (l2h) bulk_load_hint(d, src, bytes, b, pol_first);
+      else bulk_load(d, src, bytes, b);
     };
+    auto copy = [&](float* d, const float* src, uint32_t bytes) { copy_on(d, src, bytes, &bar[st]); };
+    if constexpr (kSplitSt) {
+      if (part != 2) {
+        mbar_arrive_expect_tx(&bar[NS], 6 * vb);
+        copy_on(smem_f, G + e0 * 6 * n3, 6 * vb, &bar[NS]);
+      }
+      if (part != 1) {
+        mbar_arrive_expect_tx(&bar[st], vb);
+        copy(dst, uin + e0 * n3, vb);
+      }
+      return;
+    }
     if (part != 2) {
       mbar_arrive_expect_tx(&bar[st], (NV + 6) * vb);
       copy(dst + NV * SV, G + e0 * 6 * n3, 6 * vb);
@@ -366,7 +401,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   };
 
   if (tid == 0) {
-    for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
+    for (int q = 0; q < NBAR; ++q) mbar_init(&bar[q], 1);
     fence_mbar_init();
   }
   for (int q = tid; q < n2; q += blockDim.x) sD[q / n][q % n] = Dg[q];
@@ -374,7 +409,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   if (tid == 0) {
     for (int q = 0; q < NS; ++q) {
       const int64_t g0 = (int64_t)blockIdx.x + (int64_t)q * gridDim.x;
-      if (g0 < ngroups) issue(q, g0, 0);
+      if (g0 < ngroups) issue(q, g0, kSplitSt && q > 0 ? 2 : 0);   // split: G of the first only
     }
   }
   float Di[n], Dj[n], DiT[n], DjT[n];
@@ -423,13 +458,14 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     }
     float* const sb = stage0 + st * STAGE;
     float* const su = kGOnly ? sU : (PCG ? sb + 2 * SV : sb);   // p (formed in place) or u
-    const float* const Gs = sb + NV * SV + ler * 6 * n3 + ij;
+    float* const sg = kSplitSt ? smem_f : sb + NV * SV;   // G1..G6 of the group
+    const float* const Gs = sg + ler * 6 * n3 + ij;
     float* const su_e = su + ler * n3;
     // the two transposed-contraction inputs overwrite G1 and G2 of the
     // stage: each thread reads its own G entries (k, ij) before it writes
     // the same positions, and the stage is refilled only after the last
     // barrier of the group
-    float* const sr_e = sb + NV * SV + ler * 6 * n3;
+    float* const sr_e = sg + ler * 6 * n3;
     float* const ss_e = sr_e + n3;
     const int64_t e = g * EPB + le;
     const bool act = lane_ok && e < E;
@@ -487,6 +523,15 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     // t-column of v_t kept for the transposed product after the plane loop
     float utk[kSLine ? n : 1], vtk[kSLine ? n : 1];
     if constexpr (kSLine) eo_line<n>(Dc.E, Dc.O, ureg, utk);
+    if constexpr (kSplitSt) {
+      // G of this group: its copy has run since the geometric loop of the
+      // block's previous group
+      const bool okg = mbar_wait_bounded(&bar[NS], (uint32_t)(t & 1));
+      if (__syncthreads_or(!okg)) {
+        aborted = true;
+        break;
+      }
+    }
     float wreg[n];
 #pragma unroll
     for (int k = 0; k < n; ++k) wreg[k] = 0.f;
@@ -533,6 +578,16 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     }
     if constexpr (kSLine) eo_line<n>(Dc.ET, Dc.OT, vtk, wreg);
     __syncthreads();
+    if constexpr (kSplitSt) {
+      // G is no longer read: copy the block's next group's G now
+      if (tid == 0) {
+        const int64_t gn = g + (int64_t)gridDim.x;
+        if (gn < ngroups) {
+          fence_proxy_async_smem();
+          issue(st, gn, 1);
+        }
+      }
+    }
     if constexpr (kEarly) {
       // G (and r, J^{-1}) of this stage are no longer read: start the copies
       // of the next group that uses this stage now, not after the group
@@ -595,7 +650,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       const int64_t gn = g + NS * (int64_t)gridDim.x;
       if (gn < ngroups) {
         fence_proxy_async_smem();
-        issue(st, gn, kEarly ? 2 : 0);
+        issue(st, gn, kEarly || kSplitSt ? 2 : 0);
       }
     }
   }
@@ -613,6 +668,8 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         const int done_uses = t > s2 ? (t - 1 - s2) / NS + 1 : 0;
         if (g_out < ngroups) mbar_wait_bounded(&bar[s2], (uint32_t)(done_uses & 1));
       }
+      // split stage: the G copy of group t (issued before the group began)
+      if (kSplitSt) mbar_wait_bounded(&bar[NS], (uint32_t)(t & 1));
     }
     return;
   }
@@ -649,6 +706,7 @@ int ax_tma_launch(Handle& h, const float* u, float* w, const AxPrologue* pro) {
   const int64_t groups = (h.E + S::EPB - 1) / S::EPB;
   int64_t cap = (int64_t)h.num_sms * per_sm;
   if (cap > h.max_blocks) cap = h.max_blocks;
+  if (h.ax_grid_cap > 0 && cap > h.ax_grid_cap) cap = h.ax_grid_cap;
   const int grid = (int)(groups < cap ? groups : cap);
   const float* r = PCG ? (const float*)pro->r : nullptr;
   const float* minv = PCG ? (const float*)pro->minv : nullptr;

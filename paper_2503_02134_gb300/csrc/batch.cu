@@ -46,6 +46,7 @@ struct BatchProb {
 
 constexpr int kUpdItem4 = 1024;           // float4 per update work item (4096 values)
 constexpr int kBatchOrders = 5;           // n = 2, 4, 6, 8, 10 (odd N <= 9)
+constexpr int kBatchVariants = 4;         // launch variants 0..3 of the staged operator shape
 inline int order_slot(int n) { return n / 2 - 1; }
 
 // Batched operator for the problems of one order n: the PCG-mode element
@@ -570,7 +571,7 @@ struct sem_batch_s {
   int first_of[sem::kBatchOrders] = {};   // a problem of each order (its D is the order's D)
   int variant[sem::kBatchOrders] = {};
   int grid[sem::kBatchOrders] = {};
-  float tune_ms[sem::kBatchOrders][sem::kTmaVariants] = {};
+  float tune_ms[sem::kBatchOrders][sem::kBatchVariants] = {};
   std::vector<sem::BatchProb> probs_host;
   cudaGraphExec_t graph = nullptr;
   int graph_chunk = 0;
@@ -755,7 +756,7 @@ static int batch_autotune(sem_batch_s& b) {
     if (!b.present[q]) continue;
     const int n = 2 * q + 2;
     float best = 1e30f;
-    for (int V = 0; V < kTmaVariants && !rc; ++V) {
+    for (int V = 0; V < kBatchVariants && !rc; ++V) {
       for (int p = 0; p < b.count; ++p)
         if (b.subs[p]->n == n) batch_set_groups(b, p, batch_epb_of(n, V));
       SEM_CUDA(cudaMemcpyAsync(b.d_probs, b.probs_host.data(), sizeof(BatchProb) * b.count,
@@ -985,7 +986,7 @@ extern "C" int sem_batch_get_option(sem_batch b, const char* key, double* value)
   else if (order_of("variant_n", &q)) *value = b->present[q] ? b->variant[q] : -1;
   else if (order_of("grid_n", &q)) *value = b->present[q] ? b->grid[q] : 0;
   else if (k.rfind("tune_ms_n", 0) == 0 && k.size() >= 13 && k[k.size() - 2] == 'v' &&
-           k[k.size() - 1] >= '0' && k[k.size() - 1] < '0' + kTmaVariants &&
+           k[k.size() - 1] >= '0' && k[k.size() - 1] < '0' + kBatchVariants &&
            order_of("tune_ms_n", &q))
     *value = b->tune_ms[q][k[k.size() - 1] - '0'];
   else {

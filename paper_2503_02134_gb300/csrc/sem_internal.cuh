@@ -12,7 +12,7 @@
 namespace sem {
 
 constexpr int kMaxN = 15;
-constexpr int kTmaVariants = 4;   // launch variants of the bulk-copy staged FP32 operator
+constexpr int kTmaVariants = 5;   // launch variants of the bulk-copy staged FP32 operator
 constexpr int kMaxn = kMaxN + 1;
 
 // Per-iteration scalars of one PCG solve, resident on the device so that no
@@ -87,9 +87,10 @@ struct Handle {
   int2* gs_chunks = nullptr;   // per 32-segment chunk: {copies m, first slot}
   int64_t n_chunks = 0, n_slots = 0;
   bool use_tma = true;         // FP32 operator: bulk-copy staged kernel where it applies
+  int ax_grid_cap = 0;         // staged FP32 operator: largest grid (0: no cap)
   int ax_variant = 0;          // launch variant of the staged FP32 operator (plain / PCG mode)
   int ax_variant_pcg = 0;
-  float ax_tune_ms[2][4] = {};  // autotuner timings [plain, PCG][variant]
+  float ax_tune_ms[2][kTmaVariants] = {};  // autotuner timings [plain, PCG][variant]
   bool l2_persist = false;     // mixed solve: keep w resident in L2 (access-policy window)
   bool l2_hints = false;       // PCG kernels: per-access L2 eviction priorities keep w resident
   int64_t l2_window_bytes = 0;     // window of the last mixed solve (0: none set)

@@ -462,31 +462,43 @@ def test_kernel_timing_mode(sem):
     S.close()
 
 
-@pytest.mark.parametrize("dims,N", [((5, 4, 3), 7), ((3, 2, 3), 11), ((2, 3, 2), 13),
-                                    ((3, 2, 2), 15)])
+@pytest.mark.parametrize("dims,N", [((5, 4, 3), 7), ((3, 3, 2), 9), ((3, 2, 3), 11),
+                                    ((2, 3, 2), 13), ((3, 2, 2), 15)])
 def test_launch_variants_agree(sem, dims, N):
     """Every staged-operator launch variant and the unstaged kernel give the
     same FP32 result (identical arithmetic per element); the set-up
     autotuner's choice is readable.  At N = 11, 13, 15 (one element already
     fills a block) some variants' stages exceed shared memory: their tuner
     entry is -1 and selecting them runs the unstaged kernel.  At N = 15 the
-    stages hold G only (96 KB), so one or two stages fit in either mode."""
+    stages hold G only (96 KB), so one or two stages fit in either mode.
+    Variant 4 (G in one buffer, u in two) exists in plain mode at N = 9, 11
+    and 13 only.  Each variant also runs with the grid capped at two blocks,
+    so that every block walks several element groups through the reuse of
+    its stages (barrier phases, early and late refills)."""
     P = so.Problem(*dims, N, deform=True)
     S = sem.Solver(*dims, N, deform=True)
-    for key in ("ax_variant", "ax_variant_pcg"):
-        assert sem.sem_get_option(S.h, key) in (0, 1, 2, 3)
+    assert sem.sem_get_option(S.h, "ax_variant") in (0, 1, 2, 3, 4)
+    assert sem.sem_get_option(S.h, "ax_variant_pcg") in (0, 1, 2, 3)
     assert sem.sem_get_option(S.h, "ax_tune_ms_plain_0") > 0
+    tune = {mode: [sem.sem_get_option(S.h, f"ax_tune_ms_{mode}_{v}") for v in range(5)]
+            for mode in ("plain", "pcg")}
+    assert tune["pcg"][4] == -1.0
+    assert (tune["plain"][4] > 0) == (N in (9, 11, 13))
     if N == 15:
         for mode in ("plain", "pcg"):
-            tune = [sem.sem_get_option(S.h, f"ax_tune_ms_{mode}_{v}") for v in range(4)]
-            assert tune[1] == tune[3] == -1.0 and tune[0] > 0 and tune[2] > 0
+            t = tune[mode]
+            assert t[1] == t[3] == -1.0 and t[0] > 0 and t[2] > 0
     u = cu(sem_inputs.uniform_local(P.L, seed=31, dtype=np.float32), torch.float32)
     outs = []
-    for v in range(4):
-        sem.sem_set_option(S.h, "ax_variant", v)
-        w = torch.empty_like(u)
-        sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)
-        outs.append(w)
+    for cap in (0, 2):
+        sem.sem_set_option(S.h, "ax_grid_cap", cap)
+        assert sem.sem_get_option(S.h, "ax_grid_cap") == cap
+        for v in range(5):
+            sem.sem_set_option(S.h, "ax_variant", v)
+            w = torch.empty_like(u)
+            sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)
+            outs.append(w)
+    sem.sem_set_option(S.h, "ax_grid_cap", 0)
     sem.sem_set_option(S.h, "use_tma", 0)
     w = torch.empty_like(u)
     sem.sem_ax_local(S.h, u, w, sem.SEM_MIXED_FP32)
@@ -500,11 +512,14 @@ def test_launch_variants_agree(sem, dims, N):
     sem.sem_rhs(S.h, sem.RHS_UNIFORM, 4, b)
     sem.sem_set_option(S.h, "use_tma", 1)
     xs = []
-    for v in range(4):
-        sem.sem_set_option(S.h, "ax_variant_pcg", v)
-        x, info = S.solve(b, tol=1e-9, maxit=3000, precision=sem.SEM_MIXED_FP32)
-        assert info["rc"] == 0 and info["relres_true"] <= 1e-9
-        xs.append(x)
+    for cap in (0, 2):
+        sem.sem_set_option(S.h, "ax_grid_cap", cap)
+        for v in range(4):
+            sem.sem_set_option(S.h, "ax_variant_pcg", v)
+            x, info = S.solve(b, tol=1e-9, maxit=3000, precision=sem.SEM_MIXED_FP32)
+            assert info["rc"] == 0 and info["relres_true"] <= 1e-9
+            xs.append(x)
+    sem.sem_set_option(S.h, "ax_grid_cap", 0)
     for x in xs[1:]:
         assert rel_maxerr(x.cpu(), xs[0].cpu()) < 1e-7
     S.close()
