@@ -316,7 +316,8 @@ int sem_fma_peak(int fp64, int iters, double* tflops);
  *                                   staged FP32 operator, plain / PCG mode;
  *                                   sem_setup's autotuner picks the fastest
  *                                   (4: G in one buffer refilled after the
- *                                   geometric step, u in two; plain mode at
+ *                                   geometric step, u or p_old in two, r and
+ *                                   J^-1 in one refilled once p is formed;
  *                                   n = 10, 12, 14 only).  A variant whose
  *                                   stages do not fit runs the unstaged kernel
  *   "ax_grid_cap" largest grid of the staged FP32 operator (0, the default:

@@ -78,16 +78,17 @@ constexpr int tma_ps() {
   return P;
 }
 
-// Variant 4, the split stage: one buffer of G with its own barrier, two
-// buffers of u with theirs.  G of the next element is copied while the
-// block is still on the transposed lines and the epilogue of this one, u of
-// the element after next while it computes this one; with 8 element
-// vectors per block (one more than two blocks of the single-stage variant)
-// two blocks still fit on an SM at n = 14.  Plain mode only: in PCG mode
-// r and J^{-1} are read with p_old at the start of the element.
+// Variant 4, the split stage (line orders below 16): one buffer of G with
+// its own barrier, two buffers of u (PCG mode: p_old) with theirs, and in
+// PCG mode one buffer of r and J^{-1} with a third barrier.  G of the next
+// element is copied while the block is still on the transposed lines and
+// the epilogue of this one, r and J^{-1} as soon as p is formed, u of the
+// element after next while it computes this one.  Plain mode holds 8
+// element vectors per block (two blocks still fit on an SM at n = 14), PCG
+// mode 10.
 template <int n, bool PCG, int V>
 constexpr bool tma_split() {
-  return V == 4 && !PCG && tma_sline<n>() && !tma_gonly<n>();
+  return V == 4 && tma_sline<n>() && !tma_gonly<n>();
 }
 
 template <int n, bool PCG, int V>
@@ -97,7 +98,8 @@ constexpr size_t tma_smem_bytes() {
   constexpr size_t ubuf = tma_gonly<n>() ? S::VEC : 0;      // thread-written u
   constexpr size_t sbuf = tma_sline<n>() ? (size_t)S::EPB * n * tma_ps<n>() * 4 : 0;
   if constexpr (tma_split<n, PCG, V>())
-    return (size_t)(6 + S::NS) * S::VEC + sbuf + (S::NS + 1) * sizeof(uint64_t);
+    return (size_t)(6 + (PCG ? 2 : 0) + S::NS) * S::VEC + sbuf +
+           (S::NS + (PCG ? 2 : 1)) * sizeof(uint64_t);
   return S::NS * (size_t)(NV + 6) * S::VEC + ubuf + sbuf + S::NS * sizeof(uint64_t);
 }
 
@@ -305,6 +307,9 @@ __device__ __forceinline__ float col_dot_2acc(const float* __restrict__ p, const
   return s0 + s1;
 }
 
+// Copy parts of the split stage (variant 4), a mask.
+constexpr int kPartG = 1, kPartU = 2, kPartRM = 4, kPartAll = 7;
+
 template <int n, bool PCG, int DM, int V>
 __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     ax_tma_kernel(const float* __restrict__ uin, float* __restrict__ wout,
@@ -318,10 +323,12 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   constexpr bool kGOnly = tma_gonly<n>();
   constexpr int NV = kGOnly ? 0 : (PCG ? 3 : 1);   // vectors staged with G
   constexpr int SV = EPB * n3;                 // floats of one vector per stage
-  // variant 4: G in one buffer (barrier NS), u in NS stages (barriers 0..NS-1)
+  // variant 4: G in one buffer (barrier NS), PCG mode r and J^{-1} in one
+  // (barrier NS + 1), u or p_old in NS stages (barriers 0..NS-1)
   constexpr bool kSplitSt = tma_split<n, PCG, V>();
+  constexpr int SPLIT_FIXED = 6 + (PCG ? 2 : 0);   // split: vectors of the single buffers
   constexpr int STAGE = kSplitSt ? SV : (NV + 6) * SV;   // floats per stage
-  constexpr int STAGED = kSplitSt ? (6 + NS) * SV : NS * STAGE;   // floats of all stages
+  constexpr int STAGED = kSplitSt ? (SPLIT_FIXED + NS) * SV : NS * STAGE;   // floats of all stages
   // n >= 10: split accumulator chains (one or two blocks of few warps per SM)
   constexpr bool kSplit = n >= 10;
   constexpr bool kSLine = tma_sline<n>();
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   // slower with a single stage, where the block waits for its own copy)
   constexpr bool kEarly = kSLine && NS >= 2 && !kSplitSt;
   extern __shared__ __align__(128) float smem_f[];
-  float* const stage0 = kSplitSt ? smem_f + 6 * SV : smem_f;
+  float* const stage0 = kSplitSt ? smem_f + SPLIT_FIXED * SV : smem_f;
   // kGOnly: u (or p) of the group, then u_r; kSLine: the s-line buffer
   // (u_s, v_s, then w_s)
   constexpr int SSE = n * tma_ps<n>();                 // floats of one element's s-lines
@@ -339,7 +346,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   float* const sS = smem_f + STAGED + (kGOnly ? SV : 0);
   uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_f + STAGED + (kGOnly ? SV : 0) +
                                                     (kSLine ? EPB * SSE : 0));
-  constexpr int NBAR = NS + (kSplitSt ? 1 : 0);
+  constexpr int NBAR = NS + (kSplitSt ? (PCG ? 2 : 1) : 0);
+  // split stage: copies of G and of r, J^{-1} issued so far (thread 0), so
+  // that an aborted block knows which phase of their barriers is outstanding
+  uint32_t n_g = 0, n_rm = 0;
   __shared__ float sD[n][n + 1];
   __shared__ double sh_red[S::NT / 32];
 
@@ -363,7 +373,8 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   // whole stage, G and, in PCG mode, r and J^{-1}; part 2 (once the group
   // is finished): u, or p_old in PCG mode.  The stage's barrier phase
   // completes only when the bytes of both parts have landed.  Split stage:
-  // part 1 is G into its own buffer (barrier NS), part 2 u into stage st,
+  // a mask of kPartG (G into its buffer, barrier NS), kPartU (u or p_old
+  // into stage st) and kPartRM (r and J^{-1} into theirs, barrier NS + 1),
   // each with its own transaction count.
   auto issue = [&](int st, int64_t g, int part) {
     const int64_t e0 = g * EPB;
@@ -376,13 +387,20 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     };
     auto copy = [&](float* d, const float* src, uint32_t bytes) { copy_on(d, src, bytes, &bar[st]); };
     if constexpr (kSplitSt) {
-      if (part != 2) {
+      if (part & kPartG) {
         mbar_arrive_expect_tx(&bar[NS], 6 * vb);
         copy_on(smem_f, G + e0 * 6 * n3, 6 * vb, &bar[NS]);
+        ++n_g;
       }
-      if (part != 1) {
+      if (PCG && (part & kPartRM)) {
+        mbar_arrive_expect_tx(&bar[NS + 1], 2 * vb);
+        copy_on(smem_f + 6 * SV, rr + e0 * n3, vb, &bar[NS + 1]);
+        copy_on(smem_f + 7 * SV, minv + e0 * n3, vb, &bar[NS + 1]);
+        ++n_rm;
+      }
+      if (part & kPartU) {
         mbar_arrive_expect_tx(&bar[st], vb);
-        copy(dst, uin + e0 * n3, vb);
+        copy(dst, PCG ? pp + e0 * n3 : uin + e0 * n3, vb);
       }
       return;
     }
@@ -409,7 +427,10 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   if (tid == 0) {
     for (int q = 0; q < NS; ++q) {
       const int64_t g0 = (int64_t)blockIdx.x + (int64_t)q * gridDim.x;
-      if (g0 < ngroups) issue(q, g0, kSplitSt && q > 0 ? 2 : 0);   // split: G of the first only
+      if (g0 < ngroups) {
+        if constexpr (kSplitSt) issue(q, g0, q == 0 ? kPartAll : kPartU);   // G, r, J^{-1}: first only
+        else issue(q, g0, 0);
+      }
     }
   }
   float Di[n], Dj[n], DiT[n], DjT[n];
@@ -451,13 +472,17 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   // (t / NS)-th use, so its barrier phase parity is (t / NS) & 1
   for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, ++t) {
     const int st = t % NS;
-    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((t / NS) & 1));
+    bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((t / NS) & 1));
+    if constexpr (kSplitSt && PCG) ok = ok && mbar_wait_bounded(&bar[NS + 1], (uint32_t)(t & 1));
     if (__syncthreads_or(!ok)) {
       aborted = true;
       break;
     }
     float* const sb = stage0 + st * STAGE;
-    float* const su = kGOnly ? sU : (PCG ? sb + 2 * SV : sb);   // p (formed in place) or u
+    // p (formed in place) or u; r and J^{-1} of the group
+    float* const su = kGOnly ? sU : (PCG && !kSplitSt ? sb + 2 * SV : sb);
+    const float* const sR = kSplitSt ? smem_f + 6 * SV : sb;
+    const float* const sM = kSplitSt ? smem_f + 7 * SV : sb + SV;
     float* const sg = kSplitSt ? smem_f : sb + NV * SV;   // G1..G6 of the group
     const float* const Gs = sg + ler * 6 * n3 + ij;
     float* const su_e = su + ler * n3;
@@ -486,7 +511,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         const int si = k * n2 + ij;
         float v;
         if (PCG) {
-          v = sb[SV + ler * n3 + si] * sb[ler * n3 + si] + beta * su_e[si];
+          v = sM[ler * n3 + si] * sR[ler * n3 + si] + beta * su_e[si];
           if (lane_ok) su_e[si] = v;   // p goes to memory with w in the epilogue
         } else {
           v = su_e[si];
@@ -502,6 +527,16 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       // (constant bank); u_s goes to the s-line buffer at once, u_r over the
       // same row of u once every thread has read u
       if (PCG || kGOnly) __syncthreads();   // u or p complete in shared memory
+      if constexpr (kSplitSt && PCG) {
+        // r and J^{-1} are no longer read: copy the block's next group's
+        if (tid == 0) {
+          const int64_t gn = g + (int64_t)gridDim.x;
+          if (gn < ngroups) {
+            fence_proxy_async_smem();
+            issue(st, gn, kPartRM);
+          }
+        }
+      }
       float a[n], y[n], yr[n];
 #pragma unroll
       for (int l = 0; l < n; ++l) a[l] = su_e[lb_at<n, kSwz>(ir, l, jr)];
@@ -584,7 +619,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         const int64_t gn = g + (int64_t)gridDim.x;
         if (gn < ngroups) {
           fence_proxy_async_smem();
-          issue(st, gn, 1);
+          issue(st, gn, kPartG);
         }
       }
     }
@@ -650,7 +685,7 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
       const int64_t gn = g + NS * (int64_t)gridDim.x;
       if (gn < ngroups) {
         fence_proxy_async_smem();
-        issue(st, gn, kEarly || kSplitSt ? 2 : 0);
+        issue(st, gn, kSplitSt ? kPartU : (kEarly ? 2 : 0));
       }
     }
   }
@@ -668,8 +703,11 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
         const int done_uses = t > s2 ? (t - 1 - s2) / NS + 1 : 0;
         if (g_out < ngroups) mbar_wait_bounded(&bar[s2], (uint32_t)(done_uses & 1));
       }
-      // split stage: the G copy of group t (issued before the group began)
-      if (kSplitSt) mbar_wait_bounded(&bar[NS], (uint32_t)(t & 1));
+      // split stage: the last copies of G and of r, J^{-1} that were issued
+      // (their barrier phases complete in order, so waiting on the last
+      // one covers the earlier ones; a completed phase returns at once)
+      if (kSplitSt && n_g) mbar_wait_bounded(&bar[NS], (n_g - 1) & 1u);
+      if (kSplitSt && PCG && n_rm) mbar_wait_bounded(&bar[NS + 1], (n_rm - 1) & 1u);
     }
     return;
   }

@@ -471,19 +471,19 @@ def test_launch_variants_agree(sem, dims, N):
     fills a block) some variants' stages exceed shared memory: their tuner
     entry is -1 and selecting them runs the unstaged kernel.  At N = 15 the
     stages hold G only (96 KB), so one or two stages fit in either mode.
-    Variant 4 (G in one buffer, u in two) exists in plain mode at N = 9, 11
-    and 13 only.  Each variant also runs with the grid capped at two blocks,
+    Variant 4 (G in one buffer, u or p_old in two, PCG mode r and J^-1 in
+    a third) exists at N = 9, 11 and 13 only.  Each variant also runs with the grid capped at two blocks,
     so that every block walks several element groups through the reuse of
     its stages (barrier phases, early and late refills)."""
     P = so.Problem(*dims, N, deform=True)
     S = sem.Solver(*dims, N, deform=True)
     assert sem.sem_get_option(S.h, "ax_variant") in (0, 1, 2, 3, 4)
-    assert sem.sem_get_option(S.h, "ax_variant_pcg") in (0, 1, 2, 3)
+    assert sem.sem_get_option(S.h, "ax_variant_pcg") in (0, 1, 2, 3, 4)
     assert sem.sem_get_option(S.h, "ax_tune_ms_plain_0") > 0
     tune = {mode: [sem.sem_get_option(S.h, f"ax_tune_ms_{mode}_{v}") for v in range(5)]
             for mode in ("plain", "pcg")}
-    assert tune["pcg"][4] == -1.0
-    assert (tune["plain"][4] > 0) == (N in (9, 11, 13))
+    for mode in ("plain", "pcg"):
+        assert (tune[mode][4] > 0) == (N in (9, 11, 13))
     if N == 15:
         for mode in ("plain", "pcg"):
             t = tune[mode]
@@ -514,7 +514,7 @@ def test_launch_variants_agree(sem, dims, N):
     xs = []
     for cap in (0, 2):
         sem.sem_set_option(S.h, "ax_grid_cap", cap)
-        for v in range(4):
+        for v in range(5):
             sem.sem_set_option(S.h, "ax_variant_pcg", v)
             x, info = S.solve(b, tol=1e-9, maxit=3000, precision=sem.SEM_MIXED_FP32)
             assert info["rc"] == 0 and info["relres_true"] <= 1e-9
