@@ -571,6 +571,9 @@ def main():
                     help="ncu run of the FP32 operator at order N (the order sweep's mesh, or a "
                          "k^3 mesh with --profile-k): two plain calls inside the NVTX range "
                          "bench_profile_sweep")
+    ap.add_argument("--profile-variant", type=int, default=-1, metavar="V",
+                    help="with --profile-sweep: run launch variant V of the staged operator instead "
+                         "of the set-up autotuner's choice")
     ap.add_argument("--profile-batched", action="store_true",
                     help="ncu run of the 64-problem batch: one solve inside an NVTX range")
     ap.add_argument("--profile-batched-small", action="store_true",
@@ -598,6 +601,8 @@ def main():
         c = sem_inputs.order_sweep_case(N)
         k3 = (args.profile_k,) * 3 if args.profile_k > 0 else (c.kx, c.ky, c.kz)
         S = sem.Solver(*k3, N, deform=True)
+        if args.profile_variant >= 0:
+            sem.sem_set_option(S.h, "ax_variant", args.profile_variant)
         u = torch.rand(S.L, dtype=torch.float32, device="cuda",
                        generator=torch.Generator(device="cuda").manual_seed(N))
         w = torch.empty_like(u)
