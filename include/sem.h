@@ -220,9 +220,11 @@ int sem_pcg_solve_ex(sem_handle h, const double* f, const double* x0, double* x,
  * host rows (X: rows x 544, T: rows x n^3, FP32) in BF16 (bf16_mode = 1) or
  * FP32 arithmetic and returns the gradient of mean((y - T)^2) in the same
  * layout; sem_x0_features writes the FP32 features (E x 544) and scales.
- * The BF16 products run on the tensor cores (mma.sync m16n8k16, FP32
- * accumulation; the FP32 gradient-check mode on the CUDA cores).
+ * The BF16 products run on the tcgen05 tensor cores (FP32 accumulator in
+ * tensor memory; the FP32 gradient-check mode on the CUDA cores).
  * sem_x0_set_option keys:
+ *   "umma"          1 (default): BF16 products by tcgen05.mma; 0: by the
+ *                   warp-level mma.sync kernel (m16n8k16), for comparison
  *   "pair_rows"     element rows kept per training pair: a seeded random
  *                   subset (seed: the pair's index); 0 (default) keeps all E
  *   "reserve_rows"  allocate the training set for this many rows at once

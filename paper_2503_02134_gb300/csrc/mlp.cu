@@ -7,7 +7,8 @@
 // Network: 544 (530 features, or 539 with the coarse features, zero
 // padded) -> H -> H -> n^3, ReLU, FP32 master weights with BF16 copies;
 // products on the tensor cores in BF16 with FP32 accumulation (gemm_tc
-// below; the FP32 gradient-check mode uses the CUDA-core GEMM), Adam
+// below: tcgen05 with the accumulator in tensor memory, or warp-level
+// mma.sync; the FP32 gradient-check mode uses the CUDA-core GEMM), Adam
 // (Kingma & Ba 2015) on the master weights.
 // Features of element e: b_L / s_e (n^3 values), the element mean and
 // standard deviation of each geometric factor G1..G6, and the mean of b_L
@@ -20,9 +21,11 @@
 #include <algorithm>
 #include <random>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "pcg.cuh"
+#include "umma.cuh"
 
 namespace sem {
 
@@ -242,25 +245,246 @@ __global__ void reduce_splits(const float* __restrict__ part, int splits, int M,
   }
 }
 
+// Operand preparation for the tcgen05 GEMM: dst[r][k] = src(r, k) in BF16
+// for r < R, k < Kp (zero for k >= K), src(r, k) = TR ? src[k ld + r] :
+// src[r ld + k]; 32 x 32 tiles through shared memory, so that both the
+// reads and the writes run along contiguous addresses.
+template <typename T, bool TR>
+__global__ void __launch_bounds__(256)
+    to_kmajor_bf16(const T* __restrict__ src, int ld, int R, int K, int Kp, bf16* __restrict__ dst) {
+  __shared__ float tile[32][33];   // tile[k - k0][r - r0]
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int i = ty; i < 32; i += 8) {
+    if (TR) {
+      const int k = k0 + i, r = r0 + tx;
+      tile[i][tx] = (k < K && r < R) ? to_f(src[(size_t)k * ld + r]) : 0.f;
+    } else {
+      const int r = r0 + i, k = k0 + tx;
+      tile[tx][i] = (r < R && k < K) ? to_f(src[(size_t)r * ld + k]) : 0.f;
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, k = k0 + tx;
+    if (r < R && k < Kp) dst[(size_t)r * Kp + k] = __float2bfloat16_rn(tile[tx][i]);
+  }
+}
+
+// The same product on the tcgen05 tensor cores (umma.cuh), for K-major
+// BF16 operands A [M][K] (row stride lda) and B [N][K] (ldb), K and the
+// strides multiples of 8, 16-byte aligned: a 128 x 128 output tile per
+// 128-thread block, K in stages of 64 (two stages: the threads load chunk
+// c + 1 while the MMAs of chunk c run), 16-byte coalesced loads into the
+// 128-byte-swizzled layout (each 8-thread phase fills one 128-byte row: no
+// bank conflicts), the FP32 accumulator in 128 TMEM columns.  Epilogue in
+// four passes of 32 columns: each warp reads its TMEM lane quarter into a
+// padded shared tile, then every warp writes whole 32-column row segments.
+// Splits, bias, ReLU and outputs as gemm_tc_kernel.  A bounded wait that
+// gives up sets *err, waits (bounded) for the MMAs in flight, frees the
+// TMEM and leaves the tile unwritten.
+__global__ void __launch_bounds__(128)
+    gemm_umma_kernel(int M, int N, int K, int kchunk, const bf16* __restrict__ A, int lda,
+                     const bf16* __restrict__ B, int ldb, const float* __restrict__ bias, int relu,
+                     float* __restrict__ C32, bf16* __restrict__ C16, int ldc,
+                     float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ uint8_t usm_raw[];
+  uint8_t* const usm = reinterpret_cast<uint8_t*>(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* const sA = usm;
+  uint8_t* const sB = usm + kUStages * kUTileA;
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(usm + kUStages * (kUTileA + kUTileB));
+  uint32_t* const tslot = reinterpret_cast<uint32_t*>(bar + kUStages);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int m0 = blockIdx.y * kUM, n0 = blockIdx.x * kUN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  const int nch = ke > kb ? (ke - kb + kUK - 1) / kUK : 0;
+  if (warp == 0) {
+    tmem_alloc(tslot, kUCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kUStages; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  constexpr uint32_t idesc = umma_idesc(kUM, kUN);
+  bool ok = true;
+  int issued = 0;   // chunks whose MMAs thread 0 issued and committed
+  for (int c = 0; c < nch; ++c) {
+    const int s = c % kUStages;
+    if (c >= kUStages) {
+      // the stage is free once the MMAs of chunk c - 2 have completed
+      const bool w = mbar_wait_bounded(&bar[s], (uint32_t)(((c - kUStages) / kUStages) & 1));
+      if (__syncthreads_or(!w)) {
+        ok = false;
+        break;
+      }
+    }
+    const int k0 = kb + c * kUK;
+    uint8_t* const a_st = sA + s * kUTileA;
+    uint8_t* const b_st = sB + s * kUTileB;
+    // 128 rows x 8 chunks of 16 bytes per operand: 8 per thread, eight
+    // consecutive threads on the eight chunks of one row
+#pragma unroll
+    for (int i = 0; i < kUM * (kUK / 8) / 128; ++i) {
+      const int q = tid + 128 * i;
+      const int row = q >> 3, ch = q & 7;
+      const int gk = k0 + 8 * ch;
+      const int gm = m0 + row, gn = n0 + row;
+      uint4 va = make_uint4(0u, 0u, 0u, 0u), vb = va;
+      if (gk < ke) {
+        if (gm < M) va = __ldg(reinterpret_cast<const uint4*>(A + (size_t)gm * lda + gk));
+        if (gn < N) vb = __ldg(reinterpret_cast<const uint4*>(B + (size_t)gn * ldb + gk));
+      }
+      *reinterpret_cast<uint4*>(a_st + umma_chunk_off(row, ch)) = va;
+      *reinterpret_cast<uint4*>(b_st + umma_chunk_off(row, ch)) = vb;
+    }
+    // the tensor core reads shared memory through the async proxy
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_addr(a_st), b0 = smem_addr(b_st);
+#pragma unroll
+      for (int ks = 0; ks < kUK / 16; ++ks)
+        umma_bf16(tmem, umma_desc(a0 + ks * 32), umma_desc(b0 + ks * 32), idesc,
+                  (c > 0 || ks > 0) ? 1u : 0u);
+      umma_commit(&bar[s]);
+    }
+    issued = c + 1;
+  }
+  if (ok && nch > 0) {
+    // the last commit completes after every MMA issued before it
+    const int c = nch - 1;
+    const bool w = mbar_wait_bounded(&bar[c % kUStages], (uint32_t)((c / kUStages) & 1));
+    if (__syncthreads_or(!w)) ok = false;
+  }
+  if (!ok) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      const int c = issued - 1;
+      if (c >= 0) mbar_wait_bounded(&bar[c % kUStages], (uint32_t)((c / kUStages) & 1));
+    }
+  } else {
+    tc_fence_after();
+    // the operand stages are free: a [128][33] float tile for one pass
+    float (*tileC)[33] = reinterpret_cast<float (*)[33]>(usm);
+#pragma unroll 1
+    for (int cc = 0; cc < kUN / 32; ++cc) {
+      float v[32];
+      if (nch > 0) {
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tileC[warp * 32 + lane][j] = v[j];
+      __syncthreads();
+      const int gn = n0 + cc * 32 + lane;
+#pragma unroll 4
+      for (int rr = warp; rr < kUM; rr += 4) {
+        const int gm = m0 + rr;
+        if (gm < M && gn < N) {
+          const float a = tileC[rr][lane];
+          if (part) {
+            part[((size_t)blockIdx.z * M + gm) * N + gn] = a;
+          } else {
+            float o = a + (bias ? bias[gn] : 0.f);
+            if (relu) o = o > 0.f ? o : 0.f;
+            if (C32) C32[(size_t)gm * ldc + gn] = o;
+            if (C16) C16[(size_t)gm * ldc + gn] = __float2bfloat16_rn(o);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kUCols);
+}
+
 // Partial tiles of the split-K products: up to kMaxSplits x M x N floats.
 constexpr int kMaxSplits = 32;
 
+// Which tensor-core GEMM runs the BF16 products, and the error word of its
+// bounded waits.
+struct TcCfg {
+  bool umma = true;      // tcgen05 (gemm_umma_kernel); false: mma.sync (gemm_tc_kernel)
+  int* err = nullptr;
+  bf16 *ua = nullptr, *ub = nullptr;   // K-major BF16 copies of the operands (grown on demand)
+  int64_t ua_cap = 0, ub_cap = 0;
+};
+
+// Grows one operand scratch buffer to hold `need` values.
+static int tc_scratch(bf16** buf, int64_t* cap, int64_t need) {
+  if (need <= *cap) return 0;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  SEM_CUDA(cudaMalloc((void**)buf, (size_t)need * sizeof(bf16)));
+  *cap = need;
+  return 0;
+}
+
 template <typename TAe, typename TBe, bool TA, bool TB>
-static int gemm_tc(cudaStream_t st, int num_sms, float* scratch, int64_t scratch_floats, int M,
-                   int N, int K, const TAe* A, int lda, const TBe* B, int ldb, const float* bias,
-                   int relu, float* C32, bf16* C16, int ldc, double* ms_acc = nullptr) {
-  const int gx = (N + kTN - 1) / kTN, gy = (M + kTM - 1) / kTM;
+static int gemm_tc(TcCfg& cfg, cudaStream_t st, int num_sms, float* scratch,
+                   int64_t scratch_floats, int M, int N, int K, const TAe* A, int lda, const TBe* B,
+                   int ldb, const float* bias, int relu, float* C32, bf16* C16, int ldc,
+                   double* ms_acc = nullptr) {
+  const int tm = cfg.umma ? kUM : kTM, tn = cfg.umma ? kUN : kTN, tk = cfg.umma ? kUK : kTK;
+  const int gx = (N + tn - 1) / tn, gy = (M + tm - 1) / tm;
   // split K until the grid covers the SMs about twice (weight gradients:
   // K = the batch rows, M x N = one weight matrix)
   int splits = 1;
   while (splits < kMaxSplits && (int64_t)gx * gy * splits < 2LL * num_sms &&
-         K / (2 * splits) >= 4 * kTK && (int64_t)(2 * splits) * M * N <= scratch_floats)
+         K / (2 * splits) >= 4 * tk && (int64_t)(2 * splits) * M * N <= scratch_floats)
     splits *= 2;
-  const int kchunk = ((K + splits - 1) / splits + kTK - 1) / kTK * kTK;
+  const int kchunk = ((K + splits - 1) / splits + tk - 1) / tk * tk;
   dim3 grid(gx, gy, splits);
-  gemm_tc_kernel<TAe, TBe, TA, TB><<<grid, 128, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, bias,
-                                                         relu, C32, C16, ldc,
-                                                         splits > 1 ? scratch : nullptr);
+  if (cfg.umma) {
+    // K-major BF16 operands: used in place where they already are, else
+    // converted (and transposed) into the model's scratch, K padded to a
+    // multiple of 8 with zeros
+    const int Kp = (K + 7) / 8 * 8;
+    const int kch = ((Kp + splits - 1) / splits + kUK - 1) / kUK * kUK;
+    const bf16* Ak = nullptr;
+    const bf16* Bk = nullptr;
+    int ldak = Kp, ldbk = Kp;
+    if (std::is_same<TAe, bf16>::value && !TA && lda % 8 == 0 && K % 8 == 0 &&
+        ((uintptr_t)A & 15) == 0) {
+      Ak = reinterpret_cast<const bf16*>(A);
+      ldak = lda;
+    } else {
+      int rc = tc_scratch(&cfg.ua, &cfg.ua_cap, (int64_t)M * Kp);
+      if (rc) return rc;
+      to_kmajor_bf16<TAe, TA><<<dim3((Kp + 31) / 32, (M + 31) / 32), 256, 0, st>>>(A, lda, M, K, Kp, cfg.ua);
+      Ak = cfg.ua;
+    }
+    if (std::is_same<TBe, bf16>::value && TB && ldb % 8 == 0 && K % 8 == 0 &&
+        ((uintptr_t)B & 15) == 0) {
+      Bk = reinterpret_cast<const bf16*>(B);
+      ldbk = ldb;
+    } else {
+      int rc = tc_scratch(&cfg.ub, &cfg.ub_cap, (int64_t)N * Kp);
+      if (rc) return rc;
+      to_kmajor_bf16<TBe, !TB><<<dim3((Kp + 31) / 32, (N + 31) / 32), 256, 0, st>>>(B, ldb, N, K, Kp, cfg.ub);
+      Bk = cfg.ub;
+    }
+    SEM_CUDA(cudaGetLastError());
+    SEM_CUDA(cudaFuncSetAttribute(gemm_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kUSmem));
+    gemm_umma_kernel<<<grid, 128, kUSmem, st>>>(M, N, Kp, kch, Ak, ldak, Bk, ldbk, bias, relu, C32,
+                                                C16, ldc, splits > 1 ? scratch : nullptr, cfg.err);
+  } else {
+    gemm_tc_kernel<TAe, TBe, TA, TB><<<grid, 128, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, bias,
+                                                           relu, C32, C16, ldc,
+                                                           splits > 1 ? scratch : nullptr);
+  }
   SEM_CUDA(cudaGetLastError());
   if (splits > 1) {
     const int64_t MN = (int64_t)M * N;
@@ -518,6 +742,7 @@ struct sem_x0_model_s {
   sem::bf16* Xall = nullptr;   // features of every element of one pair (E rows)
   sem::bf16* Tall = nullptr;
   int* sel = nullptr;       // selected element rows of one pair
+  sem::TcCfg tc;            // BF16 GEMM kind ("umma" option) and its device error word
 };
 
 namespace sem {
@@ -564,13 +789,13 @@ static int x0_forward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16* 
     return gemm<float, float, false, false>(st, rows, M.out, M.H, M.H2, M.H, wf + M.off[4], M.out,
                                             wf + M.off[5], 0, M.Y, nullptr, M.out);
   }
-  if ((rc = gemm_tc<bf16, bf16, false, false>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.in, X, M.in, wb + M.off[0], M.H,
+  if ((rc = gemm_tc<bf16, bf16, false, false>(M.tc, st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.in, X, M.in, wb + M.off[0], M.H,
                                            wf + M.off[1], 1, M.H1, M.H1b, M.H)))
     return rc;
-  if ((rc = gemm_tc<bf16, bf16, false, false>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.H, M.H1b, M.H, wb + M.off[2], M.H,
+  if ((rc = gemm_tc<bf16, bf16, false, false>(M.tc, st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.H, M.H1b, M.H, wb + M.off[2], M.H,
                                            wf + M.off[3], 1, M.H2, M.H2b, M.H)))
     return rc;
-  return gemm_tc<bf16, bf16, false, false>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.out, M.H, M.H2b, M.H, wb + M.off[4], M.out,
+  return gemm_tc<bf16, bf16, false, false>(M.tc, st, M.h->num_sms, M.gs, M.gs_floats, rows, M.out, M.H, M.H2b, M.H, wb + M.off[4], M.out,
                                         wf + M.off[5], 0, M.Y, nullptr, M.out);
 }
 
@@ -587,7 +812,7 @@ static int x0_backward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16*
                                               M.g + M.off[4], nullptr, M.out)))
       return rc;
   } else {
-    if ((rc = gemm_tc<bf16, float, true, false>(st, M.h->num_sms, M.gs, M.gs_floats, M.H, M.out, rows, M.H2b, M.H, M.dY, M.out, nullptr, 0,
+    if ((rc = gemm_tc<bf16, float, true, false>(M.tc, st, M.h->num_sms, M.gs, M.gs_floats, M.H, M.out, rows, M.H2b, M.H, M.dY, M.out, nullptr, 0,
                                              M.g + M.off[4], nullptr, M.out)))
       return rc;
   }
@@ -598,7 +823,7 @@ static int x0_backward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16*
                                               nullptr, 0, M.dH2, nullptr, M.H)))
       return rc;
   } else {
-    if ((rc = gemm_tc<float, bf16, false, true>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.out, M.dY, M.out, M.w16 + M.off[4], M.out,
+    if ((rc = gemm_tc<float, bf16, false, true>(M.tc, st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.out, M.dY, M.out, M.w16 + M.off[4], M.out,
                                              nullptr, 0, M.dH2, nullptr, M.H)))
       return rc;
   }
@@ -609,7 +834,7 @@ static int x0_backward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16*
                                               M.g + M.off[2], nullptr, M.H)))
       return rc;
   } else {
-    if ((rc = gemm_tc<bf16, float, true, false>(st, M.h->num_sms, M.gs, M.gs_floats, M.H, M.H, rows, M.H1b, M.H, M.dH2, M.H, nullptr, 0,
+    if ((rc = gemm_tc<bf16, float, true, false>(M.tc, st, M.h->num_sms, M.gs, M.gs_floats, M.H, M.H, rows, M.H1b, M.H, M.dH2, M.H, nullptr, 0,
                                              M.g + M.off[2], nullptr, M.H)))
       return rc;
   }
@@ -620,7 +845,7 @@ static int x0_backward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16*
                                               nullptr, 0, M.dH, nullptr, M.H)))
       return rc;
   } else {
-    if ((rc = gemm_tc<float, bf16, false, true>(st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.H, M.dH2, M.H, M.w16 + M.off[2], M.H,
+    if ((rc = gemm_tc<float, bf16, false, true>(M.tc, st, M.h->num_sms, M.gs, M.gs_floats, rows, M.H, M.H, M.dH2, M.H, M.w16 + M.off[2], M.H,
                                              nullptr, 0, M.dH, nullptr, M.H)))
       return rc;
   }
@@ -631,7 +856,7 @@ static int x0_backward(sem_x0_model_s& M, cudaStream_t st, int rows, const bf16*
                                               M.g + M.off[0], nullptr, M.H)))
       return rc;
   } else {
-    if ((rc = gemm_tc<bf16, float, true, false>(st, M.h->num_sms, M.gs, M.gs_floats, M.in, M.H, rows, X, M.in, M.dH, M.H, nullptr, 0,
+    if ((rc = gemm_tc<bf16, float, true, false>(M.tc, st, M.h->num_sms, M.gs, M.gs_floats, M.in, M.H, rows, X, M.in, M.dH, M.H, nullptr, 0,
                                              M.g + M.off[0], nullptr, M.H)))
       return rc;
   }
@@ -723,13 +948,24 @@ static int x0_features(sem_x0_model_s& M, const double* b, bf16* X16, float* X32
   return 0;
 }
 
+// After a stream synchronisation: whether a tensor-core GEMM's bounded wait
+// gave up since the last check (its tile was then left unwritten).
+static int x0_check_err(sem_x0_model_s& M) {
+  int e = 0;
+  SEM_CUDA(cudaMemcpy(&e, M.tc.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!e) return 0;
+  SEM_CUDA(cudaMemset(M.tc.err, 0, sizeof(int)));
+  set_error("learned guess: a tensor-core GEMM's bounded wait gave up (MMA did not complete)");
+  return SEM_ETIMEOUT;
+}
+
 static void x0_free(sem_x0_model_s* M) {
   if (!M) return;
   if (M->h && M->h->stream) cudaStreamSynchronize(M->h->stream);
   void* ptrs[] = {M->w, M->g, M->m, M->v, M->w16, M->Xtr, M->Ttr, M->Xb, M->Tb, M->H1b, M->H2b,
                   M->H1, M->H2, M->Y, M->dY, M->dH, M->dH2, M->rowidx, M->part, M->emean,
                   M->escale, M->u, M->Xf, M->gs, M->zc, M->rc32, M->dz32, M->r64,
-                  M->ratio, M->Xall, M->Tall, M->sel};
+                  M->ratio, M->Xall, M->Tall, M->sel, M->tc.err, M->tc.ua, M->tc.ub};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete M;
@@ -771,7 +1007,7 @@ extern "C" int sem_x0_create(sem_handle h, int hidden, uint64_t seed, sem_x0_mod
       (rc = x0_alloc(*M, o * 4, (void**)&M->m)) || (rc = x0_alloc(*M, o * 4, (void**)&M->v)) ||
       (rc = x0_alloc(*M, o * 2, (void**)&M->w16)) || (rc = x0_alloc(*M, h->E * 8, (void**)&M->emean)) ||
       (rc = x0_alloc(*M, h->E * 8, (void**)&M->escale)) ||
-      (rc = x0_alloc(*M, h->L * 8, (void**)&M->u)) ||
+      (rc = x0_alloc(*M, h->L * 8, (void**)&M->u)) || (rc = x0_alloc(*M, 4, (void**)&M->tc.err)) ||
       (rc = x0_alloc(*M, (M->gs_floats = (int64_t)kMaxSplits *
                                          std::max<int64_t>({sz[0], sz[2], sz[4], 1 << 20})) * 4,
                      (void**)&M->gs))) {
@@ -792,7 +1028,8 @@ extern "C" int sem_x0_create(sem_handle h, int hidden, uint64_t seed, sem_x0_mod
   }
   cudaError_t ce;
   if ((ce = cudaMemcpy(M->w, w.data(), o * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (ce = cudaMemset(M->m, 0, o * 4)) != cudaSuccess || (ce = cudaMemset(M->v, 0, o * 4)) != cudaSuccess) {
+      (ce = cudaMemset(M->m, 0, o * 4)) != cudaSuccess || (ce = cudaMemset(M->v, 0, o * 4)) != cudaSuccess ||
+      (ce = cudaMemset(M->tc.err, 0, 4)) != cudaSuccess) {
     x0_free(M);
     return cuda_fail(ce, "sem_x0_create");
   }
@@ -866,6 +1103,7 @@ extern "C" int sem_x0_gradients(sem_x0_model m, const float* X, const float* T, 
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) rc = cuda_fail(ce, "sem_x0_gradients");
   }
+  if (!rc) rc = x0_check_err(*m);
   cudaFree(Xd);
   cudaFree(Td);
   return rc;
@@ -982,6 +1220,8 @@ extern "C" int sem_x0_set_option(sem_x0_model m, const char* key, int64_t value)
   Handle& h = *m->h;
   if (k == "pair_rows" && value >= 0) {
     m->pair_rows = value;
+  } else if (k == "umma" && (value == 0 || value == 1)) {
+    m->tc.umma = value != 0;
   } else if (k == "reserve_rows" && value >= 0) {
     return x0_reserve(*m, value);
   } else if ((k == "coarse_cycles" || k == "post_cycles") && value >= 0 && value <= 16) {
@@ -1074,6 +1314,7 @@ extern "C" int sem_x0_train(sem_x0_model m, int epochs, int batch, float lr, uin
   cudaStreamSynchronize(st);
   cudaFree(idx_dev);
   if (rc) return rc;
+  if ((rc = x0_check_err(*m))) return rc;
   if (final_loss) *final_loss = loss;
   return SEM_OK;
 }
@@ -1130,5 +1371,5 @@ extern "C" int sem_x0_predict(sem_x0_model m, const double* b, double* x0, int e
     SEM_CUDA(cudaGetLastError());
   }
   SEM_CUDA(cudaStreamSynchronize(st));
-  return SEM_OK;
+  return x0_check_err(*m);
 }

@@ -127,6 +127,56 @@ def test_gradients_match_oracle(sem):
     S.close()
 
 
+@pytest.mark.parametrize("H,rows", [(32, 40), (136, 1500), (256, 4096)])
+def test_tcgen05_gemm_matches_mma_sync_and_oracle(sem, H, rows):
+    """The BF16 products on the tcgen05 tensor cores (TMEM accumulator, the
+    default) against the warp-level mma.sync kernel and the FP64 network on
+    BF16-rounded operands: the forward products (rows x 544 by 544 x H,
+    ragged in M, N and K at H = 136), the data gradients (transposed B) and
+    the weight gradients (transposed A, K = rows: split over several blocks
+    at 1500 and 4096 rows).  The two kernels round the same BF16 products
+    and accumulate in FP32 in different orders, so they agree to 2e-3.  The
+    reference rounds only the inputs, targets and weights to BF16; the GPU
+    also rounds the activations and the back-propagated errors at each
+    product's input (seven of the eight products), which moves the weight
+    gradients by up to about 2 % at these sizes (ReLU masks flip where a
+    pre-activation is near zero): the bound against the reference is 5e-2,
+    still far below the O(1) error of a wrong operand layout."""
+    S = sem.Solver(2, 2, 2, 3)
+    n3 = 64
+    m = sem.sem_x0_create(S.h, H, 0)
+    sizes, offs = sem.sem_x0_param_count(m)
+    total = offs[5] + ((sizes[5] + 31) // 32) * 32
+    net = lx.MLP([544, H, H, n3], seed=5)
+    for q in range(1, 6, 2):
+        net.params[q] = np.random.default_rng(q + 7).standard_normal(net.params[q].shape) * 0.1
+    sem.sem_x0_params(m, _flat_params(net, offs, total), set_=True)
+    g = np.random.default_rng(H + rows)
+    X = g.standard_normal((rows, 544)).astype(np.float32)
+    T = g.standard_normal((rows, n3)).astype(np.float32)
+    out = {}
+    for umma in (1, 0):
+        sem.sem_x0_set_option(m, "umma", umma)
+        grads = np.zeros(total, dtype=np.float32)
+        loss = sem.sem_x0_gradients(m, X, T, rows, 1, grads)
+        out[umma] = (loss, grads)
+    net16 = lx.MLP([544, H, H, n3], params=[_bf16(p) if q % 2 == 0 else p.astype(np.float32)
+                                             for q, p in enumerate(net.params)])
+    ref = net16.gradients(_bf16(X), _bf16(T))
+    ref_loss = net16.loss(_bf16(X), _bf16(T))
+    (l1, g1), (l0, g0) = out[1], out[0]
+    assert abs(l1 - l0) <= 1e-3 * l0
+    assert abs(l1 - ref_loss) <= 1e-2 * ref_loss
+    for q, r in enumerate(ref):
+        a = g1[offs[q]:offs[q] + r.size].astype(np.float64)
+        b = g0[offs[q]:offs[q] + r.size].astype(np.float64)
+        nr = max(np.linalg.norm(r), 1e-30)
+        assert np.linalg.norm(a - b) / nr <= 2e-3, (q, np.linalg.norm(a - b) / nr)
+        assert np.linalg.norm(a - r.reshape(-1)) / nr <= 5e-2, q
+    sem.sem_x0_destroy(m)
+    S.close()
+
+
 def test_training_reduces_loss_and_guess_is_safe(sem):
     """Train on solver-made pairs; the energy-scaled guess is continuous and
     masked, never needs more than a handful of extra iterations, and the
