@@ -574,6 +574,10 @@ def main():
     ap.add_argument("--profile-variant", type=int, default=-1, metavar="V",
                     help="with --profile-sweep: run launch variant V of the staged operator instead "
                          "of the set-up autotuner's choice")
+    ap.add_argument("--profile-learned", action="store_true",
+                    help="ncu run of the learned guess's training: 16 pairs of the 16^3 N = 7 "
+                         "problem, one epoch of batch 8192 (two steps) inside the NVTX range "
+                         "bench_profile_learned; --profile-variant 0 runs the mma.sync products")
     ap.add_argument("--profile-batched", action="store_true",
                     help="ncu run of the 64-problem batch: one solve inside an NVTX range")
     ap.add_argument("--profile-batched-small", action="store_true",
@@ -594,6 +598,30 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     import paper_2503_02134_gb300 as sem
+
+    if args.profile_learned:
+        stream = torch.cuda.Stream()
+        S = sem.Solver(16, 16, 16, 7, deform=True, stream=stream.cuda_stream)
+        m = sem.sem_x0_create(S.h, 256, 7)
+        sem.sem_x0_set_option(m, "umma", 0 if args.profile_variant == 0 else 1)
+        sem.sem_x0_set_option(m, "pair_rows", 1024)
+        with torch.cuda.stream(stream):
+            b = torch.empty(S.L, dtype=torch.float64, device="cuda")
+            x = torch.empty_like(b)
+        for sample in range(16):
+            sem.sem_rhs_fourier(S.h, 5, sample, b)
+            S.solve(b, tol=1e-8, maxit=500, precision=sem.SEM_MIXED_FP32, precond="mg", x=x)
+            sem.sem_x0_add_pair(m, b, x)
+        sem.sem_x0_train(m, 1, 8192, 1e-3, seed=0)      # warm-up (first-use allocations)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bench_profile_learned")
+        loss = sem.sem_x0_train(m, 1, 8192, 1e-3, seed=1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_learned": "ok", "loss": loss}))
+        sem.sem_x0_destroy(m)
+        S.close()
+        return 0
 
     if args.profile_sweep:
         import sem_inputs

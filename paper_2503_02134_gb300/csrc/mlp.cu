@@ -274,26 +274,28 @@ __global__ void __launch_bounds__(256)
 // The same product on the tcgen05 tensor cores (umma.cuh), for K-major
 // BF16 operands A [M][K] (row stride lda) and B [N][K] (ldb), K and the
 // strides multiples of 8, 16-byte aligned: a 128 x 128 output tile per
-// 128-thread block, K in stages of 64 (two stages: the threads load chunk
-// c + 1 while the MMAs of chunk c run), 16-byte coalesced loads into the
-// 128-byte-swizzled layout (each 8-thread phase fills one 128-byte row: no
-// bank conflicts), the FP32 accumulator in 128 TMEM columns.  Epilogue in
-// four passes of 32 columns: each warp reads its TMEM lane quarter into a
-// padded shared tile, then every warp writes whole 32-column row segments.
-// Splits, bias, ReLU and outputs as gemm_tc_kernel.  A bounded wait that
-// gives up sets *err, waits (bounded) for the MMAs in flight, frees the
-// TMEM and leaves the tile unwritten.
+// 128-thread block, K in chunks of 64 through four shared-memory stages
+// filled by 16-byte cp.async copies (three chunks in flight while the MMAs
+// of the fourth run) in the 128-byte-swizzled layout (each 8-thread phase
+// fills one 128-byte row: no bank conflicts), the FP32 accumulator in 128
+// TMEM columns.  Epilogue in four passes of 32 columns: each warp reads its
+// TMEM lane quarter into a padded shared tile, then every warp writes whole
+// 32-column row segments.  Splits, bias, ReLU and outputs as
+// gemm_tc_kernel.  A bounded wait that gives up sets *err, waits (bounded)
+// for the MMAs in flight and for its copies, frees the TMEM and leaves the
+// tile unwritten.
 __global__ void __launch_bounds__(128)
     gemm_umma_kernel(int M, int N, int K, int kchunk, const bf16* __restrict__ A, int lda,
                      const bf16* __restrict__ B, int ldb, const float* __restrict__ bias, int relu,
                      float* __restrict__ C32, bf16* __restrict__ C16, int ldc,
                      float* __restrict__ part, int* __restrict__ err) {
+  constexpr int S = kUStages;
   extern __shared__ uint8_t usm_raw[];
   uint8_t* const usm = reinterpret_cast<uint8_t*>(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* const sA = usm;
-  uint8_t* const sB = usm + kUStages * kUTileA;
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(usm + kUStages * (kUTileA + kUTileB));
-  uint32_t* const tslot = reinterpret_cast<uint32_t*>(bar + kUStages);
+  uint8_t* const sB = usm + S * kUTileA;
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(usm + S * (kUTileA + kUTileB));
+  uint32_t* const tslot = reinterpret_cast<uint32_t*>(bar + S);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int m0 = blockIdx.y * kUM, n0 = blockIdx.x * kUN;
   const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(128)
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int s = 0; s < kUStages; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
     fence_mbar_init();
   }
   tc_fence_before();
@@ -311,43 +313,41 @@ __global__ void __launch_bounds__(128)
   tc_fence_after();
   const uint32_t tmem = *tslot;
   constexpr uint32_t idesc = umma_idesc(kUM, kUN);
-  bool ok = true;
-  int issued = 0;   // chunks whose MMAs thread 0 issued and committed
-  for (int c = 0; c < nch; ++c) {
-    const int s = c % kUStages;
-    if (c >= kUStages) {
-      // the stage is free once the MMAs of chunk c - 2 have completed
-      const bool w = mbar_wait_bounded(&bar[s], (uint32_t)(((c - kUStages) / kUStages) & 1));
-      if (__syncthreads_or(!w)) {
-        ok = false;
-        break;
-      }
-    }
-    const int k0 = kb + c * kUK;
-    uint8_t* const a_st = sA + s * kUTileA;
-    uint8_t* const b_st = sB + s * kUTileB;
-    // 128 rows x 8 chunks of 16 bytes per operand: 8 per thread, eight
-    // consecutive threads on the eight chunks of one row
+  // chunk c into stage c % S: 128 rows x 8 chunks of 16 bytes per operand,
+  // 8 per thread, eight consecutive threads on the eight chunks of one row
+  auto load_chunk = [&](int c) {
+    const int st = c % S, k0 = kb + c * kUK;
+    uint8_t* const a_st = sA + st * kUTileA;
+    uint8_t* const b_st = sB + st * kUTileB;
 #pragma unroll
     for (int i = 0; i < kUM * (kUK / 8) / 128; ++i) {
       const int q = tid + 128 * i;
       const int row = q >> 3, ch = q & 7;
       const int gk = k0 + 8 * ch;
       const int gm = m0 + row, gn = n0 + row;
-      uint4 va = make_uint4(0u, 0u, 0u, 0u), vb = va;
-      if (gk < ke) {
-        if (gm < M) va = __ldg(reinterpret_cast<const uint4*>(A + (size_t)gm * lda + gk));
-        if (gn < N) vb = __ldg(reinterpret_cast<const uint4*>(B + (size_t)gn * ldb + gk));
-      }
-      *reinterpret_cast<uint4*>(a_st + umma_chunk_off(row, ch)) = va;
-      *reinterpret_cast<uint4*>(b_st + umma_chunk_off(row, ch)) = vb;
+      const bool ia = gk < ke && gm < M, ib = gk < ke && gn < N;
+      cp_async16(a_st + umma_chunk_off(row, ch), ia ? A + (size_t)gm * lda + gk : A, ia ? 16u : 0u);
+      cp_async16(b_st + umma_chunk_off(row, ch), ib ? B + (size_t)gn * ldb + gk : B, ib ? 16u : 0u);
     }
+  };
+#pragma unroll
+  for (int c = 0; c < S - 1; ++c) {
+    if (c < nch) load_chunk(c);
+    cp_async_commit();
+  }
+  bool ok = true;
+  int issued = 0;   // chunks whose MMAs thread 0 issued and committed
+  for (int c = 0; c < nch; ++c) {
+    const int s = c % S;
+    // groups committed so far: S - 1 + c; chunk c's is complete once at
+    // most S - 2 are pending
+    cp_async_wait<S - 2>();
     // the tensor core reads shared memory through the async proxy
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = smem_addr(a_st), b0 = smem_addr(b_st);
+      const uint32_t a0 = smem_addr(sA + s * kUTileA), b0 = smem_addr(sB + s * kUTileB);
 #pragma unroll
       for (int ks = 0; ks < kUK / 16; ++ks)
         umma_bf16(tmem, umma_desc(a0 + ks * 32), umma_desc(b0 + ks * 32), idesc,
@@ -355,18 +355,32 @@ __global__ void __launch_bounds__(128)
       umma_commit(&bar[s]);
     }
     issued = c + 1;
+    // chunk c + S - 1 refills the stage of chunk c - 1 once its MMAs are done
+    const int cn = c + S - 1;
+    if (cn < nch) {
+      if (c >= 1) {
+        const bool w = mbar_wait_bounded(&bar[(c - 1) % S], (uint32_t)(((c - 1) / S) & 1));
+        if (__syncthreads_or(!w)) {
+          ok = false;
+          break;
+        }
+      }
+      load_chunk(cn);
+    }
+    cp_async_commit();
   }
   if (ok && nch > 0) {
     // the last commit completes after every MMA issued before it
     const int c = nch - 1;
-    const bool w = mbar_wait_bounded(&bar[c % kUStages], (uint32_t)((c / kUStages) & 1));
+    const bool w = mbar_wait_bounded(&bar[c % S], (uint32_t)((c / S) & 1));
     if (__syncthreads_or(!w)) ok = false;
   }
+  cp_async_wait<0>();   // no copy into this block's shared memory outlives it
   if (!ok) {
     if (tid == 0) {
       atomicExch(err, 1);
       const int c = issued - 1;
-      if (c >= 0) mbar_wait_bounded(&bar[c % kUStages], (uint32_t)((c / kUStages) & 1));
+      if (c >= 0) mbar_wait_bounded(&bar[c % S], (uint32_t)((c / S) & 1));
     }
   } else {
     tc_fence_after();

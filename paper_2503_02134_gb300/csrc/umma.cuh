@@ -21,7 +21,7 @@
 namespace sem {
 
 constexpr int kUM = 128, kUN = 128, kUK = 64;    // CTA tile (M x N) and K per stage
-constexpr int kUStages = 2;
+constexpr int kUStages = 4;
 constexpr uint32_t kUTileA = kUM * kUK * 2;      // bytes of one stage of A (16 KB)
 constexpr uint32_t kUTileB = kUN * kUK * 2;      // and of B
 constexpr uint32_t kUCols = kUN;                 // TMEM columns of the FP32 accumulator
@@ -48,6 +48,21 @@ __host__ __device__ constexpr uint64_t umma_desc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes 0 fills zeros (the
+// source address must still be valid)
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst_smem)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
