@@ -320,7 +320,7 @@ int sem_fma_peak(int fp64, int iters, double* tflops);
  *                                   (4: G in one buffer refilled after the
  *                                   geometric step, u or p_old in two, r and
  *                                   J^-1 in one refilled once p is formed;
- *                                   n = 10, 12, 14 only).  A variant whose
+ *                                   n = 6 .. 14 only).  A variant whose
  *                                   stages do not fit runs the unstaged kernel
  *   "ax_grid_cap" largest grid of the staged FP32 operator (0, the default:
  *                 resident blocks on every SM); a small cap makes every block

@@ -14,11 +14,11 @@
 // The t-direction contractions (u_t = D u along k and the accumulation of
 // D^T v_t) index D with the two unrolled loop counters only, so D is passed
 // by value as a kernel parameter: the entries are constant-bank operands of
-// the FMAs and cost no shared-memory access.  Shared-memory wavefronts are
-// what bounds this kernel at n >= 8 (per k-plane and warp: n/4 vector row
-// loads for u_r, n loads for u_s, 6 for G, the same again for the transposed
-// pass), so the 2n broadcast loads of D per plane that this removes are
-// about a third of them.
+// the FMAs and cost no shared-memory access.  Shared-memory wavefronts
+// bounded the per-node form of this kernel at n >= 8 (per k-plane and
+// warp: n/4 vector row loads for u_r, n loads for u_s, 6 for G, the same
+// again for the transposed pass); the whole-line form that even n >= 6 now
+// takes (tma_sline) needs about 19 shared-memory accesses per node.
 #pragma once
 
 #include "ax_kernel.cuh"
@@ -31,9 +31,9 @@ namespace sem {
 // n >= 12 one element already fills 144..256 threads: variants 0..2 are one
 // element per stage with two, three and one stage, variant 3 two elements
 // per stage (two stages).  A variant whose stages do not fit in shared
-// memory (tma_fits) is never launched.  Variant 4 (plain mode, line orders
-// below 16 only, see tma_split) splits the stage: G alone single-staged and
-// refilled as soon as the geometric loop is done with it, u double-staged.
+// memory (tma_fits) is never launched.  Variant 4 (line orders below 16,
+// see tma_split) splits the stage: G alone single-staged and refilled as
+// soon as the geometric loop is done with it, u double-staged.
 template <int n, int V>
 struct TmaShape {
   static constexpr int n2 = n * n;
@@ -51,11 +51,13 @@ struct TmaShape {
   static constexpr uint32_t VEC = EPB * n3 * 4;                 // bytes of one vector per stage
 };
 
-// Orders whose s-direction contractions run as whole lines through a
-// shared-memory buffer of one element (see ax_tma_kernel).
+// Orders whose contractions run as whole lines (the even-odd halves of D,
+// the s-lines through a shared-memory buffer of one element; see
+// ax_tma_kernel).  Measured against the per-node contractions at n = 6 and
+// 8: 0.80 -> 0.92 and 0.92 -> 0.98 of the HBM peak in plain mode.
 template <int n>
 constexpr bool tma_sline() {
-  return n >= 10;
+  return n >= 6;
 }
 // Orders whose stages hold G only: u (PCG mode: r, J^{-1}, p_old) is read
 // by the threads themselves, one group ahead into registers, and stored to

@@ -462,7 +462,7 @@ def test_kernel_timing_mode(sem):
     S.close()
 
 
-@pytest.mark.parametrize("dims,N", [((5, 4, 3), 7), ((3, 3, 2), 9), ((3, 2, 3), 11),
+@pytest.mark.parametrize("dims,N", [((4, 3, 3), 5), ((5, 4, 3), 7), ((3, 3, 2), 9), ((3, 2, 3), 11),
                                     ((2, 3, 2), 13), ((3, 2, 2), 15)])
 def test_launch_variants_agree(sem, dims, N):
     """Every staged-operator launch variant and the unstaged kernel give the
@@ -472,7 +472,7 @@ def test_launch_variants_agree(sem, dims, N):
     entry is -1 and selecting them runs the unstaged kernel.  At N = 15 the
     stages hold G only (96 KB), so one or two stages fit in either mode.
     Variant 4 (G in one buffer, u or p_old in two, PCG mode r and J^-1 in
-    a third) exists at N = 9, 11 and 13 only.  Each variant also runs with the grid capped at two blocks,
+    a third) exists at the line orders below 15 (N = 5 .. 13).  Each variant also runs with the grid capped at two blocks,
     so that every block walks several element groups through the reuse of
     its stages (barrier phases, early and late refills)."""
     P = so.Problem(*dims, N, deform=True)
@@ -483,7 +483,7 @@ def test_launch_variants_agree(sem, dims, N):
     tune = {mode: [sem.sem_get_option(S.h, f"ax_tune_ms_{mode}_{v}") for v in range(5)]
             for mode in ("plain", "pcg")}
     for mode in ("plain", "pcg"):
-        assert (tune[mode][4] > 0) == (N in (9, 11, 13))
+        assert (tune[mode][4] > 0) == (N in (5, 7, 9, 11, 13))
     if N == 15:
         for mode in ("plain", "pcg"):
             t = tune[mode]
