@@ -55,6 +55,15 @@ inline int order_slot(int n) { return n / 2 - 1; }
 // block owns one contiguous range of the list; the bulk copies of the next
 // NS items are in flight while the block computes.  Each item stores its
 // partial of pap = sum p (A_L p); batch_finalize_pap sums them per problem.
+// Orders whose batched operator takes the whole-line contractions: n >= 10
+// (at n = 6 and 8 the per-node form measured faster in the batch, 3.54
+// against 3.61 s for the 64-problem solve, while the single-problem
+// operator gains from the lines there).
+template <int n>
+constexpr bool batch_sline() {
+  return n >= 10;
+}
+
 template <int n, int V>
 __global__ void __launch_bounds__(TmaShape<n, V>::NT)
     batch_ax_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ items,
@@ -64,9 +73,9 @@ __global__ void __launch_bounds__(TmaShape<n, V>::NT)
   constexpr int n2 = S::n2, n3 = S::n3, EPB = S::EPB, NS = S::NS;
   constexpr int SV = EPB * n3;       // floats of one vector per stage
   constexpr int STAGE = 9 * SV;      // r | J^{-1} | p_old | G1..G6
-  // the whole-line contractions of ax_tma_kernel (n >= 10), with its
-  // s-line buffer after the stages
-  constexpr bool kSLine = tma_sline<n>();
+  // the whole-line contractions of ax_tma_kernel, with its s-line buffer
+  // after the stages
+  constexpr bool kSLine = batch_sline<n>();
   constexpr int SSE = n * tma_ps<n>();
   const int off = seg[0], nitems = seg[1];
   extern __shared__ __align__(128) float smem_f[];
@@ -305,7 +314,7 @@ template <int n, int V>
 constexpr size_t batch_smem_bytes() {
   using S = TmaShape<n, V>;
   return sizeof(float) * (size_t)S::NS * 9 * S::EPB * S::n3 +
-         (tma_sline<n>() ? sizeof(float) * (size_t)S::EPB * n * tma_ps<n>() : 0) +
+         (batch_sline<n>() ? sizeof(float) * (size_t)S::EPB * n * tma_ps<n>() : 0) +
          S::NS * sizeof(uint64_t);
 }
 
