@@ -354,7 +354,9 @@ int sem_fma_peak(int fp64, int iters, double* tflops);
  *   "upd_variant" launch shape of the folded update kernel: register budget
  *                 for 0 (default) four, 1 five, 2 six 256-thread blocks per
  *                 SM; 3 four blocks and an L2 prefetch of each thread's next
- *                 float4 group
+ *                 float4 group; 4 four blocks with 64-bit indices; 5 five
+ *                 blocks.  0 and 5 index in 32 bits where the vectors'
+ *                 float4 indices fit in 31 bits (else 4 and 1)
  *   "mg_hcoarsen" 1 (default): the multigrid preconditioner continues below
  *                 its N = 1 level on halved meshes (see sem_mg_apply); 0:
  *                 orders only.  Changing it discards the built levels.

@@ -508,7 +508,7 @@ int sem_set_option(sem_handle h, const char* key, int64_t value) {
   } else if (k == "mg_hcoarsen" && (value == 0 || value == 1)) {
     if (h->mg_hcoarsen != (value != 0)) mg_free(*h);   // rebuilt on next use
     h->mg_hcoarsen = value != 0;
-  } else if (k == "upd_variant" && value >= 0 && value <= 3) {
+  } else if (k == "upd_variant" && value >= 0 && value <= 5) {
     h->upd_variant = (int)value;
   } else if (k == "l2_hints" && (value == 0 || value == 1)) {
     h->l2_hints = value != 0;

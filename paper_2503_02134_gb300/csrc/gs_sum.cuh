@@ -105,18 +105,17 @@ __device__ __forceinline__ float gs_sum2(float a, float b) {
 // edge) rows: rows at float4 offsets ro[0] < ... < ro[NC-1] (one of them 0,
 // the group itself), plus, where the group's first (last) value lies on an
 // i face, the single values across it in each of those rows.
-template <int NC, int n, int ACC>
-__device__ __forceinline__ float4 gs_gather_rows(const float* __restrict__ w, int64_t q,
-                                                 const int64_t* ro, float4 own, bool xm,
-                                                 bool xp) {
+template <int NC, int n, int ACC, typename I = int64_t>
+__device__ __forceinline__ float4 gs_gather_rows(const float* __restrict__ w, I q, const I* ro,
+                                                 float4 own, bool xm, bool xp) {
   constexpr int n3 = n * n * n;
   const float4* w4 = reinterpret_cast<const float4*>(w);
   float4 R[NC];
   float XM[NC], XP[NC];
 #pragma unroll
   for (int t = 0; t < NC; ++t) {
-    R[t] = ro[t] == 0 ? own : __ldg(w4 + q + ro[t]);
-    const int64_t l0 = 4 * (q + ro[t]);
+    R[t] = ro[t] == 0 ? own : __ldg(w4 + (q + ro[t]));
+    const I l0 = 4 * (q + ro[t]);
     XM[t] = xm ? __ldg(w + l0 - n3 + (n - 1)) : 0.f;
     XP[t] = xp ? __ldg(w + l0 + 3 + n3 - (n - 1)) : 0.f;
   }
@@ -139,13 +138,13 @@ __device__ __forceinline__ float4 gs_gather_rows(const float* __restrict__ w, in
 // values.  Interior rows (no j or k face) take a short path.
 // As gs_gather_row4 below, with the group's own values supplied by the
 // caller (from shared memory in the staged update) and the element's face
-// bits f.
-template <int n, int ACC>
-__device__ __forceinline__ float4 gs_gather_row4_own(const float* __restrict__ w, int64_t q,
-                                                     uint8_t f, float4 own, int64_t kx,
-                                                     int64_t kxky) {
+// bits f.  I: the index type (32-bit where the caller has checked that
+// every index of the vectors fits).
+template <int n, int ACC, typename I = int64_t>
+__device__ __forceinline__ float4 gs_gather_row4_own(const float* __restrict__ w, I q, uint8_t f,
+                                                     float4 own, I kx, I kxky) {
   constexpr int n3 = n * n * n, g4 = n3 / 4, row4 = n / 4;
-  const int64_t e = q / g4;
+  const I e = q / g4;
   const int rem = (int)(q - e * g4);
   const int i0 = (rem % row4) * 4;
   const int j = (rem / row4) % n;
@@ -156,21 +155,21 @@ __device__ __forceinline__ float4 gs_gather_row4_own(const float* __restrict__ w
   const bool xp = i0 + 3 == n - 1 && !(f & 2);
   if (!(dy | dz)) {
     float4 out = own;
-    if (xm) out.x = gs_sum2<ACC>(__ldg(w + 4 * q - n3 + (n - 1)), own.x);
-    if (xp) out.w = gs_sum2<ACC>(own.w, __ldg(w + 4 * q + 3 + n3 - (n - 1)));
+    if (xm) out.x = gs_sum2<ACC>(__ldg(w + (4 * q - n3 + (n - 1))), own.x);
+    if (xp) out.w = gs_sum2<ACC>(own.w, __ldg(w + (4 * q + 3 + n3 - (n - 1))));
     return out;
   }
-  const int64_t oy = (int64_t)dy * (kx * g4 - (int64_t)(n - 1) * row4);
-  const int64_t oz = (int64_t)dz * (kxky * g4 - (int64_t)(n - 1) * n * row4);
+  const I oy = (I)dy * (kx * g4 - (I)(n - 1) * row4);
+  const I oz = (I)dz * (kxky * g4 - (I)(n - 1) * n * row4);
   if (dy && dz) {
-    const int64_t ylo = dy < 0 ? oy : 0, yhi = dy > 0 ? oy : 0;
-    const int64_t zlo = dz < 0 ? oz : 0, zhi = dz > 0 ? oz : 0;
-    const int64_t ro[4] = {zlo + ylo, zlo + yhi, zhi + ylo, zhi + yhi};
-    return gs_gather_rows<4, n, ACC>(w, q, ro, own, xm, xp);
+    const I ylo = dy < 0 ? oy : 0, yhi = dy > 0 ? oy : 0;
+    const I zlo = dz < 0 ? oz : 0, zhi = dz > 0 ? oz : 0;
+    const I ro[4] = {zlo + ylo, zlo + yhi, zhi + ylo, zhi + yhi};
+    return gs_gather_rows<4, n, ACC, I>(w, q, ro, own, xm, xp);
   }
-  const int64_t o = dy ? oy : oz;
-  const int64_t ro[2] = {o < 0 ? o : 0, o > 0 ? o : 0};
-  return gs_gather_rows<2, n, ACC>(w, q, ro, own, xm, xp);
+  const I o = dy ? oy : oz;
+  const I ro[2] = {o < 0 ? o : 0, o > 0 ? o : 0};
+  return gs_gather_rows<2, n, ACC, I>(w, q, ro, own, xm, xp);
 }
 
 template <int n, int ACC>

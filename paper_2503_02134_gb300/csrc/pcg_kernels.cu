@@ -4,6 +4,8 @@
 // convergence test, and the scalar recurrences beta = rtz / rtz_old.
 // Also: the initial residual, the weighted dot (glsc3) and the FP64
 // refinement helpers of the mixed path.
+#include <type_traits>
+
 #include "gs_sum.cuh"
 #include "pcg.cuh"
 #include "tma.cuh"
@@ -201,10 +203,16 @@ __global__ void __launch_bounds__(kVecThreads)
 // were 40-50 % slower than one group at 4 blocks).
 template <int VAR>
 struct UpdShape {
-  static constexpr int MINB = VAR == 1 ? 5 : (VAR == 2 ? 6 : 4);
+  static constexpr int MINB = (VAR == 1 || VAR == 5) ? 5 : (VAR == 2 ? 6 : 4);
   static constexpr int GPT = 1;
   // variant 3: four blocks, and an L2 prefetch of the next trip's streams
   static constexpr bool PREFETCH = VAR == 3;
+  // variants 0 and 5 (four, five blocks) index in 32 bits -- fewer registers
+  // (measured 5.7 % faster at N = 7, 4.5 % at N = 11 than the same kernel
+  // with 64-bit indices, variant 4); the launcher takes them only where
+  // every float4 index of the vectors plus one grid stride fits in 31 bits
+  static constexpr bool I32 = VAR == 0 || VAR == 5;
+  using I = typename std::conditional<I32, int, int64_t>::type;
 };
 
 // Box mesh, n a multiple of 4: the glsc3 weights (mask / multiplicity) of
@@ -212,8 +220,8 @@ struct UpdShape {
 // element's face bits f -- the values the 1-byte codes hold: a node on s
 // faces shared with other elements has 2^s copies (weight 2^-s, exact),
 // and the weight is 0 on a Dirichlet face.
-template <int n>
-__device__ __forceinline__ float4 box_weights4(int64_t q, uint8_t f) {
+template <int n, typename I>
+__device__ __forceinline__ float4 box_weights4(I q, uint8_t f) {
   constexpr int g4 = n * n * n / 4, row4 = n / 4;
   const int rem = (int)(q % g4);
   const int i0 = (rem % row4) * 4;
@@ -246,6 +254,7 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
                                double* __restrict__ partials, double* __restrict__ hist,
                                int l2h) {
   constexpr int GPT = UpdShape<VAR>::GPT;
+  using I = typename UpdShape<VAR>::I;
   // n % 4 == 0: the dot weights from the node positions, not from the 1-byte
   // codes (one load and four reciprocals less per group; measured 1.6 % at
   // N = 7, 3.5 % at N = 11)
@@ -254,8 +263,8 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
   if (s->done) return;
   const float alpha = (float)s->alpha;
   DotAcc<float, DM> a_rr, a_rz;
-  const int64_t n4 = L >> 2;   // L = E n^3 is a multiple of 4 here
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const I n4 = (I)(L >> 2);   // L = E n^3 is a multiple of 4 here
+  const I stride = (I)gridDim.x * (I)blockDim.x;
   // with l2h the streams go through L2 evict-first, leaving w (written by
   // the operator evict-last) resident for the gathers
   const uint64_t pol = l2h ? l2_policy_evict_first() : 0ull;
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
     float4 x, r, p, m, w, wt;
     uchar4 c;
   };
-  auto load = [&](int64_t q) {
+  auto load = [&](I q) {
     Grp g;
     if (l2h) {
       g.x = ld_hint4_rw(reinterpret_cast<const float4*>(x) + q, pol);
@@ -280,9 +289,9 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
     }
     if constexpr (kPos) {
       const uint8_t f = __ldg(faces + q / (n * n * n / 4));
-      g.w = gs_gather_row4_own<n, ACC>(w, q, f, __ldg(reinterpret_cast<const float4*>(w) + q), kx,
-                                       kxky);
-      g.wt = box_weights4<n>(q, f);
+      g.w = gs_gather_row4_own<n, ACC, I>(w, q, f, __ldg(reinterpret_cast<const float4*>(w) + q),
+                                          (I)kx, (I)kxky);
+      g.wt = box_weights4<n, I>(q, f);
     } else if constexpr (n % 4 == 0) {
       g.w = gs_gather_row4<n, ACC>(w, q, faces, kx, kxky);
     } else {
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
     }
     return g;
   };
-  auto finish = [&](int64_t q, Grp g) {
+  auto finish = [&](I q, Grp g) {
     float4 xv = g.x, rv = g.r;
     const float4 pv = g.p, wv = g.w, mv = g.m;
     float4 wt;
@@ -314,9 +323,9 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
     c = wt.z * rv.z; a_rr.add(c, rv.z); a_rz.add(c, mv.z * rv.z);
     c = wt.w * rv.w; a_rr.add(c, rv.w); a_rz.add(c, mv.w * rv.w);
   };
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += GPT * stride) {
+  for (I q = (I)blockIdx.x * (I)blockDim.x + (I)threadIdx.x; q < n4; q += GPT * stride) {
     if constexpr (UpdShape<VAR>::PREFETCH) {
-      const int64_t qn = q + stride;
+      const I qn = q + stride;
       if (qn < n4) {
         prefetch_l2(reinterpret_cast<const float4*>(x) + qn);
         prefetch_l2(reinterpret_cast<const float4*>(r) + qn);
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
     if constexpr (GPT == 1) {
       finish(q, load(q));
     } else {
-      const int64_t q2 = q + stride;
+      const I q2 = q + stride;
       const bool two = q2 < n4;
       const Grp g1 = load(q);
       Grp g2 = g1;
@@ -760,6 +769,12 @@ template <int DM, int ACC>
 static void update_gs_dispatch(Handle& h, float* x, float* r, const float* p, const float* w,
                                const float* minv, PcgScalars* s, double* hist, int slot) {
   const int64_t kx = h.kx, kxky = (int64_t)h.kx * h.ky;
+  // 32-bit indices: every float4 index plus a grid stride, and the element
+  // offsets of the neighbours, below 2^31
+  const bool i32_ok = h.L / 4 + (int64_t)h.max_blocks * kVecThreads < ((int64_t)1 << 31) &&
+                      kxky * h.n * h.n * h.n / 4 < ((int64_t)1 << 30);
+  int uv = h.upd_variant;
+  if (!i32_ok && (uv == 0 || uv == 5)) uv = uv == 0 ? 4 : 1;   // the 64-bit form
   if (h.upd_tma && h.n == 8) {
     // bulk-copy staged variant (its launch errors surface at the next check)
     update_tma_launch<DM, ACC>(h, x, r, p, w, minv, s, hist);
@@ -768,10 +783,12 @@ static void update_gs_dispatch(Handle& h, float* x, float* r, const float* p, co
 #define SEM_UPD_ROW4(NN)                                                                  \
   case NN: {                                                                              \
     auto kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 0>;                               \
-    if (h.upd_variant == 1) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 1>;            \
-    if (h.upd_variant == 2) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 2>;            \
-    if (h.upd_variant == 3) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 3>;            \
-    const int grid = fused_grid(h, kern, slot + 4 * h.upd_variant);                       \
+    if (uv == 1) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 1>;                       \
+    if (uv == 2) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 2>;                       \
+    if (uv == 3) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 3>;                       \
+    if (uv == 4) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 4>;                       \
+    if (uv == 5) kern = cg_update32_gs_row4_kernel<NN, DM, ACC, 5>;                       \
+    const int grid = fused_grid(h, kern, slot + 4 * uv);                                  \
     kern<<<grid, kVecThreads, 0, h.stream>>>(x, r, p, w, h.cw8, minv, h.bfaces, kx, kxky, \
                                              h.L, s, h.partials, hist, h.l2_hints ? 1 : 0); \
     return;                                                                               \

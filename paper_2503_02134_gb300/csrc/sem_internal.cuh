@@ -98,8 +98,8 @@ struct Handle {
   int gs_acc = 2;              // mixed-path accumulation: 2 TwoSum (default), 0 FP64, 1 FP32
   int fuse_gs = 1;             // FP32 PCG on box meshes: summation folded into the update
                                // (1: n a multiple of 4, 2: every n, 0: never)
-  int upd_gs_occ[16] = {};     // resident blocks per SM of the fused update kernels (0: not yet read)
-  int upd_variant = 0;         // fused update launch shape (0..3, see pcg_kernels.cu UpdShape)
+  int upd_gs_occ[24] = {};     // resident blocks per SM of the fused update kernels (0: not yet read)
+  int upd_variant = 0;         // fused update launch shape (0..5, see pcg_kernels.cu UpdShape)
   bool upd_tma = false;        // fused update (n = 8): bulk-copy staged variant
   bool mg_hcoarsen = true;     // multigrid: h-levels below the N = 1 level
 

@@ -392,7 +392,7 @@ def test_update_variants(sem, dims, N):
     mixed = sem.SEM_MIXED_FP32
     ref, iref = S.solve(b, tol=1e-9, maxit=3000, precision=mixed)
     assert iref["rc"] == 0 and iref["relres_true"] <= 1e-9
-    for v in (1, 2, 3):
+    for v in (1, 2, 3, 4, 5):
         sem.sem_set_option(S.h, "upd_variant", v)
         assert sem.sem_get_option(S.h, "upd_variant") == v
         x, info = S.solve(b, tol=1e-9, maxit=3000, precision=mixed)
