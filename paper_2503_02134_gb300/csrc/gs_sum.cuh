@@ -213,20 +213,19 @@ __device__ __forceinline__ float4 gs_gather_row4(const float* __restrict__ w, in
 // two rows, but its two float2 halves each lie inside one row (rows have an
 // even length).  The copies of a float2 pair, as gs_gather_rows for float4:
 // rows at float2 offsets ro[t], and single values across the i faces.
-template <int NC, int n, int ACC>
-__device__ __forceinline__ float2 gs_gather_rows2(const float* __restrict__ w, int64_t q2,
-                                                  const int64_t* ro, float2 own, bool xm,
-                                                  bool xp) {
+template <int NC, int n, int ACC, typename I = int64_t>
+__device__ __forceinline__ float2 gs_gather_rows2(const float* __restrict__ w, I q2, const I* ro,
+                                                  float2 own, bool xm, bool xp) {
   constexpr int n3 = n * n * n;
   const float2* w2 = reinterpret_cast<const float2*>(w);
   float2 R[NC];
   float XM[NC], XP[NC];
 #pragma unroll
   for (int t = 0; t < NC; ++t) {
-    R[t] = ro[t] == 0 ? own : __ldg(w2 + q2 + ro[t]);
-    const int64_t l0 = 2 * (q2 + ro[t]);
-    XM[t] = xm ? __ldg(w + l0 - n3 + (n - 1)) : 0.f;
-    XP[t] = xp ? __ldg(w + l0 + 1 + n3 - (n - 1)) : 0.f;
+    R[t] = ro[t] == 0 ? own : __ldg(w2 + (q2 + ro[t]));
+    const I l0 = 2 * (q2 + ro[t]);
+    XM[t] = xm ? __ldg(w + (l0 - n3 + (n - 1))) : 0.f;
+    XP[t] = xp ? __ldg(w + (l0 + 1 + n3 - (n - 1))) : 0.f;
   }
   GsSum<float, ACC> s0, s1;
 #pragma unroll
@@ -240,12 +239,12 @@ __device__ __forceinline__ float2 gs_gather_rows2(const float* __restrict__ w, i
 }
 
 // The summed copies of float2 pair q2 (element face bits f).
-template <int n, int ACC>
-__device__ __forceinline__ float2 gs_gather_pair(const float* __restrict__ w, int64_t q2,
-                                                 uint8_t f, int64_t kx, int64_t kxky) {
+template <int n, int ACC, typename I = int64_t>
+__device__ __forceinline__ float2 gs_gather_pair(const float* __restrict__ w, I q2, uint8_t f,
+                                                 I kx, I kxky) {
   static_assert(n % 2 == 0, "float2 pairs need an even n");
   constexpr int n3 = n * n * n, g2 = n3 / 2, row2 = n / 2;
-  const int64_t e = q2 / g2;
+  const I e = q2 / g2;
   const int rem = (int)(q2 - e * g2);
   const int i0 = (rem % row2) * 2;
   const int j = (rem / row2) % n;
@@ -257,33 +256,33 @@ __device__ __forceinline__ float2 gs_gather_pair(const float* __restrict__ w, in
   const float2 own = __ldg(reinterpret_cast<const float2*>(w) + q2);
   if (!(dy | dz)) {
     float2 out = own;
-    if (xm) out.x = gs_sum2<ACC>(__ldg(w + 2 * q2 - n3 + (n - 1)), own.x);
-    if (xp) out.y = gs_sum2<ACC>(own.y, __ldg(w + 2 * q2 + 1 + n3 - (n - 1)));
+    if (xm) out.x = gs_sum2<ACC>(__ldg(w + (2 * q2 - n3 + (n - 1))), own.x);
+    if (xp) out.y = gs_sum2<ACC>(own.y, __ldg(w + (2 * q2 + 1 + n3 - (n - 1))));
     return out;
   }
-  const int64_t oy = (int64_t)dy * (kx * g2 - (int64_t)(n - 1) * row2);
-  const int64_t oz = (int64_t)dz * (kxky * g2 - (int64_t)(n - 1) * n * row2);
+  const I oy = (I)dy * (kx * g2 - (I)(n - 1) * row2);
+  const I oz = (I)dz * (kxky * g2 - (I)(n - 1) * n * row2);
   if (dy && dz) {
-    const int64_t ylo = dy < 0 ? oy : 0, yhi = dy > 0 ? oy : 0;
-    const int64_t zlo = dz < 0 ? oz : 0, zhi = dz > 0 ? oz : 0;
-    const int64_t ro[4] = {zlo + ylo, zlo + yhi, zhi + ylo, zhi + yhi};
-    return gs_gather_rows2<4, n, ACC>(w, q2, ro, own, xm, xp);
+    const I ylo = dy < 0 ? oy : 0, yhi = dy > 0 ? oy : 0;
+    const I zlo = dz < 0 ? oz : 0, zhi = dz > 0 ? oz : 0;
+    const I ro[4] = {zlo + ylo, zlo + yhi, zhi + ylo, zhi + yhi};
+    return gs_gather_rows2<4, n, ACC, I>(w, q2, ro, own, xm, xp);
   }
-  const int64_t o = dy ? oy : oz;
-  const int64_t ro[2] = {o < 0 ? o : 0, o > 0 ? o : 0};
-  return gs_gather_rows2<2, n, ACC>(w, q2, ro, own, xm, xp);
+  const I o = dy ? oy : oz;
+  const I ro[2] = {o < 0 ? o : 0, o > 0 ? o : 0};
+  return gs_gather_rows2<2, n, ACC, I>(w, q2, ro, own, xm, xp);
 }
 
 // The summed copies of float4 group q for n = 6, 10, 14: its two float2
 // halves (both in element q / (n^3 / 4), since n^3 / 2 is even).
-template <int n, int ACC>
-__device__ __forceinline__ float4 gs_gather_row2x2(const float* __restrict__ w, int64_t q,
-                                                   const uint8_t* __restrict__ faces,
-                                                   int64_t kx, int64_t kxky) {
+template <int n, int ACC, typename I = int64_t>
+__device__ __forceinline__ float4 gs_gather_row2x2(const float* __restrict__ w, I q,
+                                                   const uint8_t* __restrict__ faces, I kx,
+                                                   I kxky) {
   constexpr int g4 = n * n * n / 4;
   const uint8_t f = __ldg(faces + q / g4);
-  const float2 a = gs_gather_pair<n, ACC>(w, 2 * q, f, kx, kxky);
-  const float2 b = gs_gather_pair<n, ACC>(w, 2 * q + 1, f, kx, kxky);
+  const float2 a = gs_gather_pair<n, ACC, I>(w, 2 * q, f, kx, kxky);
+  const float2 b = gs_gather_pair<n, ACC, I>(w, 2 * q + 1, f, kx, kxky);
   return make_float4(a.x, a.y, b.x, b.y);
 }
 

@@ -210,7 +210,7 @@ struct UpdShape {
   // variants 0 and 5 (four, five blocks) index in 32 bits -- fewer registers
   // (measured 5.7 % faster at N = 7, 4.5 % at N = 11 than the same kernel
   // with 64-bit indices, variant 4); the launcher takes them only where
-  // every float4 index of the vectors plus one grid stride fits in 31 bits
+  // every value index the kernel forms fits in 31 bits
   static constexpr bool I32 = VAR == 0 || VAR == 5;
   using I = typename std::conditional<I32, int, int64_t>::type;
 };
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kVecThreads, UpdShape<VAR>::MINB)
     } else if constexpr (n % 4 == 0) {
       g.w = gs_gather_row4<n, ACC>(w, q, faces, kx, kxky);
     } else {
-      g.w = gs_gather_row2x2<n, ACC>(w, q, faces, kx, kxky);
+      g.w = gs_gather_row2x2<n, ACC, I>(w, q, faces, (I)kx, (I)kxky);
     }
     return g;
   };
@@ -769,10 +769,10 @@ template <int DM, int ACC>
 static void update_gs_dispatch(Handle& h, float* x, float* r, const float* p, const float* w,
                                const float* minv, PcgScalars* s, double* hist, int slot) {
   const int64_t kx = h.kx, kxky = (int64_t)h.kx * h.ky;
-  // 32-bit indices: every float4 index plus a grid stride, and the element
-  // offsets of the neighbours, below 2^31
-  const bool i32_ok = h.L / 4 + (int64_t)h.max_blocks * kVecThreads < ((int64_t)1 << 31) &&
-                      kxky * h.n * h.n * h.n / 4 < ((int64_t)1 << 30);
+  // 32-bit indices: every value index the kernel forms (float4, float2
+  // and float indices of the vectors, past the end by at most one grid
+  // stride of float4 groups; neighbour offsets are below L / 4) below 2^31
+  const bool i32_ok = h.L + 4 * (int64_t)h.max_blocks * kVecThreads < ((int64_t)1 << 31);
   int uv = h.upd_variant;
   if (!i32_ok && (uv == 0 || uv == 5)) uv = uv == 0 ? 4 : 1;   // the 64-bit form
   if (h.upd_tma && h.n == 8) {
